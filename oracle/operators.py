@@ -1,0 +1,213 @@
+"""Oracle: global operators and solves (eqs. ad5, pressure_final, d2m, m2d).
+
+With G the global gradient (rows (c, j, k): component c of dual DOF k of
+edge j; columns (i, l): DOF l of triangle i) built from the blocks Q_ij of
+eq. ad5.2, and Mhat^{-1} block diagonal (dense Cholesky per edge, both
+components), the left-hand side of eq. pressure_final is
+    sum_j D_ij Mhat_j^{-1} (Q_lj p_l + Q_rj p_r) = -(G^T Mhat^{-1} G p)_i
+because D = -Q^T.  Reading (sign): the oracle and the library expose the
+symmetric positive semidefinite form
+    S = dt^2 * G^T Mhat^{-1} G,
+so a caller holding the paper's right-hand side negates it; and the implicit
+diffusion system of eq. ad5 (lambda = nu) becomes
+    H = Mbar + nu*dt * G^T Mhat^{-1} G   (SPD).
+Mean-zero reading: the Schur solution is the x with sum(x) = 0 (coefficient
+space), b is projected the same way.
+
+Solves: sparse direct LU (SuperLU) of S with DOF 0 grounded, shifted to
+mean zero (equal to the bordered-system solution), LU of H; a plain CG (x0 = 0, stop at ||r||/||b|| <= tol) for sizes
+where a factorisation does not fit.
+
+Vectors are in the natural numbering: triangle i, local DOF k at i*Nphi + k.
+
+Test infrastructure only (see the package docstring).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .assemble import Blocks
+
+
+def gradient_matrix(bl: Blocks) -> sp.csr_matrix:
+    """Global G (2*Nd*Npsi x Ne*Nphi) from the blocks Q_ij of eq. ad5.2."""
+    nd = bl.conn.n_edge
+    npsi, nphi = bl.Q.shape[2], bl.Q.shape[3]
+    rows, cols, vals = [], [], []
+    kk, ll = np.meshgrid(np.arange(npsi), np.arange(nphi), indexing="ij")
+    for side in range(2):
+        tri_id = bl.conn.lr[:, side]
+        for c in range(2):
+            r = c * nd * npsi + np.arange(nd)[:, None, None] * npsi + kk[None]
+            col = tri_id[:, None, None] * nphi + ll[None]
+            rows.append(np.broadcast_to(r, (nd, npsi, nphi)).ravel())
+            cols.append(np.broadcast_to(col, (nd, npsi, nphi)).ravel())
+            vals.append(bl.Q[:, side, :, :, c].ravel())
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    keep = vals != 0.0
+    G = sp.coo_matrix((vals[keep], (rows[keep], cols[keep])),
+                      shape=(2 * nd * npsi, bl.conn.n_tri * nphi))
+    return G.tocsr()
+
+
+def divergence_matrix(bl: Blocks) -> sp.csr_matrix:
+    """Global D (Ne*Nphi x 2*Nd*Npsi) from the blocks D_ij of eq. D."""
+    nd = bl.conn.n_edge
+    nphi, npsi = bl.D.shape[2], bl.D.shape[3]
+    rows, cols, vals = [], [], []
+    kk, ll = np.meshgrid(np.arange(nphi), np.arange(npsi), indexing="ij")
+    for side in range(2):
+        tri_id = bl.conn.lr[:, side]
+        for c in range(2):
+            r = tri_id[:, None, None] * nphi + kk[None]
+            col = c * nd * npsi + np.arange(nd)[:, None, None] * npsi + ll[None]
+            rows.append(np.broadcast_to(r, (nd, nphi, npsi)).ravel())
+            cols.append(np.broadcast_to(col, (nd, nphi, npsi)).ravel())
+            vals.append(bl.D[:, side, :, :, c].ravel())
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    keep = vals != 0.0
+    D = sp.coo_matrix((vals[keep], (rows[keep], cols[keep])),
+                      shape=(bl.conn.n_tri * nphi, 2 * nd * npsi))
+    return D.tocsr()
+
+
+def dual_mass_inverse(bl: Blocks) -> np.ndarray:
+    """Mhat_j^{-1} per edge by dense Cholesky: f64[Nd, Npsi, Npsi]."""
+    Lc = np.linalg.cholesky(bl.Mhat)
+    eye = np.broadcast_to(np.eye(bl.Mhat.shape[1]), bl.Mhat.shape)
+    Linv = np.linalg.solve(Lc, eye)
+    return np.swapaxes(Linv, -1, -2) @ Linv
+
+
+def block_diag_csr(blocks, repeat=1) -> sp.csr_matrix:
+    mats = [sp.csr_matrix(b) for b in blocks] * repeat
+    return sp.block_diag(mats, format="csr")
+
+
+class Operators:
+    """Global sparse operators of one mesh and degree."""
+
+    def __init__(self, bl: Blocks):
+        self.bl = bl
+        self.p = bl.p
+        self.nphi = bl.Mbar.shape[1]
+        self.npsi = bl.Mhat.shape[1]
+        self.n = bl.conn.n_tri * self.nphi
+        self.nd = bl.conn.n_edge
+        self.G = gradient_matrix(bl)
+        self.Dm = divergence_matrix(bl)
+        self.Minv = dual_mass_inverse(bl)
+        self._K = None
+
+    # -- factored applies -------------------------------------------------
+    def apply_Mhat_inv(self, v):
+        """v laid out [2, Nd, Npsi] (flattened)."""
+        v = v.reshape(2, self.nd, self.npsi)
+        return np.einsum("jkl,cjl->cjk", self.Minv, v).ravel()
+
+    def apply_K(self, x):
+        """K_h x = G^T Mhat^{-1} G x."""
+        return self.G.T @ self.apply_Mhat_inv(self.G @ x)
+
+    def apply_schur(self, x, dt):
+        return dt * dt * self.apply_K(x)
+
+    def apply_Mbar(self, x):
+        x = x.reshape(-1, self.nphi)
+        return np.einsum("ekl,el->ek", self.bl.Mbar, x).ravel()
+
+    def apply_helmholtz(self, x, nu_dt):
+        return self.apply_Mbar(x) + nu_dt * self.apply_K(x)
+
+    # -- assembled matrices ----------------------------------------------
+    def K(self):
+        if self._K is None:
+            Minv = block_diag_csr(self.Minv, repeat=2)
+            self._K = (self.G.T @ (Minv @ self.G)).tocsr()
+        return self._K
+
+    def schur_matrix(self, dt):
+        return (dt * dt) * self.K()
+
+    def helmholtz_matrix(self, nu_dt):
+        return (block_diag_csr(self.bl.Mbar) + nu_dt * self.K()).tocsr()
+
+    # -- projections of eqs. d2m / m2d ------------------------------------
+    def d2m_rhs(self, vhat):
+        """b_i = sum_{j in S_i} U_ij^T vhat_j (the M-weighted form of eq. d2m)
+        for one scalar dual field vhat [Nd, Npsi]."""
+        vhat = vhat.reshape(self.nd, self.npsi)
+        out = np.zeros((self.bl.conn.n_tri, self.nphi))
+        for side in range(2):
+            contrib = np.einsum("jkl,jk->jl", self.bl.U[:, side], vhat)
+            np.add.at(out, self.bl.conn.lr[:, side], contrib)
+        return out.ravel()
+
+    def d2m(self, vhat):
+        """Eq. d2m: vbar_i = Mbar_i^{-1} sum_j U_ij^T vhat_j."""
+        b = self.d2m_rhs(vhat).reshape(-1, self.nphi)
+        return np.linalg.solve(self.bl.Mbar, b[..., None])[..., 0].ravel()
+
+    def m2d(self, vbar):
+        """Eq. m2d: vhat_j = Mhat_j^{-1} (U_lj vbar_l + U_rj vbar_r)."""
+        vbar = vbar.reshape(-1, self.nphi)
+        lr = self.bl.conn.lr
+        t = (np.einsum("jkl,jl->jk", self.bl.U[:, 0], vbar[lr[:, 0]])
+             + np.einsum("jkl,jl->jk", self.bl.U[:, 1], vbar[lr[:, 1]]))
+        return np.einsum("jkl,jl->jk", self.Minv, t).ravel()
+
+
+def project_mean(v):
+    return v - v.mean()
+
+
+def schur_solve_direct(S, b):
+    """Mean-zero solution of S x = Pi b.  The nullspace of S is span{1}, so
+    grounding DOF 0 (deleting its row and column) leaves a nonsingular SPD
+    system; its sparse LU solution (x_0 = 0) is then shifted to mean zero.
+    This equals the solution of the bordered system [[S, 1], [1^T, 0]]
+    without the fill-in of the dense border."""
+    S = sp.csr_matrix(S)
+    n = S.shape[0]
+    rhs = project_mean(b)
+    A = S[1:, 1:].tocsc()
+    x = np.zeros(n)
+    x[1:] = spla.splu(A).solve(rhs[1:])
+    return project_mean(x)
+
+
+def direct_solve(A, b):
+    return spla.splu(sp.csc_matrix(A)).solve(b)
+
+
+def cg(apply, b, tol=1e-12, maxit=100000, mean_zero=False):
+    """Plain conjugate gradients, x0 = 0, stop at ||r||_2 <= tol ||b||_2.
+    Returns (x, iterations, recursive relative residual)."""
+    if mean_zero:
+        b = project_mean(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    bn = np.sqrt(b @ b)
+    if bn == 0.0:
+        return x, 0, 0.0
+    it = 0
+    while np.sqrt(rr) > tol * bn and it < maxit:
+        q = apply(p)
+        if mean_zero:
+            q = project_mean(q)
+        alpha = rr / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = r @ r
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it, np.sqrt(rr) / bn
