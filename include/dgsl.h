@@ -1,0 +1,250 @@
+/*
+ * dgsl — GB300-native implicit-stage solver library for the staggered
+ * semi-Lagrangian IMEX DG method of Tavelli & Boscheri.
+ *
+ * The library builds, from a periodic triangulation and a degree p, the
+ * operators of the implicit stage (Sec. 2.3-2.4) and solves
+ *
+ *   pressure Schur system (eq. pressure_final, eq. pressure_IMEX):
+ *       S p = b,   S = dt^2 * G^T Mhat^{-1} G          (symmetric, PSD)
+ *   implicit diffusion / viscosity system (eq. ad5, lambda = nu):
+ *       H v = b,   H = Mbar + nu*dt * G^T Mhat^{-1} G  (SPD)
+ *
+ * with G the gradient operator of eq. ad5.2 (blocks Q_ij), Mhat the C0 dual
+ * mass matrix of eq. Mj (one (p+1)^2 block per edge quad) and Mbar the main
+ * mass matrix of eq. Mi.  Because D = -Q^T (Sec. 2.3), the paper's left-hand
+ * side sum_j D_ij Mhat_j^{-1}(Q_lj p_l + Q_rj p_r) equals -(G^T Mhat^{-1} G p)_i;
+ * the library exposes the positive semidefinite sign, so a caller holding the
+ * paper's right-hand side passes its negation.
+ *
+ * Conventions for every call below
+ *  - Every call returns an int status (DGSL_OK = 0).  No C++ exception
+ *    crosses this boundary.  dgsl_last_error() returns a thread-local
+ *    message for the last failing call on the calling thread.
+ *  - "device pointer": memory on the operator's CUDA device, owned by the
+ *    caller (e.g. a PyTorch tensor's data_ptr()); "host pointer": ordinary
+ *    host memory owned by the caller.  The library never retains caller
+ *    pointers after a call returns unless the call says so (dgsl_submit).
+ *  - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Device-pointer calls are asynchronous on that stream
+ *    unless stated otherwise.
+ *  - Vector layout (internal order): triangles are renumbered by reverse
+ *    Cuthill-McKee and edges by (colour, RCM key).  A main-grid vector is
+ *    double[n_tri][n_phi] with triangle t at internal position t; a scalar
+ *    dual-grid field is double[n_edge][n_psi] in internal edge order; a
+ *    vector dual field is double[2][n_edge][n_psi] (x component first).
+ *    dgsl_query_maps() returns perm (internal -> natural triangle id) and
+ *    edge_perm (internal -> natural edge id).  Several right-hand sides are
+ *    stored one after another (rhs-major).
+ *  - Local DOF order: main node k of T_ref is (a/p, b/p), a + b <= p,
+ *    b-major then a.  Dual DOF order: the n_phi nodes of the left half, then
+ *    the right-half nodes off the diagonal, in the same order.
+ */
+#ifndef DGSL_H
+#define DGSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+enum {
+  DGSL_OK = 0,
+  DGSL_EINVAL = 1,      /* bad argument (NULL, size, degree out of 1..4, ...) */
+  DGSL_EMESH = 2,       /* inverted / degenerate / non-manifold / too coarse mesh */
+  DGSL_ENOMEM = 3,      /* host or device allocation failed */
+  DGSL_EBUDGET = 4,     /* request can never fit the server's memory budget */
+  DGSL_ENOTCONV = 5,    /* max_iters reached; best iterate returned */
+  DGSL_ETIMEOUT = 6,    /* a bounded device wait expired */
+  DGSL_EPENDING = 7,    /* dgsl_poll: request not finished yet */
+  DGSL_ECUDA = 8,       /* CUDA runtime error */
+  DGSL_ENODEVICE = 9    /* called a device path on a host-only operator */
+};
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* dgsl_last_error(void);
+
+/* Library version string. */
+const char* dgsl_version(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t dgsl_launch_count(void);
+
+/* ------------------------------------------------------------ mesh */
+/* Periodic triangulation (Sec. 2.1).  Host pointers, caller-owned, copied
+ * during dgsl_build_operators and never retained.
+ *   xy  : double[n_vertices][2] vertex coordinates
+ *   tri : int32[n_triangles][3] counter-clockwise vertex ids (after each
+ *         triangle's vertices are moved to their minimum image relative to
+ *         its first vertex)
+ *   period : the torus periods in x and y (> 0). */
+typedef struct {
+  int32_t n_vertices;
+  const double* xy;
+  int32_t n_triangles;
+  const int32_t* tri;
+  double period[2];
+} dgsl_mesh;
+
+typedef struct dgsl_operator dgsl_operator;
+
+enum { DGSL_STORE_F64 = 1, DGSL_STORE_F32 = 2, DGSL_STORE_BF16 = 4 };
+
+typedef struct {
+  int32_t host_only;   /* 1: build host maps and FP64 blocks only (no GPU) */
+  int32_t device;      /* CUDA device ordinal */
+  int32_t store;       /* DGSL_STORE_* mask of block copies kept on device
+                          (0 = F64|F32) */
+  int32_t factored;    /* 1: also keep the per-edge G / Mhat^{-1} blocks */
+} dgsl_build_opts;
+
+/* Builds connectivity (left/right triangles by first encounter), the RCM
+ * order, the greedy edge colouring, the geometry and, from the reference
+ * operators of Sec. 2.4, the per-edge blocks G_lj, G_rj, Mhat_j^{-1} and
+ * the assembled couplings K = G^T Mhat^{-1} G (4 blocks per triangle row).
+ * p in 1..4.  opts may be NULL (defaults).  On success *out owns all host
+ * and device storage; release it with dgsl_destroy_operator.
+ * Errors: EINVAL, EMESH (inverted, degenerate, non-manifold or a periodic
+ * mesh so coarse that two triangles share two edges), ENOMEM, ECUDA. */
+int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* opts,
+                         dgsl_operator** out);
+void dgsl_destroy_operator(dgsl_operator* op);
+
+typedef struct {
+  int32_t p, n_phi, n_psi;
+  int32_t n_tri, n_edge, n_colours;
+  int64_t n_dof;          /* n_tri * n_phi */
+  int64_t n_dual;         /* n_edge * n_psi */
+  int64_t device_bytes;   /* device memory held by the operator */
+  int32_t host_only;
+  int32_t device;
+} dgsl_info;
+int dgsl_operator_info(const dgsl_operator* op, dgsl_info* out);
+
+/* Host copies of the index maps (caller-allocated host arrays; any member
+ * may be NULL to skip it).  Natural numbering unless noted.
+ *   edge_vtx [n_edge][2]  (X1, X2): counter-clockwise in the left triangle
+ *   lr       [n_edge][2]  left, right triangle
+ *   loc      [n_edge][2]  local edge index (0..2) in left, right
+ *   shift    [n_edge][2]  periods added to the right triangle's frame
+ *   tri_edge [n_tri][3]   edge of local edge k = (v_k, v_{k+1 mod 3})
+ *   perm     [n_tri]      internal -> natural triangle
+ *   edge_perm[n_edge]     internal -> natural edge
+ *   colour   [n_edge]     colour of each natural edge
+ *   colour_offsets [n_colours + 1] internal edge ranges per colour */
+typedef struct {
+  int32_t* edge_vtx;
+  int32_t* lr;
+  uint8_t* loc;
+  int8_t* shift;
+  int32_t* tri_edge;
+  int32_t* perm;
+  int32_t* edge_perm;
+  uint8_t* colour;
+  int32_t* colour_offsets;
+} dgsl_maps;
+int dgsl_query_maps(const dgsl_operator* op, dgsl_maps* out);
+
+enum { DGSL_MAIN = 0, DGSL_DUAL = 1 };
+/* Physical coordinates of the nodal DOFs, host double[n][2] in internal
+ * order: grid DGSL_MAIN -> n_tri*n_phi nodes (each triangle in its own
+ * unwrapped frame); DGSL_DUAL -> n_edge*n_psi nodes (in the left triangle's
+ * frame). */
+int dgsl_node_coords(const dgsl_operator* op, int grid, double* xy);
+
+/* Host FP64 copies of the blocks, internal edge order (any may be NULL):
+ *   G    [n_edge][2 side][2 comp][n_phi m][n_phi k] = Q_{s,j}[L_s(m), k, comp]
+ *        (eq. ad5.2 restricted to the dual nodes of side s)
+ *   Minv [n_edge][n_psi][n_psi]   Mhat_j^{-1}
+ *   Mref [n_phi][n_phi]           Mbar_ref (eq. MassMatrixM)
+ *   area [n_tri]                  A_i = 2|T_i| (internal order) */
+int dgsl_query_blocks(const dgsl_operator* op, double* G, double* Minv, double* Mref,
+                      double* area);
+
+/* ------------------------------------------------------------ applies */
+/* Forms of the Schur / Helmholtz matvec. */
+enum {
+  DGSL_FORM_ASSEMBLED = 0,  /* stored couplings K (4 blocks per triangle row) */
+  DGSL_FORM_FACTORED = 1    /* stored G, Mhat^{-1} per edge, edge-coloured phases */
+};
+
+/* y = dt^2 G^T Mhat^{-1} G x  (eq. pressure_final, PSD sign).
+ * x, y: device double[n_rhs][n_dof], internal order, may not alias.
+ * form: DGSL_FORM_*; FACTORED needs opts.factored at build time. */
+int dgsl_apply_schur(const dgsl_operator* op, int form, double dt, const double* x, double* y,
+                     int n_rhs, void* stream);
+
+/* Same in FP32 (FP32 blocks and vectors, FP32 accumulation). */
+int dgsl_apply_schur_f32(const dgsl_operator* op, float dt, const float* x, float* y, int n_rhs,
+                         void* stream);
+
+/* y = (Mbar + nu_dt G^T Mhat^{-1} G) x  (eq. ad5 with lambda*dt = nu_dt). */
+int dgsl_apply_helmholtz(const dgsl_operator* op, double nu_dt, const double* x, double* y,
+                         int n_rhs, void* stream);
+
+/* b_i = sum_{j in S_i} U_ij^T vhat_j (eq. d2m times Mbar_i; eq. u), for
+ * n_rhs scalar dual fields vhat [n_rhs][n_edge][n_psi] -> b [n_rhs][n_dof]. */
+int dgsl_project_d2m_rhs(const dgsl_operator* op, const double* vhat, double* b, int n_rhs,
+                         void* stream);
+
+/* vhat_j = Mhat_j^{-1} (U_lj vbar_l + U_rj vbar_r) (eq. m2d), for n_rhs scalar
+ * main fields vbar [n_rhs][n_dof] -> vhat [n_rhs][n_edge][n_psi]. */
+int dgsl_project_m2d(const dgsl_operator* op, const double* vbar, double* vhat, int n_rhs,
+                     void* stream);
+
+/* y = G^T vhat = -sum_j D_ij vhat_j (eqs. ins.1 / D), vhat a vector dual field
+ * [n_rhs][2][n_edge][n_psi] -> y [n_rhs][n_dof]. */
+int dgsl_apply_div(const dgsl_operator* op, const double* vhat, double* y, int n_rhs,
+                   void* stream);
+
+/* ------------------------------------------------------------ solves */
+enum { DGSL_SCHUR = 0, DGSL_HELMHOLTZ = 1 };
+enum {
+  DGSL_PREC_F64 = 0,       /* FP64 CG on FP64 blocks */
+  DGSL_PREC_F32_IR = 1,    /* FP32 inner CG, FP64 iterative refinement */
+  DGSL_PREC_BF16_IR = 2    /* BF16-stored blocks, FP32 inner CG, FP64 refinement */
+};
+
+typedef struct {
+  double tol;            /* target ||b - A x||_2 / ||b||_2 (default 1e-10) */
+  int32_t max_iters;     /* cap on CG iterations, all refinements (default 200000) */
+  int32_t precision;     /* DGSL_PREC_* */
+  int32_t use_x0;        /* 1: x holds the initial guess */
+  double inner_tol;      /* inner CG relative tolerance under refinement (1e-4) */
+  int32_t max_refine;    /* refinement steps cap (default 30) */
+  int32_t form;          /* DGSL_FORM_* of the FP64 operator */
+} dgsl_solve_opts;
+
+typedef struct {
+  int32_t status;        /* DGSL_OK or DGSL_ENOTCONV / DGSL_ETIMEOUT */
+  int32_t iters;         /* CG iterations (sum over refinements) */
+  int32_t refinements;   /* outer FP64 refinement steps */
+  int32_t cg_launches;   /* persistent CG launches (one per refinement step) */
+  double relres;         /* final ||b - A x|| / ||b|| with the FP64 operator */
+  double cg_kernel_ms;   /* device time of those launches (CUDA events on the
+                            solve's stream) */
+  int32_t grid;          /* CTAs of the persistent CG launches */
+  int32_t pad;
+} dgsl_solve_info;
+
+/* Solves A x = b for kind DGSL_SCHUR (A = S with dt = coef) or
+ * DGSL_HELMHOLTZ (A = H with nu_dt = coef) by matrix-free CG (Sec. 2.3,
+ * after eq. pressure_final), with x0 = 0 unless use_x0, stopping at the
+ * relative residual tol.  For DGSL_SCHUR, b is projected to mean zero and x
+ * is returned with sum(x) = 0 (coefficient space).  b, x: device
+ * double[n_rhs][n_dof] in internal order; info: host array [n_rhs] or NULL.
+ * Blocks the calling thread until the solves finish (it reads the status
+ * words back).  Returns DGSL_ENOTCONV (x = last iterate) if any right-hand
+ * side missed tol within max_iters. */
+int dgsl_cg_solve(const dgsl_operator* op, int kind, double coef, const double* b, double* x,
+                  int n_rhs, const dgsl_solve_opts* opts, dgsl_solve_info* info, void* stream);
+
+void dgsl_default_solve_opts(dgsl_solve_opts* opts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGSL_H */

@@ -74,15 +74,63 @@ def _sub_triangles(conn: Connectivity, idx):
     return l, r, Pl, Pr, Tl, Tr, (X1l, X2l), (X1r, X2r)
 
 
-def assemble(xy, tri, period, p, chunk=1024) -> Blocks:
-    conn = connectivity(xy, tri, period)
+def edge_blocks(conn: Connectivity, p, idx):
+    """Mhat, D, Q, U, normal, length for the edges idx (physical quadrature)."""
     nphi, npsi = B.n_phi(p), B.n_psi(p)
     L, R = B.dual_maps(p)
     nq = p + 2
     rpts, rw = B.duffy_rule(nq)           # on T_ref, sum w = 1/2
     tau, wt = B.gauss_legendre(nq)        # on [0, 1]
+    ne_ = len(idx)
+    Mhat = np.zeros((ne_, npsi, npsi))
+    D = np.zeros((ne_, 2, nphi, npsi, 2))
+    Q = np.zeros((ne_, 2, npsi, nphi, 2))
+    U = np.zeros((ne_, 2, npsi, nphi))
+    l, r, Pl, Pr, Tl, Tr, (X1l, X2l), (X1r, X2r) = _sub_triangles(conn, idx)
+    d = X2l - X1l
+    glen = np.hypot(d[:, 0], d[:, 1])
+    n = np.stack([d[:, 1], -d[:, 0]], 1) / glen[:, None]
+    for side, (Pi, Tsub, Xa, Xb, tri_id, perm) in enumerate(
+            [(Pl, Tl, X1l, X2l, l, L), (Pr, Tr, X1r, X2r, r, R)]):
+        sg = sigma(tri_id, l, r)                                # +1 / -1
+        # volume part on the physical sub-triangle
+        s1 = Tsub[:, 1] - Tsub[:, 0]
+        s2 = Tsub[:, 2] - Tsub[:, 0]
+        a_sub = s1[:, 0] * s2[:, 1] - s1[:, 1] * s2[:, 0]        # A_ij
+        xs = B.triangle_points(Tsub, rpts)                      # [E, q, 2]
+        ws = rw[None, :] * a_sub[:, None]
+        psi_loc = B.eval_phi(p, B.pull_back(Tsub, xs))          # [E, q, Nphi]
+        psi = np.zeros(psi_loc.shape[:2] + (npsi,))
+        psi[..., perm] = psi_loc
+        xi = B.pull_back(Pi, xs)
+        ph = B.eval_phi(p, xi)                                  # [E, q, Nphi]
+        gref = B.eval_grad_phi(p, xi)                           # [E, q, Nphi, 2]
+        J = np.stack([Pi[:, 1] - Pi[:, 0], Pi[:, 2] - Pi[:, 0]], axis=-1)  # dx/dxi
+        # grad_x phi = J^{-T} grad_xi phi
+        JT = np.swapaxes(J, -1, -2)
+        gx = np.linalg.solve(JT[:, None, None, :, :], gref[..., None])[..., 0]
+        # edge part on the physical segment, parametrised X1 -> X2
+        xe = Xa[:, None, :] + tau[None, :, None] * (Xb - Xa)[:, None, :]
+        we = wt[None, :] * glen[:, None]
+        pe_loc = B.eval_phi(p, B.pull_back(Tsub, xe))
+        pe = np.zeros(pe_loc.shape[:2] + (npsi,))
+        pe[..., perm] = pe_loc
+        phe = B.eval_phi(p, B.pull_back(Pi, xe))
+        sn = sg[:, None] * n                                    # sigma_ij n_j
+        Mhat += np.einsum("eq,eqk,eql->ekl", ws, psi, psi)
+        line = np.einsum("eq,eqk,eql->ekl", we, phe, pe)        # phi_k psi_l
+        vol = np.einsum("eq,eqkc,eql->eklc", ws, gx, psi)       # grad phi_k psi_l
+        D[:, side] = line[..., None] * sn[:, None, None, :] - vol
+        lineq = np.einsum("eq,eqk,eql->ekl", we, pe, phe)       # psi_k phi_l
+        volq = np.einsum("eq,eqk,eqlc->eklc", ws, psi, gx)      # psi_k grad phi_l
+        Q[:, side] = volq - lineq[..., None] * sn[:, None, None, :]
+        U[:, side] = np.einsum("eq,eqk,eql->ekl", ws, psi, ph)
+    return Mhat, D, Q, U, n, glen
 
-    # --- main mass matrices, eq. Mi, physical quadrature on T_i
+
+def main_mass(conn: Connectivity, p):
+    """Mbar_i (eq. Mi) by physical quadrature on T_i, and A_i = 2|T_i|."""
+    rpts, rw = B.duffy_rule(p + 2)
     P = conn.tri_xy
     e1 = P[:, 1] - P[:, 0]
     e2 = P[:, 2] - P[:, 0]
@@ -90,8 +138,13 @@ def assemble(xy, tri, period, p, chunk=1024) -> Blocks:
     xq = B.triangle_points(P, rpts)                     # [Ne, q, 2]
     phi = B.eval_phi(p, B.pull_back(P, xq))             # [Ne, q, Nphi]
     wq = rw[None, :] * area2[:, None]                   # physical weights
-    Mbar = np.einsum("eq,eqk,eql->ekl", wq, phi, phi)
+    return np.einsum("eq,eqk,eql->ekl", wq, phi, phi), area2
 
+
+def assemble(xy, tri, period, p, chunk=1024, conn=None) -> Blocks:
+    conn = conn if conn is not None else connectivity(xy, tri, period)
+    nphi, npsi = B.n_phi(p), B.n_psi(p)
+    Mbar, area2 = main_mass(conn, p)
     nd = conn.n_edge
     Mhat = np.zeros((nd, npsi, npsi))
     D = np.zeros((nd, 2, nphi, npsi, 2))
@@ -101,45 +154,5 @@ def assemble(xy, tri, period, p, chunk=1024) -> Blocks:
     length = np.zeros(nd)
     for s0 in range(0, nd, chunk):
         idx = np.arange(s0, min(nd, s0 + chunk))
-        l, r, Pl, Pr, Tl, Tr, (X1l, X2l), (X1r, X2r) = _sub_triangles(conn, idx)
-        d = X2l - X1l
-        glen = np.hypot(d[:, 0], d[:, 1])
-        n = np.stack([d[:, 1], -d[:, 0]], 1) / glen[:, None]
-        normal[idx] = n
-        length[idx] = glen
-        for side, (Pi, Tsub, Xa, Xb, tri_id, perm) in enumerate(
-                [(Pl, Tl, X1l, X2l, l, L), (Pr, Tr, X1r, X2r, r, R)]):
-            sg = sigma(tri_id, l, r)                                # +1 / -1
-            # volume part on the physical sub-triangle
-            s1 = Tsub[:, 1] - Tsub[:, 0]
-            s2 = Tsub[:, 2] - Tsub[:, 0]
-            a_sub = s1[:, 0] * s2[:, 1] - s1[:, 1] * s2[:, 0]        # A_ij
-            xs = B.triangle_points(Tsub, rpts)                      # [E, q, 2]
-            ws = rw[None, :] * a_sub[:, None]
-            psi_loc = B.eval_phi(p, B.pull_back(Tsub, xs))          # [E, q, Nphi]
-            psi = np.zeros(psi_loc.shape[:2] + (npsi,))
-            psi[..., perm] = psi_loc
-            xi = B.pull_back(Pi, xs)
-            ph = B.eval_phi(p, xi)                                  # [E, q, Nphi]
-            gref = B.eval_grad_phi(p, xi)                           # [E, q, Nphi, 2]
-            J = np.stack([Pi[:, 1] - Pi[:, 0], Pi[:, 2] - Pi[:, 0]], axis=-1)  # dx/dxi
-            # grad_x phi = J^{-T} grad_xi phi
-            JT = np.swapaxes(J, -1, -2)
-            gx = np.linalg.solve(JT[:, None, None, :, :], gref[..., None])[..., 0]
-            # edge part on the physical segment, parametrised X1 -> X2
-            xe = Xa[:, None, :] + tau[None, :, None] * (Xb - Xa)[:, None, :]
-            we = wt[None, :] * glen[:, None]
-            pe_loc = B.eval_phi(p, B.pull_back(Tsub, xe))
-            pe = np.zeros(pe_loc.shape[:2] + (npsi,))
-            pe[..., perm] = pe_loc
-            phe = B.eval_phi(p, B.pull_back(Pi, xe))
-            sn = sg[:, None] * n                                    # sigma_ij n_j
-            Mhat[idx] += np.einsum("eq,eqk,eql->ekl", ws, psi, psi)
-            line = np.einsum("eq,eqk,eql->ekl", we, phe, pe)        # phi_k psi_l
-            vol = np.einsum("eq,eqkc,eql->eklc", ws, gx, psi)       # grad phi_k psi_l
-            D[idx, side] = line[..., None] * sn[:, None, None, :] - vol
-            lineq = np.einsum("eq,eqk,eql->ekl", we, pe, phe)       # psi_k phi_l
-            volq = np.einsum("eq,eqk,eqlc->eklc", ws, psi, gx)      # psi_k grad phi_l
-            Q[idx, side] = volq - lineq[..., None] * sn[:, None, None, :]
-            U[idx, side] = np.einsum("eq,eqk,eql->ekl", ws, psi, ph)
+        Mhat[idx], D[idx], Q[idx], U[idx], normal[idx], length[idx] = edge_blocks(conn, p, idx)
     return Blocks(p, conn, area2, Mbar, Mhat, D, Q, U, normal, length)

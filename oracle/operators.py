@@ -211,3 +211,33 @@ def cg(apply, b, tol=1e-12, maxit=100000, mean_zero=False):
         rr = rr_new
         it += 1
     return x, it, np.sqrt(rr) / bn
+
+
+def sampled_rows(conn, p, x, tri_ids, coefK, coefM=0.0):
+    """Rows of (coefM Mbar + coefK G^T Mhat^{-1} G) x for the triangles tri_ids
+    only (natural numbering), assembling just the edges they touch.  Used to
+    check full-size results one output block at a time."""
+    from .assemble import edge_blocks, main_mass
+    from . import basis as B
+    nphi = B.n_phi(p)
+    tri_ids = np.asarray(tri_ids)
+    edges = np.unique(conn.tri_edge[tri_ids].ravel())
+    Mhat, D, Q, U, n, glen = edge_blocks(conn, p, edges)
+    Lc = np.linalg.cholesky(Mhat)
+    X = x.reshape(-1, nphi)
+    lr = conn.lr[edges]
+    t = np.stack([np.einsum("eklc,el->cek", Q[:, s], X[lr[:, s]]) for s in range(2)]).sum(0)
+    g = np.stack([np.linalg.solve(np.swapaxes(Lc, -1, -2),
+                                  np.linalg.solve(Lc, t[c][..., None]))[..., 0] for c in range(2)])
+    pos = {int(e): k for k, e in enumerate(edges)}
+    out = np.zeros((len(tri_ids), nphi))
+    for a, i in enumerate(tri_ids):
+        for e in conn.tri_edge[i]:
+            k = pos[int(e)]
+            s = 0 if conn.lr[e, 0] == i else 1
+            out[a] += coefK * np.einsum("klc,ck->l", Q[k, s], g[:, k])
+    if coefM != 0.0:
+        sub = type(conn)(len(tri_ids), 0, None, None, None, None, None, conn.tri_xy[tri_ids])
+        Mb, _ = main_mass(sub, p)
+        out += coefM * np.einsum("akl,al->ak", Mb, X[tri_ids])
+    return out

@@ -1,0 +1,549 @@
+// C-ABI of dgsl: operator build and upload, applies, and the CG solve driver
+// (FP64 iterative refinement around the persistent CG kernels).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host.h"
+#include "kernels.h"
+
+using namespace dgsl;
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define DGSL_CUDA(expr)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess) throw Error(DGSL_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+uint16_t f32_to_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;  // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+}  // namespace
+
+struct dgsl_operator {
+  HostMesh hm;
+  RefOps ro;
+  HostBlocks hb;      // kept for host queries (host_only or factored builds)
+  bool have_blocks = false;
+  int host_only = 0;
+  DevOp d;
+  std::vector<void*> allocs;
+  int64_t device_bytes = 0;
+  std::mutex mu;
+  // solve workspace (grown on demand)
+  struct Work {
+    int64_t n = 0;
+    double* r64 = nullptr;
+    double* d64 = nullptr;
+    float* r32 = nullptr;
+    float* d32 = nullptr;
+    void* p = nullptr;   // 2n doubles (covers 2n floats)
+    void* q = nullptr;   // n doubles
+    double* part = nullptr;
+    double* part2 = nullptr;
+    GridBarrier* bar = nullptr;
+    CGResult* res = nullptr;
+    double* h_part = nullptr;   // pinned
+    CGResult* h_res = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int max_parts = 0;
+  } w;
+
+  template <class T>
+  T* dalloc(size_t count) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) throw Error(DGSL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(p);
+    device_bytes += (int64_t)bytes;
+    return static_cast<T*>(p);
+  }
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    T* p = dalloc<T>(v.size());
+    if (!v.empty()) DGSL_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  ~dgsl_operator() {
+    if (!host_only) {
+      cudaSetDevice(d.device);
+      for (void* p : allocs) cudaFree(p);
+      if (w.h_part) cudaFreeHost(w.h_part);
+      if (w.h_res) cudaFreeHost(w.h_res);
+      if (w.ev0) cudaEventDestroy(w.ev0);
+      if (w.ev1) cudaEventDestroy(w.ev1);
+    }
+  }
+  void ensure_work() {
+    if (w.n == d.n && w.r64) return;
+    w.n = d.n;
+    w.max_parts = cg_max_blocks(d, 0);
+    w.r64 = dalloc<double>(d.n);
+    w.d64 = dalloc<double>(d.n);
+    w.r32 = dalloc<float>(d.n);
+    w.d32 = dalloc<float>(d.n);
+    w.p = dalloc<double>(2 * d.n);
+    w.q = dalloc<double>(d.n);
+    w.part = dalloc<double>(4 * (size_t)w.max_parts);
+    w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
+    w.bar = dalloc<GridBarrier>(1);
+    w.res = dalloc<CGResult>(1);
+    DGSL_CUDA(cudaMallocHost(&w.h_part, 2 * (size_t)w.max_parts * sizeof(double)));
+    DGSL_CUDA(cudaMallocHost(&w.h_res, sizeof(CGResult)));
+    DGSL_CUDA(cudaEventCreate(&w.ev0));
+    DGSL_CUDA(cudaEventCreate(&w.ev1));
+  }
+};
+
+namespace {
+
+template <class T>
+std::vector<T> to_ell(const HostBlocks& hb, int64_t n, T (*cvt)(double)) {
+  const int N = hb.nphi, NC = 4 * N;
+  const int VEC = 16 / (int)sizeof(T);
+  const int NG = (NC + VEC - 1) / VEC;
+  std::vector<T> out((size_t)NG * n * VEC, cvt(0.0));
+  for (int i = 0; i < hb.ne; ++i)
+    for (int k = 0; k < N; ++k) {
+      const int64_t row = (int64_t)i * N + k;
+      for (int c = 0; c < NC; ++c) {
+        const int b = c / N, kk = c % N;
+        double v = b == 0 ? hb.Kd[((size_t)i * N + k) * N + kk] : hb.Ko[(((size_t)i * 3 + (b - 1)) * N + k) * N + kk];
+        out[((size_t)(c / VEC) * n + row) * VEC + c % VEC] = cvt(v);
+      }
+    }
+  return out;
+}
+double cvt_d(double v) { return v; }
+float cvt_f(double v) { return (float)v; }
+uint16_t cvt_b(double v) { return f32_to_bf16_bits((float)v); }
+
+const dgsl_operator* check_dev(const dgsl_operator* op) {
+  if (!op) throw Error(DGSL_EINVAL, "operator is NULL");
+  if (op->host_only) throw Error(DGSL_ENODEVICE, "operator was built host-only");
+  return op;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dgsl_last_error(void) { return g_last_error.c_str(); }
+const char* dgsl_version(void) { return "dgsl 0.1 (sm_103a)"; }
+uint64_t dgsl_launch_count(void) { return launch_count(); }
+
+void dgsl_default_solve_opts(dgsl_solve_opts* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->max_iters = 200000;
+  o->precision = DGSL_PREC_F64;
+  o->use_x0 = 0;
+  o->inner_tol = 1e-4;
+  o->max_refine = 30;
+  o->form = DGSL_FORM_ASSEMBLED;
+}
+
+int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* opts, dgsl_operator** out) {
+  if (!mesh || !out) return fail(DGSL_EINVAL, "mesh and out must be non-NULL");
+  *out = nullptr;
+  dgsl_build_opts o{0, 0, 0, 0};
+  if (opts) o = *opts;
+  if (o.store == 0) o.store = DGSL_STORE_F64 | DGSL_STORE_F32;
+  try {
+    auto op = std::make_unique<dgsl_operator>();
+    op->host_only = o.host_only;
+    op->ro = build_reference_operators(p);
+    op->hm = build_mesh(*mesh);
+    HostBlocks hb = build_blocks(op->hm, op->ro);
+    DevOp& d = op->d;
+    d.p = p;
+    d.nphi = op->ro.nphi;
+    d.npsi = op->ro.npsi;
+    d.ne = op->hm.ne;
+    d.nd = op->hm.nd;
+    d.ncol = op->hm.n_colours();
+    d.n = (int64_t)d.ne * d.nphi;
+    d.device = o.device;
+    if (d.ncol > 8) throw Error(DGSL_EMESH, "edge colouring needs more than 8 colours");
+    for (int c = 0; c <= d.ncol; ++c) d.colour_offsets[c] = op->hm.colour_offsets[c];
+    if (!o.host_only) {
+      DGSL_CUDA(cudaSetDevice(o.device));
+      upload_dual_tables(o.device);
+      std::vector<int32_t> cols((size_t)4 * d.ne);
+      for (int i = 0; i < d.ne; ++i) {
+        cols[i] = i;
+        for (int b = 1; b < 4; ++b) cols[(size_t)b * d.ne + i] = hb.nbr[(size_t)i * 3 + b - 1];
+      }
+      d.cols = op->upload(cols);
+      d.area = op->upload(hb.area);
+      d.Mref = op->upload(op->ro.Mref);
+      if (o.store & DGSL_STORE_F64) d.K64 = op->upload(to_ell<double>(hb, d.n, cvt_d));
+      if (o.store & DGSL_STORE_F32) d.K32 = op->upload(to_ell<float>(hb, d.n, cvt_f));
+      if (o.store & DGSL_STORE_BF16) d.K16 = op->upload(to_ell<uint16_t>(hb, d.n, cvt_b));
+      if (o.factored) {
+        d.G = op->upload(hb.G);
+        d.Minv = op->upload(hb.Minv);
+        d.Uloc = op->upload(hb.Uloc);
+        d.elr = op->upload(hb.elr);
+        std::vector<int32_t> tedge((size_t)3 * d.ne, -1);
+        for (int e = 0; e < d.nd; ++e)
+          for (int s = 0; s < 2; ++s) tedge[(size_t)hb.elr[2 * e + s] * 3 + hb.eloc[2 * e + s]] = 2 * e + s;
+        d.tedge = op->upload(tedge);
+      }
+      DGSL_CUDA(cudaDeviceSynchronize());
+    }
+    if (o.host_only || o.factored) {
+      op->hb = std::move(hb);
+      op->have_blocks = true;
+    }
+    *out = op.release();
+    return DGSL_OK;
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(DGSL_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(DGSL_EINVAL, e.what());
+  }
+}
+
+void dgsl_destroy_operator(dgsl_operator* op) { delete op; }
+
+int dgsl_operator_info(const dgsl_operator* op, dgsl_info* out) {
+  if (!op || !out) return fail(DGSL_EINVAL, "NULL argument");
+  out->p = op->d.p;
+  out->n_phi = op->d.nphi;
+  out->n_psi = op->d.npsi;
+  out->n_tri = op->d.ne;
+  out->n_edge = op->d.nd;
+  out->n_colours = op->d.ncol;
+  out->n_dof = op->d.n;
+  out->n_dual = (int64_t)op->d.nd * op->d.npsi;
+  out->device_bytes = op->device_bytes;
+  out->host_only = op->host_only;
+  out->device = op->d.device;
+  return DGSL_OK;
+}
+
+int dgsl_query_maps(const dgsl_operator* op, dgsl_maps* m) {
+  if (!op || !m) return fail(DGSL_EINVAL, "NULL argument");
+  const HostMesh& h = op->hm;
+  auto cp = [](void* dst, const void* src, size_t bytes) {
+    if (dst) std::memcpy(dst, src, bytes);
+  };
+  cp(m->edge_vtx, h.edge_vtx.data(), h.edge_vtx.size() * 4);
+  cp(m->lr, h.lr.data(), h.lr.size() * 4);
+  cp(m->loc, h.loc.data(), h.loc.size());
+  cp(m->shift, h.shift.data(), h.shift.size());
+  cp(m->tri_edge, h.tri_edge.data(), h.tri_edge.size() * 4);
+  cp(m->perm, h.perm.data(), h.perm.size() * 4);
+  cp(m->edge_perm, h.edge_perm.data(), h.edge_perm.size() * 4);
+  cp(m->colour, h.colour.data(), h.colour.size());
+  cp(m->colour_offsets, h.colour_offsets.data(), h.colour_offsets.size() * 4);
+  return DGSL_OK;
+}
+
+int dgsl_node_coords(const dgsl_operator* op, int grid, double* xy) {
+  if (!op || !xy) return fail(DGSL_EINVAL, "NULL argument");
+  if (grid != DGSL_MAIN && grid != DGSL_DUAL) return fail(DGSL_EINVAL, "grid must be DGSL_MAIN or DGSL_DUAL");
+  node_coords(op->hm, op->ro, grid, xy);
+  return DGSL_OK;
+}
+
+int dgsl_query_blocks(const dgsl_operator* op, double* G, double* Minv, double* Mref, double* area) {
+  if (!op) return fail(DGSL_EINVAL, "NULL operator");
+  if ((G || Minv) && !op->have_blocks) return fail(DGSL_EINVAL, "blocks kept only for host_only or factored builds");
+  if (G) std::memcpy(G, op->hb.G.data(), op->hb.G.size() * sizeof(double));
+  if (Minv) std::memcpy(Minv, op->hb.Minv.data(), op->hb.Minv.size() * sizeof(double));
+  if (Mref) std::memcpy(Mref, op->ro.Mref.data(), op->ro.Mref.size() * sizeof(double));
+  if (area) {
+    for (int i = 0; i < op->hm.ne; ++i) {
+      const double* P = &op->hm.txy[(size_t)op->hm.perm[i] * 6];
+      area[i] = (P[2] - P[0]) * (P[5] - P[1]) - (P[3] - P[1]) * (P[4] - P[0]);
+    }
+  }
+  return DGSL_OK;
+}
+
+#define DGSL_TRY(body)                                  \
+  try {                                                 \
+    body;                                               \
+  } catch (const Error& e) {                            \
+    return fail(e.code, e.what());                      \
+  } catch (const std::exception& e) {                   \
+    return fail(DGSL_EINVAL, e.what());                 \
+  }
+
+static int check_vec_args(const void* a, const void* b, int n_rhs) {
+  if (!a || !b) return fail(DGSL_EINVAL, "vector pointers must be non-NULL");
+  if (n_rhs < 1) return fail(DGSL_EINVAL, "n_rhs must be >= 1");
+  return DGSL_OK;
+}
+
+int dgsl_apply_schur(const dgsl_operator* op, int form, double dt, const double* x, double* y, int n_rhs,
+                     void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(x, y, n_rhs)) return e;
+    if (form != DGSL_FORM_ASSEMBLED && form != DGSL_FORM_FACTORED) return fail(DGSL_EINVAL, "unknown form");
+    if (form == DGSL_FORM_FACTORED && !op->d.G) return fail(DGSL_EINVAL, "factored form needs opts.factored");
+    if (form == DGSL_FORM_ASSEMBLED && !op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings not stored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < n_rhs; ++k) {
+      const double* xk = x + (size_t)k * op->d.n;
+      double* yk = y + (size_t)k * op->d.n;
+      if (form == DGSL_FORM_ASSEMBLED) DGSL_CUDA(launch_apply_assembled_f64(op->d, dt * dt, 0.0, xk, yk, s));
+      else DGSL_CUDA(launch_apply_factored_f64(op->d, dt * dt, 0.0, xk, yk, s));
+    }
+    return DGSL_OK;
+  });
+}
+
+int dgsl_apply_schur_f32(const dgsl_operator* op, float dt, const float* x, float* y, int n_rhs, void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(x, y, n_rhs)) return e;
+    if (!op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_apply_assembled_f32(op->d, dt * dt, x + (size_t)k * op->d.n, y + (size_t)k * op->d.n,
+                                           (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+int dgsl_apply_helmholtz(const dgsl_operator* op, double nu_dt, const double* x, double* y, int n_rhs,
+                         void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(x, y, n_rhs)) return e;
+    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings not stored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_apply_assembled_f64(op->d, nu_dt, 1.0, x + (size_t)k * op->d.n, y + (size_t)k * op->d.n,
+                                           (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+int dgsl_project_d2m_rhs(const dgsl_operator* op, const double* vhat, double* b, int n_rhs, void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(vhat, b, n_rhs)) return e;
+    if (!op->d.Uloc) return fail(DGSL_EINVAL, "projections need opts.factored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    const size_t nv = (size_t)op->d.nd * op->d.npsi;
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_d2m_rhs(op->d, vhat + k * nv, b + (size_t)k * op->d.n, (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+int dgsl_project_m2d(const dgsl_operator* op, const double* vbar, double* vhat, int n_rhs, void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(vbar, vhat, n_rhs)) return e;
+    if (!op->d.Uloc) return fail(DGSL_EINVAL, "projections need opts.factored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    const size_t nv = (size_t)op->d.nd * op->d.npsi;
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_m2d(op->d, vbar + (size_t)k * op->d.n, vhat + k * nv, (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+int dgsl_apply_div(const dgsl_operator* op, const double* vhat, double* y, int n_rhs, void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(vhat, y, n_rhs)) return e;
+    if (!op->d.G) return fail(DGSL_EINVAL, "divergence needs opts.factored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    const size_t nv = (size_t)2 * op->d.nd * op->d.npsi;
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_div(op->d, vhat + k * nv, y + (size_t)k * op->d.n, (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ solve driver
+namespace {
+
+struct Sums {
+  double s, ss;
+};
+
+Sums read_sums(dgsl_operator* op, const double* dev_part, int nparts, cudaStream_t s) {
+  DGSL_CUDA(cudaMemcpyAsync(op->w.h_part, dev_part, 2 * (size_t)nparts * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DGSL_CUDA(cudaStreamSynchronize(s));
+  Sums r{0.0, 0.0};
+  for (int j = 0; j < nparts; ++j) {
+    r.s += op->w.h_part[2 * j];
+    r.ss += op->w.h_part[2 * j + 1];
+  }
+  return r;
+}
+
+// One right-hand side.  Outer loop: r = b - A x in FP64 (assembled FP64
+// couplings); inner: CG on A d = r in FP64 (PREC_F64) or on the FP32 / BF16
+// couplings with FP32 vectors; x += d in FP64.
+int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double* x, const dgsl_solve_opts& o,
+              dgsl_solve_info* info, cudaStream_t s) {
+  DevOp& d = op->d;
+  auto& w = op->w;
+  const int64_t n = d.n;
+  const int mean_zero = kind == DGSL_SCHUR ? 1 : 0;
+  const double coefK = kind == DGSL_SCHUR ? coef * coef : coef;
+  const double coefM = kind == DGSL_SCHUR ? 0.0 : 1.0;
+  const uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
+  int nparts = 0;
+  DGSL_CUDA(launch_sum2(b, n, w.part2, w.max_parts, &nparts, s));
+  Sums sb = read_sums(op, w.part2, nparts, s);
+  const double b_mean = mean_zero ? sb.s / (double)n : 0.0;
+  double bnorm2 = mean_zero ? std::max(0.0, sb.ss - (double)n * b_mean * b_mean) : sb.ss;
+  if (!o.use_x0) DGSL_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  int iters = 0, refinements = 0, status = DGSL_OK, launches = 0, grid_used = 0;
+  double kernel_ms = 0.0;
+  double relres = 0.0, best = INFINITY;
+  int stall = 0;
+  CGWork cw;
+  cw.p = w.p;
+  cw.q = w.q;
+  cw.part = w.part;
+  cw.bar = w.bar;
+  cw.res = w.res;
+  cw.max_parts = w.max_parts;
+  for (;;) {
+    DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, w.r64, w.part2, w.max_parts, &nparts, s));
+    Sums sr = read_sums(op, w.part2, nparts, s);
+    // the exact projection keeps sum(r) at rounding level; the norm uses all of r
+    const double rnorm = std::sqrt(sr.ss);
+    bnorm2 = bnorm2 > 0.0 ? bnorm2 : 0.0;
+    const double bnorm = std::sqrt(bnorm2);
+    relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (bnorm == 0.0 || relres <= o.tol) break;
+    if (iters >= o.max_iters || refinements >= o.max_refine) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+    if (relres < 0.5 * best) {
+      best = relres;
+      stall = 0;
+    } else if (++stall >= 3) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+    const int budget = o.max_iters - iters;
+    // aim the inner solve a little below what the outer target still needs
+    const double need = 0.5 * o.tol / relres;
+    int grid = 0;
+    DGSL_CUDA(cudaEventRecord(w.ev0, s));
+    if (o.precision == DGSL_PREC_F64) {
+      const double stop_rel = std::max(need, 1e-15);
+      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, w.d64, w.r64, stop_rel, budget, cw, timeout_ns, s, &grid));
+    } else {
+      const int bf16 = o.precision == DGSL_PREC_BF16_IR;
+      const double stop_rel = std::min(1.0, std::max(o.inner_tol, need));
+      DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
+      DGSL_CUDA(launch_cg_f32(d, bf16, (float)coefK, (float)coefM, mean_zero, w.d32, w.r32, stop_rel, budget, cw,
+                              timeout_ns, s, &grid));
+    }
+    DGSL_CUDA(cudaEventRecord(w.ev1, s));
+    DGSL_CUDA(cudaMemcpyAsync(w.h_res, w.res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    const CGResult cr = *w.h_res;
+    {
+      float ms = 0.f;
+      DGSL_CUDA(cudaEventElapsedTime(&ms, w.ev0, w.ev1));
+      kernel_ms += ms;
+      ++launches;
+      grid_used = grid;
+    }
+    if (cr.status != 0) {
+      status = DGSL_ETIMEOUT;
+      break;
+    }
+    iters += cr.iters;
+    ++refinements;
+    if (o.precision == DGSL_PREC_F64) {
+      DGSL_CUDA(launch_axpy_f64(1.0, w.d64, x, n, s));
+    } else {
+      DGSL_CUDA(launch_axpy_f32_to_f64(rnorm, w.d32, x, n, s));
+    }
+    if (cr.iters == 0) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+  }
+  if (mean_zero) {
+    DGSL_CUDA(launch_sum2(x, n, w.part2, w.max_parts, &nparts, s));
+    DGSL_CUDA(launch_sum_to_first(w.part2, nparts, s));
+    DGSL_CUDA(launch_remove_mean_f64(x, w.part2, n, s));
+  }
+  DGSL_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->refinements = refinements;
+    info->cg_launches = launches;
+    info->relres = relres;
+    info->cg_kernel_ms = kernel_ms;
+    info->grid = grid_used;
+    info->pad = 0;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, const double* b, double* x, int n_rhs,
+                             const dgsl_solve_opts* opts, dgsl_solve_info* info, void* stream) {
+  DGSL_TRY({
+    check_dev(cop);
+    if (int e = check_vec_args(b, x, n_rhs)) return e;
+    if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
+    if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
+    dgsl_solve_opts o;
+    dgsl_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
+    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
+    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_work();
+    int worst = DGSL_OK;
+    for (int k = 0; k < n_rhs; ++k) {
+      int st = solve_one(op, kind, coef, b + (size_t)k * op->d.n, x + (size_t)k * op->d.n, o, info ? info + k : nullptr,
+                         (cudaStream_t)stream);
+      if (st != DGSL_OK && worst == DGSL_OK) worst = st;
+    }
+    if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";
+    return worst;
+  });
+}

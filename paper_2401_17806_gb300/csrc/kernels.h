@@ -1,0 +1,100 @@
+// Device-side operator layout and kernel launchers of dgsl (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kcommon.cuh"
+
+namespace dgsl {
+
+// Device copy of one operator.  All arrays are in internal order.
+//
+// Assembled couplings K = G^T Mhat^{-1} G: for triangle row i and column
+// slot b (b = 0: i itself, b = 1..3: neighbour across local edge b-1) the
+// block K_b(i) is N_phi x N_phi.  Element (row = i*N_phi + k, c = b*N_phi + kk)
+// with c in [0, 4 N_phi) is stored at  vals[(c / VEC) * n_dof * VEC + row * VEC + c % VEC],
+// VEC = 16 / sizeof(value): each thread (one matrix row) reads 16-byte
+// vectors and a warp reads 512 contiguous bytes per load.
+struct DevOp {
+  int p = 0, nphi = 0, npsi = 0, ne = 0, nd = 0, ncol = 0;
+  int64_t n = 0;                   // n_dof
+  int device = 0;
+  int32_t* cols = nullptr;         // [4][ne]
+  double* K64 = nullptr;           // assembled, FP64
+  float* K32 = nullptr;            // assembled, FP32
+  uint16_t* K16 = nullptr;         // assembled, BF16 bits
+  double* area = nullptr;          // [ne]  A_i = 2|T_i|
+  double* Mref = nullptr;          // [nphi][nphi]
+  // factored per-edge blocks (optional)
+  double* G = nullptr;             // [nd][2][2][nphi][nphi]
+  double* Minv = nullptr;          // [nd][npsi][npsi]
+  double* Uloc = nullptr;          // [nd][2][nphi][nphi]  A_ij U[a][m][k]
+  int32_t* elr = nullptr;          // [nd][2]
+  int32_t* tedge = nullptr;        // [ne][3]  2*internal_edge + side
+  int colour_offsets[9] = {0};
+};
+
+// Dual-index tables (filled once per device): for degree p,
+// lmap[p][m], rmap[p][m]: dual index of the left / right local node m;
+// dl[p][l], dr[p][l]: local node of dual index l on the left / right half (-1 if none).
+void upload_dual_tables(int device);
+
+// ---- applies (stream-ordered, asynchronous)
+cudaError_t launch_apply_assembled_f64(const DevOp& op, double coefK, double coefM, const double* x,
+                                       double* y, cudaStream_t s);
+cudaError_t launch_apply_assembled_f32(const DevOp& op, float coefK, const float* x, float* y,
+                                       cudaStream_t s);
+cudaError_t launch_apply_factored_f64(const DevOp& op, double coefK, double coefM, const double* x,
+                                      double* y, cudaStream_t s);
+cudaError_t launch_d2m_rhs(const DevOp& op, const double* vhat, double* b, cudaStream_t s);
+cudaError_t launch_m2d(const DevOp& op, const double* vbar, double* vhat, cudaStream_t s);
+cudaError_t launch_div(const DevOp& op, const double* vhat, double* y, cudaStream_t s);
+
+// ---- vector helpers for the refinement loop
+// r = b - A x (FP64 assembled form, A = coefM Mbar + coefK K), optional mean
+// projection of b; partial sums of r.r written to part[nblocks]; returns the
+// number of CTAs used (<= max_parts).
+cudaError_t launch_residual_f64(const DevOp& op, double coefK, double coefM, int mean_zero,
+                                const double* b, const double* x, double b_mean, double* r,
+                                double* part, int max_parts, int* nparts, cudaStream_t s);
+cudaError_t launch_sum2(const double* v, int64_t n, double* part, int max_parts, int* nparts,
+                        cudaStream_t s);  // part[j] = (sum v, sum v*v) over CTA j's share
+cudaError_t launch_scale_to_f32(const double* v, double scale, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_axpy_f32_to_f64(double a, const float* d, double* x, int64_t n, cudaStream_t s);
+cudaError_t launch_remove_mean_f64(double* x, const double* sum_dev, int64_t n, cudaStream_t s);
+cudaError_t launch_axpy_f64(double a, const double* d, double* x, int64_t n, cudaStream_t s);
+// part[0] = sum_j part[2 j] (fixed order, one CTA)
+cudaError_t launch_sum_to_first(double* part, int nparts, cudaStream_t s);
+
+// ---- persistent conjugate gradients (cooperative launch)
+// Solves A d = r0 from d = 0 with A = coefM Mbar + coefK K (assembled form in
+// the vector type's precision).  r0 is consumed (r holds the final residual).
+// Iterates until r.r <= stop_rr or max_iters.  Result words in `res`:
+//   res->iters, res->rr (final recursive r.r), res->status.
+struct CGResult {
+  int iters;
+  int status;
+  double rr0;
+  double rr;
+};
+struct CGWork {
+  void* p = nullptr;      // 2 x n vectors (double buffered search direction)
+  void* q = nullptr;      // n
+  double* part = nullptr; // 2 x max_parts x 2
+  GridBarrier* bar = nullptr;
+  CGResult* res = nullptr;
+  int max_parts = 0;
+};
+cudaError_t launch_cg_f64(const DevOp& op, double coefK, double coefM, int mean_zero, double* x,
+                          double* r, double stop_rel, int max_iters, const CGWork& w,
+                          uint64_t timeout_ns, cudaStream_t s, int* grid_used);
+cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, int mean_zero, float* x,
+                          float* r, double stop_rel, int max_iters, const CGWork& w,
+                          uint64_t timeout_ns, cudaStream_t s, int* grid_used);
+int cg_max_blocks(const DevOp& op, int prec);
+
+void count_launch(int n = 1);
+uint64_t launch_count();
+
+}  // namespace dgsl

@@ -1,0 +1,272 @@
+"""ctypes binding of the dgsl C-ABI (``include/dgsl.h``).
+
+Argument marshalling only: every computation runs in ``libdgsl.so``.
+Device vectors are passed as PyTorch CUDA tensors (their ``data_ptr()``),
+streams as ``torch.cuda.Stream`` (their ``cuda_stream`` handle) or None for
+the current stream.  If the library has not been built this module raises on
+first use; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- constants
+OK, EINVAL, EMESH, ENOMEM, EBUDGET, ENOTCONV, ETIMEOUT, EPENDING, ECUDA, ENODEVICE = range(10)
+STORE_F64, STORE_F32, STORE_BF16 = 1, 2, 4
+MAIN, DUAL = 0, 1
+FORM_ASSEMBLED, FORM_FACTORED = 0, 1
+SCHUR, HELMHOLTZ = 0, 1
+PREC_F64, PREC_F32_IR, PREC_BF16_IR = 0, 1, 2
+
+
+class DgslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dgsl error {code}: {msg}")
+        self.code = code
+
+
+class dgsl_mesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("xy", C.POINTER(C.c_double)),
+                ("n_triangles", C.c_int32), ("tri", C.POINTER(C.c_int32)),
+                ("period", C.c_double * 2)]
+
+
+class dgsl_build_opts(C.Structure):
+    _fields_ = [("host_only", C.c_int32), ("device", C.c_int32), ("store", C.c_int32),
+                ("factored", C.c_int32)]
+
+
+class dgsl_info(C.Structure):
+    _fields_ = [("p", C.c_int32), ("n_phi", C.c_int32), ("n_psi", C.c_int32),
+                ("n_tri", C.c_int32), ("n_edge", C.c_int32), ("n_colours", C.c_int32),
+                ("n_dof", C.c_int64), ("n_dual", C.c_int64), ("device_bytes", C.c_int64),
+                ("host_only", C.c_int32), ("device", C.c_int32)]
+
+
+class dgsl_maps(C.Structure):
+    _fields_ = [("edge_vtx", C.c_void_p), ("lr", C.c_void_p), ("loc", C.c_void_p),
+                ("shift", C.c_void_p), ("tri_edge", C.c_void_p), ("perm", C.c_void_p),
+                ("edge_perm", C.c_void_p), ("colour", C.c_void_p),
+                ("colour_offsets", C.c_void_p)]
+
+
+class dgsl_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iters", C.c_int32), ("precision", C.c_int32),
+                ("use_x0", C.c_int32), ("inner_tol", C.c_double), ("max_refine", C.c_int32),
+                ("form", C.c_int32)]
+
+
+class dgsl_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("refinements", C.c_int32),
+                ("cg_launches", C.c_int32), ("relres", C.c_double), ("cg_kernel_ms", C.c_double),
+                ("grid", C.c_int32), ("pad", C.c_int32)]
+
+
+_LIB = None
+
+_SIGS = {
+    "dgsl_last_error": (C.c_char_p, []),
+    "dgsl_version": (C.c_char_p, []),
+    "dgsl_launch_count": (C.c_uint64, []),
+    "dgsl_build_operators": (C.c_int, [C.POINTER(dgsl_mesh), C.c_int, C.POINTER(dgsl_build_opts),
+                                       C.POINTER(C.c_void_p)]),
+    "dgsl_destroy_operator": (None, [C.c_void_p]),
+    "dgsl_operator_info": (C.c_int, [C.c_void_p, C.POINTER(dgsl_info)]),
+    "dgsl_query_maps": (C.c_int, [C.c_void_p, C.POINTER(dgsl_maps)]),
+    "dgsl_node_coords": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dgsl_query_blocks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dgsl_apply_schur": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                   C.c_int, C.c_void_p]),
+    "dgsl_apply_schur_f32": (C.c_int, [C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_void_p]),
+    "dgsl_apply_helmholtz": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_void_p]),
+    "dgsl_project_d2m_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dgsl_project_m2d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dgsl_apply_div": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
+                                C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
+    "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libdgsl.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(code):
+    if code != OK:
+        raise DgslError(code, load().dgsl_last_error().decode())
+    return code
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dptr(t, dtype_name, numel):
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise ValueError(f"{dtype_name} tensor expected, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"tensor has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def dgsl_version():
+    return load().dgsl_version().decode()
+
+
+def dgsl_launch_count():
+    return int(load().dgsl_launch_count())
+
+
+def dgsl_default_solve_opts():
+    o = dgsl_solve_opts()
+    load().dgsl_default_solve_opts(C.byref(o))
+    return o
+
+
+class Operator:
+    """Owning handle of one built operator (``dgsl_build_operators``)."""
+
+    def __init__(self, xy, tri, period, p, host_only=False, device=0, store=0, factored=False):
+        lib = load()
+        self._xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        m = dgsl_mesh(self._xy.shape[0], self._xy.ctypes.data_as(C.POINTER(C.c_double)),
+                      self._tri.shape[0], self._tri.ctypes.data_as(C.POINTER(C.c_int32)),
+                      (C.c_double * 2)(float(period[0]), float(period[1])))
+        o = dgsl_build_opts(int(host_only), int(device), int(store), int(factored))
+        h = C.c_void_p()
+        _check(lib.dgsl_build_operators(C.byref(m), int(p), C.byref(o), C.byref(h)))
+        self.h = h
+        inf = dgsl_info()
+        _check(lib.dgsl_operator_info(self.h, C.byref(inf)))
+        self.p = inf.p
+        self.n_phi, self.n_psi = inf.n_phi, inf.n_psi
+        self.n_tri, self.n_edge, self.n_colours = inf.n_tri, inf.n_edge, inf.n_colours
+        self.n_dof, self.n_dual = inf.n_dof, inf.n_dual
+        self.device_bytes = inf.device_bytes
+        self.device = inf.device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dgsl_destroy_operator(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host queries
+    def maps(self):
+        ne, nd = self.n_tri, self.n_edge
+        out = dict(edge_vtx=np.zeros((nd, 2), np.int32), lr=np.zeros((nd, 2), np.int32),
+                   loc=np.zeros((nd, 2), np.uint8), shift=np.zeros((nd, 2), np.int8),
+                   tri_edge=np.zeros((ne, 3), np.int32), perm=np.zeros(ne, np.int32),
+                   edge_perm=np.zeros(nd, np.int32), colour=np.zeros(nd, np.uint8),
+                   colour_offsets=np.zeros(self.n_colours + 1, np.int32))
+        m = dgsl_maps(*[C.c_void_p(out[f].ctypes.data) for f, _ in dgsl_maps._fields_])
+        _check(load().dgsl_query_maps(self.h, C.byref(m)))
+        return out
+
+    def node_coords(self, grid):
+        n = self.n_dof if grid == MAIN else self.n_dual
+        out = np.zeros((n, 2))
+        _check(load().dgsl_node_coords(self.h, int(grid), C.c_void_p(out.ctypes.data)))
+        return out
+
+    def blocks(self):
+        n, npsi = self.n_phi, self.n_psi
+        G = np.zeros((self.n_edge, 2, 2, n, n))
+        Minv = np.zeros((self.n_edge, npsi, npsi))
+        Mref = np.zeros((n, n))
+        area = np.zeros(self.n_tri)
+        _check(load().dgsl_query_blocks(self.h, C.c_void_p(G.ctypes.data), C.c_void_p(Minv.ctypes.data),
+                                        C.c_void_p(Mref.ctypes.data), C.c_void_p(area.ctypes.data)))
+        return G, Minv, Mref, area
+
+    # ---- device applies
+    def dgsl_apply_schur(self, dt, x, y, n_rhs=1, form=FORM_ASSEMBLED, stream=None):
+        n = self.n_dof * n_rhs
+        _check(load().dgsl_apply_schur(self.h, int(form), float(dt), _dptr(x, "float64", n),
+                                       _dptr(y, "float64", n), int(n_rhs), _stream(stream)))
+
+    def dgsl_apply_schur_f32(self, dt, x, y, n_rhs=1, stream=None):
+        n = self.n_dof * n_rhs
+        _check(load().dgsl_apply_schur_f32(self.h, float(dt), _dptr(x, "float32", n),
+                                           _dptr(y, "float32", n), int(n_rhs), _stream(stream)))
+
+    def dgsl_apply_helmholtz(self, nu_dt, x, y, n_rhs=1, stream=None):
+        n = self.n_dof * n_rhs
+        _check(load().dgsl_apply_helmholtz(self.h, float(nu_dt), _dptr(x, "float64", n),
+                                           _dptr(y, "float64", n), int(n_rhs), _stream(stream)))
+
+    def dgsl_project_d2m_rhs(self, vhat, b, n_rhs=1, stream=None):
+        _check(load().dgsl_project_d2m_rhs(self.h, _dptr(vhat, "float64", self.n_dual * n_rhs),
+                                           _dptr(b, "float64", self.n_dof * n_rhs), int(n_rhs),
+                                           _stream(stream)))
+
+    def dgsl_project_m2d(self, vbar, vhat, n_rhs=1, stream=None):
+        _check(load().dgsl_project_m2d(self.h, _dptr(vbar, "float64", self.n_dof * n_rhs),
+                                       _dptr(vhat, "float64", self.n_dual * n_rhs), int(n_rhs),
+                                       _stream(stream)))
+
+    def dgsl_apply_div(self, vhat, y, n_rhs=1, stream=None):
+        _check(load().dgsl_apply_div(self.h, _dptr(vhat, "float64", 2 * self.n_dual * n_rhs),
+                                     _dptr(y, "float64", self.n_dof * n_rhs), int(n_rhs),
+                                     _stream(stream)))
+
+    def dgsl_cg_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, check=True):
+        """Returns a list of dgsl_solve_info (one per right-hand side)."""
+        if opts is None:
+            opts = dgsl_default_solve_opts()
+        infos = (dgsl_solve_info * n_rhs)()
+        n = self.n_dof * n_rhs
+        code = load().dgsl_cg_solve(self.h, int(kind), float(coef), _dptr(b, "float64", n),
+                                    _dptr(x, "float64", n), int(n_rhs), C.byref(opts), infos,
+                                    _stream(stream))
+        if check and code not in (OK,):
+            _check(code)
+        return list(infos)
+
+
+def solve_opts(**kw):
+    o = dgsl_default_solve_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o

@@ -1,0 +1,167 @@
+"""GPU parity of the CG solves (eq. pressure_final / eq. ad5) through the
+C-ABI against the oracle's sparse direct solves: FP64 CG and FP32 inner CG
+under FP64 iterative refinement; residual measured by the oracle's FP64
+operator, error against the direct solution; edge cases (zero right-hand
+side, iteration cap, several right-hand sides, determinism, mean-zero
+output) and a full-size 256 x 256, p = 3 solve checked on sampled rows."""
+import numpy as np
+import pytest
+
+from oracle import assemble as OA
+from oracle import fields as OF
+from oracle import mesh as OM
+from oracle import operators as OP
+from paper_2401_17806_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_apply import dev, rel, to_internal, to_natural  # noqa: E402
+
+
+def _setup(N, p, seed, store=0):
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, per = synth.jittered_periodic_mesh(N, seed)
+    op = dgsl.Operator(xy, tri, per, p, store=store)
+    orc = OP.Operators(OA.assemble(xy, tri, per, p))
+    return op, orc, op.maps()
+
+
+def _solve(op, m, kind, coef, b_nat, **kw):
+    from paper_2401_17806_gb300 import dgsl
+    b = dev(to_internal(b_nat, m["perm"], op.n_phi))
+    x = torch.zeros_like(b)
+    info = op.dgsl_cg_solve(kind, coef, b, x, opts=dgsl.solve_opts(**kw), check=False)[0]
+    torch.cuda.synchronize()
+    return to_natural(x.cpu().numpy(), m["perm"], op.n_phi), info, x
+
+
+def test_c1_manufactured_fp64_to_1e12(dgsl_lib):
+    """16 x 16 mesh, p = 1, dt = 1e-2, b = dt^2 int phi f, f = -Laplace(p_ex)."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(16, 1, 0)
+    dt = 1e-2
+    f = lambda x, y: synth.manufactured_pressure(x, y)[1]
+    b = dt * dt * OF.load_vector(orc.bl.conn, 1, f)
+    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b, tol=1e-12, precision=dgsl.PREC_F64)
+    assert info.status == dgsl.OK and info.relres <= 1e-12
+    S = orc.schur_matrix(dt)
+    pb = OP.project_mean(b)
+    assert np.linalg.norm(pb - S @ x) / np.linalg.norm(pb) <= 1e-12
+    xd = OP.schur_solve_direct(S, b)
+    assert rel(x, xd) <= 1e-10
+    assert abs(x.sum()) <= 1e-12 * np.abs(x).sum()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,p", [(8, 2), (20, 3), (12, 4)])
+def test_schur_solve_parity(dgsl_lib, prec, N, p):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(N, p, 2)
+    dt = 1e-3
+    b = synth.standard_normal(op.n_dof, 31)
+    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b, tol=1e-12, precision=prec)
+    assert info.status == dgsl.OK, info.status
+    S = orc.schur_matrix(dt)
+    pb = OP.project_mean(b)
+    assert np.linalg.norm(pb - S @ x) / np.linalg.norm(pb) <= 1e-12
+    xd = OP.schur_solve_direct(S, b)
+    # error bound: kappa * residual (kappa of the projected operator)
+    ev = np.linalg.eigvalsh(S.toarray()) if op.n_dof <= 2500 else None
+    kappa = ev[-1] / ev[1] if ev is not None else 1e6
+    assert rel(x, xd) <= max(1e-10, 10 * kappa * 1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_helmholtz_solve_parity(dgsl_lib, prec):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(20, 3, 4)
+    nu_dt = 1e-3
+    b = synth.standard_normal(op.n_dof, 41)
+    x, info, _ = _solve(op, m, dgsl.HELMHOLTZ, nu_dt, b, tol=1e-12, precision=prec)
+    assert info.status == dgsl.OK
+    H = orc.helmholtz_matrix(nu_dt)
+    assert np.linalg.norm(b - H @ x) / np.linalg.norm(b) <= 1e-12
+    assert rel(x, OP.direct_solve(H, b)) <= 1e-10
+
+
+def test_exactness_variant(dgsl_lib):
+    """b = S Pi(p_ex) is solved exactly by Pi(p_ex) - mean."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(16, 2, 6)
+    dt = 1e-2
+    X = OF.main_nodes(orc.bl.conn, 2)
+    pe = synth.manufactured_pressure(X[..., 0], X[..., 1])[0].ravel()
+    b = orc.apply_schur(pe, dt)
+    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b, tol=1e-13, precision=dgsl.PREC_F32_IR)
+    assert info.status == dgsl.OK
+    assert rel(x, pe - pe.mean()) <= 1e-10
+
+
+def test_edge_cases(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(8, 2, 7)
+    # zero right-hand side
+    x, info, _ = _solve(op, m, dgsl.SCHUR, 1e-2, np.zeros(op.n_dof))
+    assert info.status == dgsl.OK and info.iters == 0 and np.all(x == 0)
+    # constant right-hand side is all nullspace: projected b = 0
+    x, info, _ = _solve(op, m, dgsl.SCHUR, 1e-2, np.ones(op.n_dof))
+    assert info.status == dgsl.OK and np.abs(x).max() == 0
+    # iteration cap
+    b = synth.standard_normal(op.n_dof, 3)
+    x, info, _ = _solve(op, m, dgsl.SCHUR, 1e-2, b, max_iters=3, tol=1e-12)
+    assert info.status == dgsl.ENOTCONV and info.iters <= 3
+    # invalid arguments are rejected before any launch
+    bb = dev(np.zeros(op.n_dof))
+    with pytest.raises(dgsl.DgslError):
+        op.dgsl_cg_solve(7, 1.0, bb, bb.clone())
+    with pytest.raises(dgsl.DgslError):
+        op.dgsl_cg_solve(dgsl.SCHUR, -1.0, bb, bb.clone())
+
+
+def test_multiple_rhs_and_determinism(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(12, 3, 8)
+    dt = 1e-2
+    bs = [synth.standard_normal(op.n_dof, 50 + k) for k in range(2)]
+    b = dev(np.concatenate([to_internal(v, m["perm"], op.n_phi) for v in bs]))
+    outs = []
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        infos = op.dgsl_cg_solve(dgsl.SCHUR, dt, b, x, n_rhs=2,
+                                 opts=dgsl.solve_opts(tol=1e-11, precision=dgsl.PREC_F32_IR))
+        torch.cuda.synchronize()
+        assert all(i.status == dgsl.OK for i in infos)
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])         # bitwise deterministic
+    S = orc.schur_matrix(dt)
+    for k in range(2):
+        xk = to_natural(outs[0].reshape(2, -1)[k], m["perm"], op.n_phi)
+        pb = OP.project_mean(bs[k])
+        assert np.linalg.norm(pb - S @ xk) / np.linalg.norm(pb) <= 1e-11
+        # each right-hand side alone gives the same answer
+        xa, _, _ = _solve(op, m, dgsl.SCHUR, dt, bs[k], tol=1e-11, precision=dgsl.PREC_F32_IR)
+        assert np.array_equal(xa, xk)
+
+
+def test_full_size_solve_sampled_residual(dgsl_lib):
+    """256 x 256, p = 3, dt = 1e-3, FP32 inner CG + FP64 refinement to 1e-10:
+    the oracle recomputes sampled rows of the residual."""
+    from paper_2401_17806_gb300 import dgsl
+    N, p, dt = 256, 3, 1e-3
+    xy, tri, per = synth.jittered_periodic_mesh(N, 0)
+    op = dgsl.Operator(xy, tri, per, p)
+    conn = OM.connectivity(xy, tri, per)
+    m = op.maps()
+    b64 = synth.standard_normal(op.n_dof, 11) * dt * dt
+    b64 -= b64.mean()
+    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b64, tol=1e-10, precision=dgsl.PREC_F32_IR)
+    assert info.status == dgsl.OK and info.relres <= 1e-10
+    rng = np.random.default_rng(2)
+    ids = rng.choice(op.n_tri, 400, replace=False)
+    Sx = OP.sampled_rows(conn, p, x, ids, dt * dt)
+    r = b64.reshape(-1, op.n_phi)[ids] - Sx
+    # a global relative residual of 1e-10 bounds the sampled block's norm by
+    # ||r||; compare against the same sample of b
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b64)

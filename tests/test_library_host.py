@@ -1,0 +1,95 @@
+"""Host-side parity of the library (no GPU): connectivity, RCM, colouring and
+edge order bit-exact against the oracle; node positions and the FP64 block
+precompute (reference-operator form of Sec. 2.4) against the oracle's
+physical-coordinate quadrature."""
+import numpy as np
+import pytest
+
+from oracle import assemble as OA
+from oracle import basis as OB
+from oracle import fields as OF
+from oracle import mesh as OM
+from oracle import operators as OP
+from paper_2401_17806_gb300 import synth
+
+
+def host_op(N, p, seed=0):
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, per = synth.jittered_periodic_mesh(N, seed)
+    return dgsl.Operator(xy, tri, per, p, host_only=True), (xy, tri, per)
+
+
+@pytest.mark.parametrize("N,seed", [(3, 0), (5, 1), (16, 2), (33, 3)])
+def test_maps_bit_exact(dgsl_lib, N, seed):
+    op, (xy, tri, per) = host_op(N, 1, seed)
+    m = op.maps()
+    c = OM.connectivity(xy, tri, per)
+    perm = OM.rcm_order(c)
+    colour, eperm, offs = OM.colouring(c, perm)
+    np.testing.assert_array_equal(m["edge_vtx"], c.edge_vtx)
+    np.testing.assert_array_equal(m["lr"], c.lr)
+    np.testing.assert_array_equal(m["loc"], c.loc)
+    np.testing.assert_array_equal(m["shift"], c.shift)
+    np.testing.assert_array_equal(m["tri_edge"], c.tri_edge)
+    np.testing.assert_array_equal(m["perm"], perm)
+    np.testing.assert_array_equal(m["colour"], colour)
+    np.testing.assert_array_equal(m["edge_perm"], eperm)
+    np.testing.assert_array_equal(m["colour_offsets"], offs)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_node_coordinates(dgsl_lib, p):
+    op, (xy, tri, per) = host_op(6, p, 4)
+    m = op.maps()
+    c = OM.connectivity(xy, tri, per)
+    main = op.node_coords(0).reshape(op.n_tri, op.n_phi, 2)
+    np.testing.assert_allclose(main, OF.main_nodes(c, p)[m["perm"]], rtol=0, atol=1e-15)
+    dual = op.node_coords(1).reshape(op.n_edge, op.n_psi, 2)
+    np.testing.assert_allclose(dual, OF.dual_nodes(c, p)[m["edge_perm"]], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_blocks_match_oracle(dgsl_lib, p):
+    op, (xy, tri, per) = host_op(5, p, 6)
+    m = op.maps()
+    G, Minv, Mref, area = op.blocks()
+    bl = OA.assemble(xy, tri, per, p)
+    L, R = OB.dual_maps(p)
+    ep = m["edge_perm"]
+    scale = np.abs(bl.Q).max()
+    for s, mp in enumerate([L, R]):
+        # library G[e][s][c][m][k] = Q_{s,j}[map_s(m), k, c], j = edge_perm[e]
+        want = np.moveaxis(bl.Q[ep, s][:, mp, :, :], -1, 1)
+        np.testing.assert_allclose(G[:, s], want, rtol=0, atol=1e-13 * scale)
+    mi = OP.dual_mass_inverse(bl)[ep]
+    np.testing.assert_allclose(Minv, mi, rtol=1e-11, atol=1e-11 * np.abs(mi).max())
+    np.testing.assert_allclose(area, bl.area2[m["perm"]], rtol=1e-15)
+    mb = bl.Mbar[m["perm"][0]]
+    np.testing.assert_allclose(Mref * area[0], mb, rtol=1e-13, atol=1e-14 * np.abs(mb).max())
+
+
+def test_bad_inputs_rejected(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, per = synth.jittered_periodic_mesh(4, 0)
+    with pytest.raises(dgsl.DgslError) as e:
+        dgsl.Operator(xy, tri, per, 5, host_only=True)
+    assert e.value.code == dgsl.EINVAL
+    bad = tri.copy()
+    bad[3] = bad[3][::-1]
+    with pytest.raises(dgsl.DgslError) as e:
+        dgsl.Operator(xy, bad, per, 2, host_only=True)
+    assert e.value.code == dgsl.EMESH
+    xy2, tri2, per2 = synth.jittered_periodic_mesh(2, 0)
+    with pytest.raises(dgsl.DgslError) as e:
+        dgsl.Operator(xy2, tri2, per2, 1, host_only=True)
+    assert e.value.code == dgsl.EMESH
+    with pytest.raises(dgsl.DgslError) as e:
+        dgsl.Operator(xy, tri, [0.0, 1.0], 1, host_only=True)
+    assert e.value.code == dgsl.EINVAL
+    op = dgsl.Operator(xy, tri, per, 1, host_only=True)
+    with pytest.raises(dgsl.DgslError) as e:
+        import torch
+        x = torch.zeros(op.n_dof, dtype=torch.float64)
+        dgsl.load().dgsl_apply_schur(op.h, 0, 1.0, x.data_ptr() or 8, x.data_ptr() or 8, 1, None)
+        dgsl._check(dgsl.load().dgsl_apply_schur(op.h, 0, 1.0, 8, 8, 1, None))
+    assert e.value.code == dgsl.ENODEVICE
