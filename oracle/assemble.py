@@ -53,15 +53,20 @@ class Blocks:
     length: np.ndarray   # [Nd]
 
 
-def _sub_triangles(conn: Connectivity, idx):
+def _sub_triangles(conn: Connectivity, idx, local=False):
     """Vertex coordinates of T_{l,j} = (b_l, X1, X2) and T_{r,j} = (b_r, X2, X1),
-    each in its own triangle's frame, plus the edge endpoints in each frame."""
+    each in its own triangle's frame, plus the edge endpoints in each frame.
+    local=True moves each triangle's frame so that its first vertex is the
+    origin (the block integrals depend only on vertex differences)."""
     l = conn.lr[idx, 0]
     r = conn.lr[idx, 1]
     al = conn.loc[idx, 0].astype(np.int64)
     ar = conn.loc[idx, 1].astype(np.int64)
     Pl = conn.tri_xy[l]
     Pr = conn.tri_xy[r]
+    if local:
+        Pl = Pl - Pl[:, :1, :]
+        Pr = Pr - Pr[:, :1, :]
     e = np.arange(len(idx))
     X1l = Pl[e, al]
     X2l = Pl[e, (al + 1) % 3]
@@ -86,7 +91,10 @@ def edge_blocks(conn: Connectivity, p, idx):
     D = np.zeros((ne_, 2, nphi, npsi, 2))
     Q = np.zeros((ne_, 2, npsi, nphi, 2))
     U = np.zeros((ne_, 2, npsi, nphi))
-    l, r, Pl, Pr, Tl, Tr, (X1l, X2l), (X1r, X2r) = _sub_triangles(conn, idx)
+    # every integral below is invariant under translating an element, so each
+    # element is evaluated relative to its first vertex: points near the
+    # element then carry no absolute-coordinate cancellation in the pull-back
+    l, r, Pl, Pr, Tl, Tr, (X1l, X2l), (X1r, X2r) = _sub_triangles(conn, idx, local=True)
     d = X2l - X1l
     glen = np.hypot(d[:, 0], d[:, 1])
     n = np.stack([d[:, 1], -d[:, 0]], 1) / glen[:, None]
@@ -131,7 +139,7 @@ def edge_blocks(conn: Connectivity, p, idx):
 def main_mass(conn: Connectivity, p):
     """Mbar_i (eq. Mi) by physical quadrature on T_i, and A_i = 2|T_i|."""
     rpts, rw = B.duffy_rule(p + 2)
-    P = conn.tri_xy
+    P = conn.tri_xy - conn.tri_xy[:, :1, :]      # element-local frame (translation invariant)
     e1 = P[:, 1] - P[:, 0]
     e2 = P[:, 2] - P[:, 0]
     area2 = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]
