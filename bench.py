@@ -1,0 +1,441 @@
+"""Benchmark of the implicit-stage hot path on one GB300 per rank.
+
+Workload (per rank): the 256 x 256 jittered periodic mesh of the synthetic
+family (131,072 triangles, 196,608 edges), p = 3, dt = 1e-3, nu = 1e-3.  One
+step is one implicit stage of the paper's pressure projection:
+  b_S = G^T vhat                      (divergence of the dual velocity, eq. ins.1)
+  b_c = sum_j U_ij^T vhat_c,j         (eq. d2m right-hand side, both components)
+  S p = b_S                           (pressure Schur solve, eq. pressure_final)
+  H vbar_c = b_c                      (viscous solves, eq. ad5 with lambda = nu)
+all to relative residual 1e-10, FP32 inner CG under FP64 refinement.  vhat
+is the Taylor-Green velocity sampled at the dual nodes plus seeded N(0, 1e-2)
+noise.  Metric: CG DOF*iterations per second (all solves of the step).
+
+Legs: the device-resident GPU leg (value), an end-to-end leg through the
+C-ABI from pinned host buffers (e2e), one FP64-CG step (the one-solve-at-a-
+time FP64 baseline), and the oracle timed on the host cores (cpu_baseline).
+`--impl reference` times the oracle alone on the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(N=256, p=3, dt=1e-3, nu=1e-3, seed=0, noise=1e-2, tol=1e-10)
+METRIC = "Schur-CG DOF*iters/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def workload_name(args):
+    return (f"pressure Schur + 2 viscous Helmholtz solves to 1e-10, {args.N}x{args.N} jittered "
+            f"periodic mesh, p={args.p}")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f32", "bf16", "f64"], default="f32")
+    ap.add_argument("--N", type=int, default=WORKLOAD["N"])
+    ap.add_argument("--p", type=int, default=WORKLOAD["p"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-iters", type=int, default=10, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        under = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(under), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    """(rank, world, local_rank); NCCL only for the timing barrier / max."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def dual_velocity(op, seed):
+    """Taylor-Green velocity at the dual nodes plus N(0, 1e-2) noise,
+    [2][n_edge][n_psi] in the library's internal edge order."""
+    import numpy as np
+    from paper_2401_17806_gb300 import synth
+    xy = op.node_coords(1)
+    u, v = synth.taylor_green_velocity(xy[:, 0], xy[:, 1])
+    noise = synth.standard_normal((2, op.n_dual), seed + 1, WORKLOAD["noise"])
+    return np.stack([u, v]) + noise
+
+
+def bytes_per_row_iter(nphi, coupling_bytes, vec_bytes):
+    """Algorithmic bytes per matrix row per CG iteration of the persistent
+    kernel: the row's 4*N_phi coupling coefficients, its share of the column
+    indices (4 int32 per triangle), and 10 vector accesses (phase A: read r and
+    p_old, write p_new and q; phase B: read p_new, q, r, x, write x and r)."""
+    return 4 * nphi * coupling_bytes + 16.0 / nphi + 10 * vec_bytes
+
+
+class Stage:
+    """Device buffers and the calls of one implicit stage."""
+
+    def __init__(self, op, vhat_np, precision):
+        import torch
+        from paper_2401_17806_gb300 import dgsl
+        self.op = op
+        self.dgsl = dgsl
+        n = op.n_dof
+        self.vhat = torch.tensor(vhat_np.ravel(), dtype=torch.float64, device="cuda")
+        self.bS = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.bH = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        self.p = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.vbar = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        prec = {"f32": dgsl.PREC_F32_IR, "bf16": dgsl.PREC_BF16_IR, "f64": dgsl.PREC_F64}[precision]
+        self.opts = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=prec)
+
+    def run(self, stream, opts=None):
+        op, d = self.op, self.dgsl
+        o = opts or self.opts
+        op.dgsl_apply_div(self.vhat, self.bS, stream=stream)
+        op.dgsl_project_d2m_rhs(self.vhat, self.bH, n_rhs=2, stream=stream)
+        infos = op.dgsl_cg_solve(d.SCHUR, WORKLOAD["dt"], self.bS, self.p, opts=o, stream=stream)
+        infos += op.dgsl_cg_solve(d.HELMHOLTZ, WORKLOAD["nu"] * WORKLOAD["dt"], self.bH, self.vbar,
+                                  n_rhs=2, opts=o, stream=stream)
+        for i in infos:
+            if i.status != d.OK:
+                raise RuntimeError(f"solve failed: status {i.status}, relres {i.relres:.3e}")
+        return infos
+
+
+def gpu_leg(args, rank, world, local):
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(local)
+    N, p = args.N, args.p
+    seed = WORKLOAD["seed"] + rank
+    xy, tri, per = synth.jittered_periodic_mesh(N, seed)
+    t0 = time.time()
+    store = dgsl.STORE_F64 | dgsl.STORE_F32 | (dgsl.STORE_BF16 if args.precision == "bf16" else 0)
+    op = dgsl.Operator(xy, tri, per, p, device=local, store=store, factored=True)
+    build_s = time.time() - t0
+    vhat = dual_velocity(op, seed)
+    st = Stage(op, vhat, args.precision)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            st.run(stream)
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    l0 = dgsl.dgsl_launch_count()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            infos += st.run(stream)
+        ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = dgsl.dgsl_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    dof_iters = sum(op.n_dof * i.iters for i in infos)
+    schur_iters = sum(i.iters for k, i in enumerate(infos) if k % 3 == 0)
+    kern_ms = sum(i.cg_kernel_ms for i in infos)
+    res = dict(ms=ms, dof_iters=dof_iters, schur_iters_per_step=schur_iters / args.steps,
+               helm_iters_per_step=(sum(i.iters for i in infos) - schur_iters) / args.steps,
+               refinements=sum(i.refinements for i in infos) / args.steps,
+               relres_max=max(i.relres for i in infos), kern_ms=kern_ms, launches=launches,
+               cg_launches=sum(i.cg_launches for i in infos), grid=infos[0].grid,
+               clocks=clk, build_s=build_s, op=op, stage=st, stream=stream,
+               iters_total=sum(i.iters for i in infos), device_bytes=op.device_bytes)
+    # ---- end to end: pinned host input -> device, stage, device -> pinned host
+    vh_host = torch.from_numpy(vhat.ravel().copy()).pin_memory()
+    p_host = torch.empty(op.n_dof, dtype=torch.float64).pin_memory()
+    v_host = torch.empty(2 * op.n_dof, dtype=torch.float64).pin_memory()
+    barrier()
+    e_infos = []
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st.vhat.copy_(vh_host, non_blocking=True)
+            e_infos += st.run(stream)
+            p_host.copy_(st.p, non_blocking=True)
+            v_host.copy_(st.vbar, non_blocking=True)
+        ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    res["e2e_ms"] = ev0.elapsed_time(ev1)
+    res["e2e_dof_iters"] = sum(op.n_dof * i.iters for i in e_infos)
+    res["h2d"] = vh_host.numel() * 8
+    res["d2h"] = (p_host.numel() + v_host.numel()) * 8
+    # ---- one-solve-at-a-time FP64 CG on the same stage
+    if not args.no_fp64_baseline and args.precision != "f64":
+        o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
+        barrier()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            f_infos = st.run(stream, o64)
+            ev1.record(stream)
+        stream.synchronize()
+        res["fp64"] = dict(ms=ev0.elapsed_time(ev1), iters=sum(i.iters for i in f_infos),
+                           dof_iters=sum(op.n_dof * i.iters for i in f_infos),
+                           kern_ms=sum(i.cg_kernel_ms for i in f_infos))
+    return res
+
+
+# ---------------------------------------------------------------- oracle legs
+
+def oracle_setup(N, p):
+    """The oracle's Schur operator and right-hand side for the workload (host
+    only; used by the CPU baseline and by --impl reference)."""
+    import numpy as np
+    from oracle import assemble as OA
+    from oracle import fields as OF
+    from oracle import operators as OP
+    from paper_2401_17806_gb300 import synth
+    xy, tri, per = synth.jittered_periodic_mesh(N, WORKLOAD["seed"])
+    orc = OP.Operators(OA.assemble(xy, tri, per, p))
+    Y = OF.dual_nodes(orc.bl.conn, p).reshape(-1, 2)
+    u, v = synth.taylor_green_velocity(Y[:, 0], Y[:, 1])
+    vhat = np.stack([u, v]) + synth.standard_normal((2, Y.shape[0]), WORKLOAD["seed"] + 1,
+                                                    WORKLOAD["noise"])
+    b = orc.G.T @ vhat.ravel()
+    return orc, b
+
+
+def oracle_cg_rate(orc, b, iters):
+    """DOF*iterations/s of the oracle's plain FP64 CG (fixed iteration count)."""
+    from oracle import operators as OP
+    dt = WORKLOAD["dt"]
+    t = time.perf_counter()
+    _, it, _ = OP.cg(lambda v: orc.apply_schur(v, dt), b, tol=0.0, maxit=iters, mean_zero=True)
+    el = time.perf_counter() - t
+    return orc.n * it / el, it, el
+
+
+def cpu_leg_main(args):
+    orc, b = oracle_setup(args.N, args.p)
+    rate, it, el = oracle_cg_rate(orc, b, args.cpu_iters)
+    print(json.dumps({"value": rate, "iters": it, "seconds": el, "n_dof": int(orc.n)}))
+
+
+def run_cpu_baseline(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--N", str(args.N), "--p", str(args.p),
+           "--cpu-iters", str(args.cpu_iters)]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, never fatal to the GPU number
+        return {"value": None, "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {type(e).__name__}"}
+    return {"value": out["value"], "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{out['iters']} FP64 CG iterations of the Schur solve on the same "
+                       f"{args.N}x{args.N}, p={args.p} mesh ({out['n_dof']} DOF), scipy/numpy "
+                       f"single-threaded, operator build excluded")}
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    orc, b = oracle_setup(args.N, args.p)
+    for _ in range(args.warmup):
+        oracle_cg_rate(orc, b, 2)
+    t = time.perf_counter()
+    dof_iters = 0
+    for _ in range(args.steps):
+        _, it, _ = oracle_cg_rate(orc, b, args.cpu_iters)
+        dof_iters += orc.n * it
+    el = time.perf_counter() - t
+    value = dof_iters / el
+    sample = (f"each step: {args.cpu_iters} FP64 CG iterations of the Schur solve on the "
+              f"{args.N}x{args.N}, p={args.p} mesh, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF*iters/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "N": args.N, "p": args.p, "n_dof": int(orc.n)},
+        "cpu_baseline": {"value": value, "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "DOF*iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------- main
+
+def main():
+    args = parse_args()
+    if args.cpu_leg:
+        cpu_leg_main(args)
+        return
+    if args.impl == "reference":
+        reference_main(args)
+        return
+    rank, world, local = dist_setup(args)
+    import torch
+    res = gpu_leg(args, rank, world, local)
+    ms, e2e_ms = res["ms"], res["e2e_ms"]
+    dof_iters, e2e_dof_iters = float(res["dof_iters"]), float(res["e2e_dof_iters"])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s = torch.tensor([dof_iters, e2e_dof_iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        ms, e2e_ms = t.tolist()
+        dof_iters, e2e_dof_iters = s.tolist()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args)
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    op = res["op"]
+    cb, vb = {"f32": (4, 4), "bf16": (2, 4), "f64": (8, 8)}[args.precision]
+    per_row = bytes_per_row_iter(op.n_phi, cb, vb)
+    alg_bytes = res["iters_total"] * op.n_dof * per_row
+    achieved = alg_bytes / (res["kern_ms"] * 1e-3) / 1e9 if res["kern_ms"] > 0 else None
+    peak, peak_src = measured_hbm_peak()
+    line = {
+        "metric": METRIC,
+        "value": dof_iters / (ms * 1e-3),
+        "unit": "DOF*iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f32": "f32+f64", "bf16": "bf16+f32+f64", "f64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(args), "N": args.N, "p": args.p, "n_dof": op.n_dof,
+            "n_tri": op.n_tri, "n_edge": op.n_edge, "dt": WORKLOAD["dt"], "nu": WORKLOAD["nu"],
+            "tol": WORKLOAD["tol"],
+            "precision": {"f32": "FP32 couplings + FP32 inner CG, FP64 refinement",
+                          "bf16": "BF16 couplings, FP32 inner CG, FP64 refinement",
+                          "f64": "FP64 CG"}[args.precision],
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2: FP32 + FP64 couplings "
+                  f"{(op.device_bytes / 1e6):.0f} MB resident, couplings streamed every iteration",
+            "schur_iters_per_step": res["schur_iters_per_step"],
+            "helmholtz_iters_per_step": res["helm_iters_per_step"],
+            "refinements_per_step": res["refinements"],
+            "max_relres": res["relres_max"],
+            "operator_build_s": res["build_s"],
+            "cg_grid_ctas": res["grid"],
+        },
+        "roofline": {
+            "kernel": "k_cg (persistent CG, FP32 couplings)" if args.precision == "f32" else "k_cg",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "bytes_per_row_iter": per_row,
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_dof_iters / (e2e_ms * 1e-3), "unit": "DOF*iters/s",
+                "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    if "fp64" in res:
+        f = res["fp64"]
+        line["fp64_cg_baseline"] = {"value": f["dof_iters"] / (f["ms"] * 1e-3), "unit": "DOF*iters/s",
+                                    "ms_per_step": f["ms"], "iters_per_step": f["iters"],
+                                    "speedup_of_value": (dof_iters / ms) / (f["dof_iters"] / f["ms"]),
+                                    "stage_time_ratio": f["ms"] / (ms / args.steps)}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
