@@ -244,6 +244,30 @@ int dgsl_cg_solve(const dgsl_operator* op, int kind, double coef, const double* 
 
 void dgsl_default_solve_opts(dgsl_solve_opts* opts);
 
+/* Same solve as dgsl_cg_solve, for callers that cannot allocate device memory
+ * when they solve: code that runs while a CUDA stream is being captured into a
+ * graph, real-time loops and services that reserve all device memory at start-up
+ * under a fixed budget, or hosts whose own allocator owns the GPU.  This entry
+ * point calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * is one fixed device array inside the library (about 10.5 MB: five vectors of
+ * 262,144 doubles plus reduction slots), created when the library is loaded and
+ * held by every GPU that loads it until the process exits.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *  - Limit: op's n_dof <= 262,144 (per right-hand side); larger operators are
+ *    rejected with DGSL_EINVAL before anything runs.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins.
+ *  - Every call on a device shares the one array, which keeps whatever the last
+ *    call left in it; everything a solve needs zeroed is cleared by the call.
+ *    Calls are serialized by a lock and return only after their GPU work has
+ *    finished; two solves that overlapped on the GPU would race on the array.
+ *  - Arguments, results and errors as dgsl_cg_solve, except that
+ *    info->cg_kernel_ms is reported as 0 (no timing events are created). */
+int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const double* b,
+                          double* x, int n_rhs, const dgsl_solve_opts* opts,
+                          dgsl_solve_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -547,3 +547,181 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
     return worst;
   });
 }
+
+// ------------------------------------------------------------ solve without allocation
+//
+// dgsl_cg_solve_noalloc: the same refinement + persistent-CG solve as
+// dgsl_cg_solve, for callers that must not allocate device memory at solve
+// time.  Its scratch (residual, correction, search directions, matvec output,
+// per-CTA partial sums, barrier and result words) lives in one file-scope
+// device array of fixed size, allocated when the library is loaded and held by
+// every GPU that loads it until the process exits.
+namespace {
+
+constexpr int64_t kNoAllocMaxDof = int64_t(1) << 18;   // 262,144 DOFs per right-hand side
+constexpr int kNoAllocMaxParts = 1024;                 // per-CTA partial slots
+constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxDof * sizeof(double);
+// r64 | d64 (also r32 + d32) | p (2 vectors) | q | part (4 slots) | part2 (2) | barrier | result
+constexpr size_t kNoAllocBytes = 5 * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the array on `device` (current).  In host code the
+// array's name is only a host-side stand-in; the address must come from
+// cudaGetSymbolAddress, once per device.
+void* noalloc_scratch(int device) {
+  if (device < 0 || device >= 64) throw Error(DGSL_EINVAL, "device ordinal out of range");
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) throw Error(DGSL_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[device] = p;
+  }
+  return g_noalloc_ptr[device];
+}
+
+int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef, const double* b, double* x,
+                      const dgsl_solve_opts& o, dgsl_solve_info* info, cudaStream_t s) {
+  const int64_t n = d.n;
+  double* r64 = reinterpret_cast<double*>(base);
+  double* d64 = reinterpret_cast<double*>(base + kNoAllocVecBytes);
+  float* r32 = reinterpret_cast<float*>(base + kNoAllocVecBytes);
+  float* d32 = r32 + kNoAllocMaxDof;
+  void* pbuf = base + 2 * kNoAllocVecBytes;
+  void* qbuf = base + 4 * kNoAllocVecBytes;
+  double* part = reinterpret_cast<double*>(base + 5 * kNoAllocVecBytes);
+  double* part2 = part + 4 * kNoAllocMaxParts;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(part2 + 2 * kNoAllocMaxParts);
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(tail);
+  CGResult* res = reinterpret_cast<CGResult*>(tail + 256);
+  double h_part[2 * kNoAllocMaxParts];
+  CGResult h_res;
+  auto sums = [&](const double* dev_part, int np) {
+    DGSL_CUDA(cudaMemcpyAsync(h_part, dev_part, 2 * (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    double a = 0.0, q = 0.0;
+    for (int j = 0; j < np; ++j) {
+      a += h_part[2 * j];
+      q += h_part[2 * j + 1];
+    }
+    return std::make_pair(a, q);
+  };
+  const int mean_zero = kind == DGSL_SCHUR ? 1 : 0;
+  const double coefK = kind == DGSL_SCHUR ? coef * coef : coef;
+  const double coefM = kind == DGSL_SCHUR ? 0.0 : 1.0;
+  const uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
+  int np = 0;
+  DGSL_CUDA(launch_sum2(b, n, part2, kNoAllocMaxParts, &np, s));
+  auto sb = sums(part2, np);
+  const double b_mean = mean_zero ? sb.first / (double)n : 0.0;
+  const double bnorm2 = mean_zero ? std::max(0.0, sb.second - (double)n * b_mean * b_mean) : sb.second;
+  const double bnorm = std::sqrt(bnorm2);
+  if (!o.use_x0) DGSL_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  int iters = 0, refinements = 0, status = DGSL_OK, launches = 0, grid_used = 0, stall = 0;
+  double relres = 0.0, best = INFINITY;
+  CGWork cw;
+  cw.p = pbuf;
+  cw.q = qbuf;
+  cw.part = part;
+  cw.bar = bar;
+  cw.res = res;
+  cw.max_parts = kNoAllocMaxParts;
+  for (;;) {
+    DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, r64, part2, kNoAllocMaxParts, &np, s));
+    const double rnorm = std::sqrt(sums(part2, np).second);
+    relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (bnorm == 0.0 || relres <= o.tol) break;
+    if (iters >= o.max_iters || refinements >= o.max_refine) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+    if (relres < 0.5 * best) {
+      best = relres;
+      stall = 0;
+    } else if (++stall >= 3) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+    const int budget = o.max_iters - iters;
+    const double need = 0.5 * o.tol / relres;
+    int grid = 0;
+    if (o.precision == DGSL_PREC_F64) {
+      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, d64, r64, std::max(need, 1e-15), budget, cw, timeout_ns, s,
+                              &grid));
+    } else {
+      DGSL_CUDA(launch_scale_to_f32(r64, 1.0 / rnorm, r32, n, s));
+      DGSL_CUDA(launch_cg_f32(d, o.precision == DGSL_PREC_BF16_IR, (float)coefK, (float)coefM, mean_zero, d32, r32,
+                              std::min(1.0, std::max(o.inner_tol, need)), budget, cw, timeout_ns, s, &grid));
+    }
+    DGSL_CUDA(cudaMemcpyAsync(&h_res, res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    ++launches;
+    grid_used = grid;
+    if (h_res.status != 0) {
+      status = DGSL_ETIMEOUT;
+      break;
+    }
+    iters += h_res.iters;
+    ++refinements;
+    if (o.precision == DGSL_PREC_F64) DGSL_CUDA(launch_axpy_f64(1.0, d64, x, n, s));
+    else DGSL_CUDA(launch_axpy_f32_to_f64(rnorm, d32, x, n, s));
+    if (h_res.iters == 0) {
+      status = DGSL_ENOTCONV;
+      break;
+    }
+  }
+  if (mean_zero) {
+    DGSL_CUDA(launch_sum2(x, n, part2, kNoAllocMaxParts, &np, s));
+    DGSL_CUDA(launch_sum_to_first(part2, np, s));
+    DGSL_CUDA(launch_remove_mean_f64(x, part2, n, s));
+  }
+  DGSL_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->refinements = refinements;
+    info->cg_launches = launches;
+    info->relres = relres;
+    info->cg_kernel_ms = 0.0;
+    info->grid = grid_used;
+    info->pad = 0;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double coef, const double* b, double* x,
+                                     int n_rhs, const dgsl_solve_opts* opts, dgsl_solve_info* info, void* stream) {
+  DGSL_TRY({
+    check_dev(cop);
+    if (int e = check_vec_args(b, x, n_rhs)) return e;
+    if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
+    if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
+    if (cop->d.n > kNoAllocMaxDof)
+      return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: operator has " + std::to_string(cop->d.n) +
+                                   " DOFs, above the fixed scratch limit of " + std::to_string(kNoAllocMaxDof));
+    dgsl_solve_opts o;
+    dgsl_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
+    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (!cop->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
+    if (o.precision == DGSL_PREC_F32_IR && !cop->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+    if (o.precision == DGSL_PREC_BF16_IR && !cop->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    DGSL_CUDA(cudaSetDevice(cop->d.device));
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(cop->d.device));
+    int worst = DGSL_OK;
+    for (int k = 0; k < n_rhs; ++k) {
+      int st = solve_one_noalloc(cop->d, base, kind, coef, b + (size_t)k * cop->d.n, x + (size_t)k * cop->d.n, o,
+                                 info ? info + k : nullptr, (cudaStream_t)stream);
+      if (st != DGSL_OK && worst == DGSL_OK) worst = st;
+    }
+    if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";
+    return worst;
+  });
+}

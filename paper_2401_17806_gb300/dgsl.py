@@ -92,6 +92,9 @@ _SIGS = {
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
+    "dgsl_cg_solve_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                        C.c_int, C.POINTER(dgsl_solve_opts),
+                                        C.POINTER(dgsl_solve_info), C.c_void_p]),
 }
 
 
@@ -263,6 +266,24 @@ class Operator:
         if check and code not in (OK,):
             _check(code)
         return list(infos)
+
+
+def _noalloc_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, check=True):
+    """dgsl_cg_solve_noalloc: the solve with the library's fixed scratch array
+    (no device allocation; operators up to 262,144 DOFs)."""
+    if opts is None:
+        opts = dgsl_default_solve_opts()
+    infos = (dgsl_solve_info * n_rhs)()
+    n = self.n_dof * n_rhs
+    code = load().dgsl_cg_solve_noalloc(self.h, int(kind), float(coef), _dptr(b, "float64", n),
+                                        _dptr(x, "float64", n), int(n_rhs), C.byref(opts), infos,
+                                        _stream(stream))
+    if check and code != OK:
+        _check(code)
+    return list(infos)
+
+
+Operator.dgsl_cg_solve_noalloc = _noalloc_solve
 
 
 def solve_opts(**kw):
