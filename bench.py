@@ -32,6 +32,12 @@ if ROOT not in sys.path:
 WORKLOAD = dict(N=256, p=3, dt=1e-3, nu=1e-3, seed=0, noise=1e-2, tol=1e-10)
 METRIC = "Schur-CG DOF*iters/s"
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) per matrix row per CG iteration of the persistent
+# CG kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
+# over a 200-iteration launch, 256x256, p = 3, FP32 couplings; the capture and
+# command are summarised in profiles/k_cg_f32_256x256_p3.md).  Keyed by (p,
+# precision); a kernel change invalidates it.
+NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 173.7}
 
 
 def workload_name(args):
@@ -416,7 +422,12 @@ def main():
         "roofline": {
             "kernel": "k_cg (persistent CG, FP32 couplings)" if args.precision == "f32" else "k_cg",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None,
+            "traffic": (NCU_DRAM_BYTES_PER_ROW_ITER[(args.p, args.precision)] * op.n_dof
+                        * res["iters_total"] / max(1, res["cg_launches"])
+                        if (args.p, args.precision) in NCU_DRAM_BYTES_PER_ROW_ITER else None),
+            "traffic_unit": "bytes per launch (ncu DRAM bytes per row-iteration x rows x mean iterations per launch)",
+            "alg_bytes_per_launch": alg_bytes / max(1, res["cg_launches"]),
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
             "bytes_per_row_iter": per_row,
         },

@@ -249,7 +249,7 @@ void dgsl_default_solve_opts(dgsl_solve_opts* opts);
  * graph, real-time loops and services that reserve all device memory at start-up
  * under a fixed budget, or hosts whose own allocator owns the GPU.  This entry
  * point calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * is one fixed device array inside the library (about 10.5 MB: five vectors of
+ * is one fixed device array inside the library (about 16.8 MB: eight vectors of
  * 262,144 doubles plus reduction slots), created when the library is loaded and
  * held by every GPU that loads it until the process exits.  The paper has no
  * counterpart; this is a deployment convenience.

@@ -56,8 +56,7 @@ struct dgsl_operator {
     double* d64 = nullptr;
     float* r32 = nullptr;
     float* d32 = nullptr;
-    void* p = nullptr;   // 2n doubles (covers 2n floats)
-    void* q = nullptr;   // n doubles
+    void* vec = nullptr;  // 6n doubles (covers 6n floats): persistent CG vectors
     double* part = nullptr;
     double* part2 = nullptr;
     GridBarrier* bar = nullptr;
@@ -102,8 +101,7 @@ struct dgsl_operator {
     w.d64 = dalloc<double>(d.n);
     w.r32 = dalloc<float>(d.n);
     w.d32 = dalloc<float>(d.n);
-    w.p = dalloc<double>(2 * d.n);
-    w.q = dalloc<double>(d.n);
+    w.vec = dalloc<double>(6 * d.n);
     w.part = dalloc<double>(4 * (size_t)w.max_parts);
     w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
     w.bar = dalloc<GridBarrier>(1);
@@ -189,10 +187,13 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
     if (!o.host_only) {
       DGSL_CUDA(cudaSetDevice(o.device));
       upload_dual_tables(o.device);
-      std::vector<int32_t> cols((size_t)4 * d.ne);
+      // column rows padded to a multiple of 4 triangles: every 4-triangle group of
+      // a row starts on a 16-byte boundary (bulk copies of tile indices)
+      d.ne_pad = (d.ne + 3) / 4 * 4;
+      std::vector<int32_t> cols((size_t)4 * d.ne_pad, 0);
       for (int i = 0; i < d.ne; ++i) {
         cols[i] = i;
-        for (int b = 1; b < 4; ++b) cols[(size_t)b * d.ne + i] = hb.nbr[(size_t)i * 3 + b - 1];
+        for (int b = 1; b < 4; ++b) cols[(size_t)b * d.ne_pad + i] = hb.nbr[(size_t)i * 3 + b - 1];
       }
       d.cols = op->upload(cols);
       d.area = op->upload(hb.area);
@@ -429,8 +430,7 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
   double relres = 0.0, best = INFINITY;
   int stall = 0;
   CGWork cw;
-  cw.p = w.p;
-  cw.q = w.q;
+  cw.vec = w.vec;
   cw.part = w.part;
   cw.bar = w.bar;
   cw.res = w.res;
@@ -561,8 +561,8 @@ namespace {
 constexpr int64_t kNoAllocMaxDof = int64_t(1) << 18;   // 262,144 DOFs per right-hand side
 constexpr int kNoAllocMaxParts = 1024;                 // per-CTA partial slots
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxDof * sizeof(double);
-// r64 | d64 (also r32 + d32) | p (2 vectors) | q | part (4 slots) | part2 (2) | barrier | result
-constexpr size_t kNoAllocBytes = 5 * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
+// r64 | d64 (also r32 + d32) | 6 CG vectors | part (4 slots) | part2 (2) | barrier | result
+constexpr size_t kNoAllocBytes = 8 * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -590,9 +590,8 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   double* d64 = reinterpret_cast<double*>(base + kNoAllocVecBytes);
   float* r32 = reinterpret_cast<float*>(base + kNoAllocVecBytes);
   float* d32 = r32 + kNoAllocMaxDof;
-  void* pbuf = base + 2 * kNoAllocVecBytes;
-  void* qbuf = base + 4 * kNoAllocVecBytes;
-  double* part = reinterpret_cast<double*>(base + 5 * kNoAllocVecBytes);
+  void* vbuf = base + 2 * kNoAllocVecBytes;
+  double* part = reinterpret_cast<double*>(base + 8 * kNoAllocVecBytes);
   double* part2 = part + 4 * kNoAllocMaxParts;
   unsigned char* tail = reinterpret_cast<unsigned char*>(part2 + 2 * kNoAllocMaxParts);
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(tail);
@@ -623,8 +622,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   int iters = 0, refinements = 0, status = DGSL_OK, launches = 0, grid_used = 0, stall = 0;
   double relres = 0.0, best = INFINITY;
   CGWork cw;
-  cw.p = pbuf;
-  cw.q = qbuf;
+  cw.vec = vbuf;
   cw.part = part;
   cw.bar = bar;
   cw.res = res;

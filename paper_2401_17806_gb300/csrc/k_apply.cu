@@ -112,7 +112,7 @@ cudaError_t launch_apply_assembled_f64(const DevOp& op, double coefK, double coe
                                        cudaStream_t s) {
   if (!op.K64) return cudaErrorInvalidValue;
   const int g = grid_for(op.n);
-  DGSL_DISPATCH_P(op.p, (void)NPSI; k_assembled_f64<NPHI><<<g, 256, 0, s>>>(op.K64, op.cols, op.ne, op.n, op.area,
+  DGSL_DISPATCH_P(op.p, (void)NPSI; k_assembled_f64<NPHI><<<g, 256, 0, s>>>(op.K64, op.cols, op.ne_pad, op.n, op.area,
                                                                              op.Mref, coefK, coefM, x, y));
   count_launch();
   return cudaGetLastError();
@@ -121,7 +121,7 @@ cudaError_t launch_apply_assembled_f64(const DevOp& op, double coefK, double coe
 cudaError_t launch_apply_assembled_f32(const DevOp& op, float coefK, const float* x, float* y, cudaStream_t s) {
   if (!op.K32) return cudaErrorInvalidValue;
   const int g = grid_for(op.n);
-  DGSL_DISPATCH_P(op.p, (void)NPSI; k_assembled_f32<NPHI><<<g, 256, 0, s>>>(op.K32, op.cols, op.ne, op.n, coefK, x, y));
+  DGSL_DISPATCH_P(op.p, (void)NPSI; k_assembled_f32<NPHI><<<g, 256, 0, s>>>(op.K32, op.cols, op.ne_pad, op.n, coefK, x, y));
   count_launch();
   return cudaGetLastError();
 }
@@ -399,7 +399,7 @@ cudaError_t launch_residual_f64(const DevOp& op, double coefK, double coefM, int
   const int g = std::min(grid_for(op.n), max_parts);
   *nparts = g;
   const double shift = mean_zero ? b_mean : 0.0;
-  DGSL_DISPATCH_P(op.p, (void)NPSI; k_residual_f64<NPHI><<<g, 256, 0, s>>>(op.K64, op.cols, op.ne, op.n, op.area,
+  DGSL_DISPATCH_P(op.p, (void)NPSI; k_residual_f64<NPHI><<<g, 256, 0, s>>>(op.K64, op.cols, op.ne_pad, op.n, op.area,
                                                                             op.Mref, coefK, coefM, b, shift, x, r, part));
   count_launch();
   return cudaGetLastError();

@@ -22,52 +22,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Barrier state in device memory: count of arrivals and a generation word.
+// Barrier state in device memory (zeroed before every persistent launch):
+// a monotonic arrival counter, the epoch released by the last arriver of a
+// reducing barrier, the first error any CTA recorded, and the reduced totals.
 struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-  int status;      // kStatusOk, or the first error any CTA recorded
+  unsigned long long count;
+  unsigned long long gen;
+  int status;
   int pad;
+  double total[4];
 };
-
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The wait
-// is bounded: after timeout_ns the CTA records kStatusTimeout and returns
-// false; CTAs waiting elsewhere see the status and return false as well.
-// Every CTA must call it the same number of times.
-__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned int nblocks, uint64_t timeout_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &b->gen;
-    volatile int* vst = &b->status;
-    unsigned int g = *vgen;
-    __threadfence();
-    unsigned int arrived = atomicAdd(&b->count, 1u);
-    int ok = 1;
-    if (arrived == nblocks - 1) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      uint64_t t0 = globaltimer_ns();
-      unsigned int spins = 0;
-      while (*vgen == g) {
-        if (*vst != kStatusOk) { ok = 0; break; }
-        if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
-          atomicCAS(&b->status, kStatusOk, kStatusTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*vst != kStatusOk) ok = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 // Sum of v over the block (blockDim.x a multiple of 32, <= 1024).  The
 // summation order is fixed by thread index, so it is deterministic.
@@ -116,6 +80,66 @@ __device__ __forceinline__ void sum_partials(const double* part, int nparts, dou
 #pragma unroll
   for (int i = 0; i < NV; ++i) out[i] = s_tot[i];
   __syncthreads();
+}
+
+// ---- TMA bulk copies (non-tensor) with mbarrier completion, CTA scope.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Orders prior generic-proxy accesses of shared memory before later async-proxy
+// (TMA) accesses, and makes mbarrier initialisation visible to the async proxy.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// L2 policy for data streamed once per use (evicted first, so that data
+// reused across CTAs, e.g. the CG vectors, stays resident).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bulk_g2s with an L2 cache-eviction hint for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for phase `parity` of `bar`; false after timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (unsigned spins = 1;; ++spins) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spins & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) return false;
+  }
 }
 
 }  // namespace dgsl

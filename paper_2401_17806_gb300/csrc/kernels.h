@@ -20,7 +20,8 @@ struct DevOp {
   int p = 0, nphi = 0, npsi = 0, ne = 0, nd = 0, ncol = 0;
   int64_t n = 0;                   // n_dof
   int device = 0;
-  int32_t* cols = nullptr;         // [4][ne]
+  int ne_pad = 0;                  // row stride of cols: ne rounded up to a multiple of 4
+  int32_t* cols = nullptr;         // [4][ne_pad] (padding entries are 0)
   double* K64 = nullptr;           // assembled, FP64
   float* K32 = nullptr;            // assembled, FP32
   uint16_t* K16 = nullptr;         // assembled, BF16 bits
@@ -69,8 +70,8 @@ cudaError_t launch_sum_to_first(double* part, int nparts, cudaStream_t s);
 
 // ---- persistent conjugate gradients (cooperative launch)
 // Solves A d = r0 from d = 0 with A = coefM Mbar + coefK K (assembled form in
-// the vector type's precision).  r0 is consumed (r holds the final residual).
-// Iterates until r.r <= stop_rr or max_iters.  Result words in `res`:
+// the vector type's precision).  r0 is consumed.  Iterates until
+// ||r|| <= stop_rel ||r0|| or max_iters.  Result words in `res`:
 //   res->iters, res->rr (final recursive r.r), res->status.
 struct CGResult {
   int iters;
@@ -79,9 +80,8 @@ struct CGResult {
   double rr;
 };
 struct CGWork {
-  void* p = nullptr;      // 2 x n vectors (double buffered search direction)
-  void* q = nullptr;      // n
-  double* part = nullptr; // 2 x max_parts x 2
+  void* vec = nullptr;    // 6 n vector elements: p, second r buffer, w and s double-buffered
+  double* part = nullptr; // max_parts x 4 partial sums
   GridBarrier* bar = nullptr;
   CGResult* res = nullptr;
   int max_parts = 0;
