@@ -268,6 +268,72 @@ int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const 
                           double* x, int n_rhs, const dgsl_solve_opts* opts,
                           dgsl_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------ batched engine and serving */
+/* One solve request: op's Schur (coef = dt) or Helmholtz (coef = nu*dt)
+ * system, b and x device double[n_dof] in op's internal order (caller-owned,
+ * kept alive until the request completes).  tol <= 0 selects 1e-10.  Several
+ * right-hand sides of one operator are several requests. */
+typedef struct {
+  const dgsl_operator* op;
+  int32_t kind;
+  int32_t pad;
+  double coef;
+  const double* b;
+  double* x;
+  double tol;
+} dgsl_request;
+
+typedef struct {
+  int32_t precision;        /* DGSL_PREC_F32_IR (default) or DGSL_PREC_BF16_IR */
+  int32_t max_iters;        /* CG iterations per request (default 200000) */
+  double inner_tol;         /* inner FP32 CG tolerance (default 1e-4) */
+  int32_t max_refine;       /* refinement steps per request (default 30) */
+  int32_t device;           /* CUDA device (all operators must live there) */
+  int64_t hbm_budget_bytes; /* server: cap on workspace + resident operators (0 = 150e9) */
+  int64_t idle_us;          /* server: how long an idle engine waits for work (default 500) */
+} dgsl_engine_opts;
+
+void dgsl_default_engine_opts(dgsl_engine_opts* opts);
+
+/* Solves n independent requests (any operators, degrees and sizes on one
+ * device) in ONE persistent cooperative launch: each request runs its own FP64
+ * iterative refinement around an FP32 (or BF16-coupling) Chronopoulos-Gear CG
+ * (eq. pressure_final / eq. ad5), all requests advancing together with one grid
+ * barrier per pass.  Results and errors per request in infos[n] (host), as for
+ * dgsl_cg_solve.  Blocks until all requests finish; allocates its workspace for
+ * the call.  n <= 1024.  The BF16 path needs operators built with
+ * DGSL_STORE_BF16.  Returns the first non-OK request status, else DGSL_OK. */
+int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_engine_opts* opts,
+                        dgsl_solve_info* infos, void* stream);
+
+/* Serving: a request loop with continuous batching.  dgsl_submit queues a
+ * request and returns at once; a scheduler thread admits queued requests while
+ * their workspace plus every operator they reference fits hbm_budget_bytes,
+ * publishes them to the running persistent engine (which picks them up at its
+ * next pass, overlapping them with the solves already on the device) or
+ * launches one, and collects completions.  The workspace arena is reserved at
+ * create time, so no device allocation happens while the engine runs.
+ * Errors: DGSL_EBUDGET from dgsl_submit if a request can never fit. */
+typedef struct dgsl_server dgsl_server;
+typedef struct {
+  int64_t submitted, completed, queued, in_flight;
+  int64_t engine_launches;
+  int64_t bytes_in_use;     /* workspace + operators of requests in flight */
+} dgsl_server_stats;
+
+int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** out);
+int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* ticket);
+/* DGSL_OK (info filled; the request's final status is info->status),
+ * DGSL_EPENDING, or DGSL_EINVAL for an unknown ticket.  A ticket can be polled
+ * until it is reported done once; after that it is forgotten. */
+int dgsl_poll(dgsl_server* srv, uint64_t ticket, dgsl_solve_info* info);
+/* Removes a request that has not been admitted yet (DGSL_OK); an admitted one
+ * runs to completion (DGSL_EPENDING). */
+int dgsl_cancel(dgsl_server* srv, uint64_t ticket);
+int dgsl_server_get_stats(dgsl_server* srv, dgsl_server_stats* out);
+/* Waits for requests in flight, stops the engine and frees the server. */
+void dgsl_server_destroy(dgsl_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

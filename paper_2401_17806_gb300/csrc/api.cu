@@ -12,6 +12,7 @@
 
 #include "host.h"
 #include "kernels.h"
+#include "operator.h"
 
 using namespace dgsl;
 
@@ -22,12 +23,11 @@ int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+}  // namespace
 
-#define DGSL_CUDA(expr)                                                                   \
-  do {                                                                                    \
-    cudaError_t e_ = (expr);                                                              \
-    if (e_ != cudaSuccess) throw Error(DGSL_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
+void dgsl_set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
 
 uint16_t f32_to_bf16_bits(float f) {
   uint32_t u;
@@ -38,80 +38,6 @@ uint16_t f32_to_bf16_bits(float f) {
   return (uint16_t)(u >> 16);
 }
 }  // namespace
-
-struct dgsl_operator {
-  HostMesh hm;
-  RefOps ro;
-  HostBlocks hb;      // kept for host queries (host_only or factored builds)
-  bool have_blocks = false;
-  int host_only = 0;
-  DevOp d;
-  std::vector<void*> allocs;
-  int64_t device_bytes = 0;
-  std::mutex mu;
-  // solve workspace (grown on demand)
-  struct Work {
-    int64_t n = 0;
-    double* r64 = nullptr;
-    double* d64 = nullptr;
-    float* r32 = nullptr;
-    float* d32 = nullptr;
-    void* vec = nullptr;  // 6n doubles (covers 6n floats): persistent CG vectors
-    double* part = nullptr;
-    double* part2 = nullptr;
-    GridBarrier* bar = nullptr;
-    CGResult* res = nullptr;
-    double* h_part = nullptr;   // pinned
-    CGResult* h_res = nullptr;  // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int max_parts = 0;
-  } w;
-
-  template <class T>
-  T* dalloc(size_t count) {
-    void* p = nullptr;
-    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) throw Error(DGSL_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    allocs.push_back(p);
-    device_bytes += (int64_t)bytes;
-    return static_cast<T*>(p);
-  }
-  template <class T>
-  T* upload(const std::vector<T>& v) {
-    T* p = dalloc<T>(v.size());
-    if (!v.empty()) DGSL_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return p;
-  }
-  ~dgsl_operator() {
-    if (!host_only) {
-      cudaSetDevice(d.device);
-      for (void* p : allocs) cudaFree(p);
-      if (w.h_part) cudaFreeHost(w.h_part);
-      if (w.h_res) cudaFreeHost(w.h_res);
-      if (w.ev0) cudaEventDestroy(w.ev0);
-      if (w.ev1) cudaEventDestroy(w.ev1);
-    }
-  }
-  void ensure_work() {
-    if (w.n == d.n && w.r64) return;
-    w.n = d.n;
-    w.max_parts = cg_max_blocks(d, 0);
-    w.r64 = dalloc<double>(d.n);
-    w.d64 = dalloc<double>(d.n);
-    w.r32 = dalloc<float>(d.n);
-    w.d32 = dalloc<float>(d.n);
-    w.vec = dalloc<double>(6 * d.n);
-    w.part = dalloc<double>(4 * (size_t)w.max_parts);
-    w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
-    w.bar = dalloc<GridBarrier>(1);
-    w.res = dalloc<CGResult>(1);
-    DGSL_CUDA(cudaMallocHost(&w.h_part, 2 * (size_t)w.max_parts * sizeof(double)));
-    DGSL_CUDA(cudaMallocHost(&w.h_res, sizeof(CGResult)));
-    DGSL_CUDA(cudaEventCreate(&w.ev0));
-    DGSL_CUDA(cudaEventCreate(&w.ev1));
-  }
-};
 
 namespace {
 

@@ -1,0 +1,83 @@
+// Host/device interface of the batched persistent solver engine (k_batch.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgsl {
+
+constexpr int kMaxSlots = 1024;       // slots per engine (admitted over its lifetime)
+
+// One solve, written by the host and copied into device memory when the engine
+// admits it.  All pointers are device pointers (the inbox itself is mapped host
+// memory).  fvec holds 8 n floats: r0 | d | p | r1 | w0 | w1 | s0 | s1.
+struct BSlotDesc {
+  int p, ne, ne_pad, mean_zero;
+  long long n;
+  const double* K64;        // FP64 couplings (refinement residual)
+  const void* Kin;          // inner couplings, float or bf16 bits (engine type)
+  const int32_t* cols;
+  const double* area;
+  const double* Mref;
+  double coefK, coefM;
+  const double* b;
+  double* x;
+  double* r64;
+  float* fvec;
+  double* part;             // [nchunk][4]
+  double tol, inner_tol;
+  int max_iters, max_refine;
+  int nchunk, chunk_tris;
+  long long ticket;
+};
+
+// Completion record of a slot (mapped host memory, written once by the engine).
+struct BCompletion {
+  int done;                 // 0 while pending; 1 when the fields below are final
+  int status;               // DGSL_OK / DGSL_ENOTCONV / DGSL_ETIMEOUT
+  int iters;
+  int refinements;
+  double relres;
+  long long ticket;
+};
+
+// Mapped host inbox: the host writes slots[count .. ] then publishes count
+// with a release store; the engine admits them at its next barrier.
+struct BInbox {
+  int count;
+  int stop;                 // host asks a running engine to exit when idle
+  int pad[2];
+  BSlotDesc slots[kMaxSlots];
+};
+
+struct EngineShared;
+struct BState;
+
+struct EngineParams {
+  BInbox* inbox;            // device view of the mapped inbox
+  BCompletion* done;        // device view of the mapped completion records [kMaxSlots]
+  BSlotDesc* slots;         // device copies [kMaxSlots]
+  BState* state;            // [kMaxSlots]
+  EngineShared* sh;
+  int* act_slot;            // [kMaxSlots]
+  int* act_chunk0;          // [kMaxSlots + 1]
+  uint64_t timeout_ns;      // bound of every device wait
+  uint64_t idle_ns;         // how long an idle engine waits for new slots before exiting
+};
+
+// Triangles per chunk for degree p (a multiple of the CG tile, itself a
+// multiple of 4 triangles).
+int engine_chunk_tris(int p);
+// Device bytes of the engine-owned areas (slot copies, state, shared words,
+// lists) and their layout inside one allocation of that size.
+size_t engine_state_bytes();
+void engine_layout(void* base, EngineParams& P);
+// EngineShared (zeroed before every launch) and the fields the host reads back.
+size_t engine_shared_bytes();
+int engine_shared_status(const void* sh_host_copy);
+int engine_shared_admitted(const void* sh_host_copy);
+// Launches the engine (cooperative) on `s`; `bf16` selects the inner coupling
+// type.  The caller zeroes EngineShared before the launch.
+cudaError_t launch_engine(const EngineParams& e, int bf16, cudaStream_t s, int* grid_used);
+
+}  // namespace dgsl

@@ -1,0 +1,500 @@
+// C-ABI of the batched engine (dgsl_cg_solve_batch) and of the request loop
+// (dgsl_server_*): host-side admission by memory budget, publication to the
+// persistent engine through a mapped inbox, completion collection.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <thread>
+#include <unordered_map>
+
+#include "kbatch.h"
+#include "operator.h"
+
+using namespace dgsl;
+
+namespace {
+
+// Engine resources on one device: mapped inbox and completion records, device
+// slot table / state / lists.
+struct EngineRes {
+  int device = -1;
+  BInbox* inbox_h = nullptr;
+  BInbox* inbox_d = nullptr;
+  BCompletion* done_h = nullptr;
+  BCompletion* done_d = nullptr;
+  void* area = nullptr;
+  EngineParams P{};
+  ~EngineRes() {
+    if (device < 0) return;
+    cudaSetDevice(device);
+    if (inbox_h) cudaFreeHost(inbox_h);
+    if (done_h) cudaFreeHost(done_h);
+    if (area) cudaFree(area);
+  }
+  void init(int dev) {
+    device = dev;
+    DGSL_CUDA(cudaSetDevice(dev));
+    DGSL_CUDA(cudaHostAlloc(&inbox_h, sizeof(BInbox), cudaHostAllocMapped));
+    DGSL_CUDA(cudaHostGetDevicePointer((void**)&inbox_d, inbox_h, 0));
+    DGSL_CUDA(cudaHostAlloc(&done_h, sizeof(BCompletion) * kMaxSlots, cudaHostAllocMapped));
+    DGSL_CUDA(cudaHostGetDevicePointer((void**)&done_d, done_h, 0));
+    std::memset(inbox_h, 0, sizeof(BInbox));
+    std::memset(done_h, 0, sizeof(BCompletion) * kMaxSlots);
+    DGSL_CUDA(cudaMalloc(&area, engine_state_bytes()));
+    engine_layout(area, P);
+    P.inbox = inbox_d;
+    P.done = done_d;
+    P.timeout_ns = 10ull * 1000 * 1000 * 1000;
+    P.idle_ns = 0;
+  }
+  cudaError_t launch(int bf16, uint64_t idle_ns, cudaStream_t s, int* grid) {
+    cudaError_t e = cudaMemsetAsync(P.sh, 0, engine_shared_bytes(), s);
+    if (e != cudaSuccess) return e;
+    EngineParams q = P;
+    q.idle_ns = idle_ns;
+    return launch_engine(q, bf16, s, grid);
+  }
+};
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Device workspace of one request: r64 (8n) | fvec (32n) | partials (32 per chunk).
+size_t request_workspace(const dgsl_operator* op) {
+  const int64_t n = op->d.n;
+  const int ct = engine_chunk_tris(op->d.p);
+  const int nchunk = (op->d.ne + ct - 1) / ct;
+  return align256(8 * (size_t)n) + align256(32 * (size_t)n) + align256(32 * (size_t)nchunk);
+}
+
+int check_request(const dgsl_request& r, const dgsl_engine_opts& o, std::string& why) {
+  if (!r.op) return why = "request has no operator", DGSL_EINVAL;
+  if (r.op->host_only) return why = "operator was built host-only", DGSL_ENODEVICE;
+  if (r.op->d.device != o.device) return why = "operator lives on another device", DGSL_EINVAL;
+  if (!r.b || !r.x) return why = "request vectors must be non-NULL", DGSL_EINVAL;
+  if (r.kind != DGSL_SCHUR && r.kind != DGSL_HELMHOLTZ) return why = "bad request kind", DGSL_EINVAL;
+  if (!(r.coef >= 0.0) || !std::isfinite(r.coef)) return why = "coef must be finite and >= 0", DGSL_EINVAL;
+  if (!r.op->d.K64) return why = "FP64 couplings are needed", DGSL_EINVAL;
+  if (o.precision == DGSL_PREC_BF16_IR ? !r.op->d.K16 : !r.op->d.K32)
+    return why = "operator lacks the couplings of the engine precision", DGSL_EINVAL;
+  return DGSL_OK;
+}
+
+BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, uint64_t ticket) {
+  const DevOp& d = r.op->d;
+  BSlotDesc s{};
+  s.p = d.p;
+  s.ne = d.ne;
+  s.ne_pad = d.ne_pad;
+  s.mean_zero = r.kind == DGSL_SCHUR;
+  s.n = d.n;
+  s.K64 = d.K64;
+  s.Kin = o.precision == DGSL_PREC_BF16_IR ? (const void*)d.K16 : (const void*)d.K32;
+  s.cols = d.cols;
+  s.area = d.area;
+  s.Mref = d.Mref;
+  s.coefK = r.kind == DGSL_SCHUR ? r.coef * r.coef : r.coef;
+  s.coefM = r.kind == DGSL_SCHUR ? 0.0 : 1.0;
+  s.b = r.b;
+  s.x = r.x;
+  s.r64 = reinterpret_cast<double*>(ws);
+  s.fvec = reinterpret_cast<float*>(ws + align256(8 * (size_t)d.n));
+  s.part = reinterpret_cast<double*>(ws + align256(8 * (size_t)d.n) + align256(32 * (size_t)d.n));
+  s.tol = r.tol > 0.0 ? r.tol : 1e-10;
+  s.inner_tol = o.inner_tol;
+  s.max_iters = o.max_iters;
+  s.max_refine = o.max_refine;
+  s.chunk_tris = engine_chunk_tris(d.p);
+  s.nchunk = (d.ne + s.chunk_tris - 1) / s.chunk_tris;
+  s.ticket = (long long)ticket;
+  return s;
+}
+
+void info_from(const BCompletion& c, dgsl_solve_info* info) {
+  info->status = c.status;
+  info->iters = c.iters;
+  info->refinements = c.refinements;
+  info->cg_launches = 1;
+  info->relres = c.relres;
+  info->cg_kernel_ms = 0.0;
+  info->grid = 0;
+  info->pad = 0;
+}
+
+std::mutex g_batch_mu;
+std::map<int, std::unique_ptr<EngineRes>> g_batch_engines;
+
+}  // namespace
+
+extern "C" void dgsl_default_engine_opts(dgsl_engine_opts* o) {
+  if (!o) return;
+  o->precision = DGSL_PREC_F32_IR;
+  o->max_iters = 200000;
+  o->inner_tol = 1e-4;
+  o->max_refine = 30;
+  o->device = 0;
+  o->hbm_budget_bytes = 150000000000LL;
+  o->idle_us = 500;
+}
+
+extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_engine_opts* opts,
+                                   dgsl_solve_info* infos, void* stream) {
+  dgsl_engine_opts o;
+  dgsl_default_engine_opts(&o);
+  if (opts) o = *opts;
+  try {
+    if (!reqs || n < 1 || n > kMaxSlots) throw Error(DGSL_EINVAL, "need 1..1024 requests");
+    if (o.precision != DGSL_PREC_F32_IR && o.precision != DGSL_PREC_BF16_IR)
+      throw Error(DGSL_EINVAL, "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR");
+    if (!(o.inner_tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) throw Error(DGSL_EINVAL, "bad engine options");
+    std::string why;
+    for (int i = 0; i < n; ++i)
+      if (int e = check_request(reqs[i], o, why)) throw Error(e, "request " + std::to_string(i) + ": " + why);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    DGSL_CUDA(cudaSetDevice(o.device));
+    auto& R = g_batch_engines[o.device];
+    if (!R) {
+      R = std::make_unique<EngineRes>();
+      R->init(o.device);
+    }
+    std::vector<size_t> off(n);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+      off[i] = total;
+      total += request_workspace(reqs[i].op);
+    }
+    char* ws = nullptr;
+    if (cudaMalloc(&ws, total) != cudaSuccess) throw Error(DGSL_ENOMEM, "batch workspace allocation failed");
+    std::unique_ptr<char, void (*)(char*)> guard(ws, [](char* q) { cudaFree(q); });
+    for (int i = 0; i < n; ++i) R->inbox_h->slots[i] = fill_desc(reqs[i], o, ws + off[i], (uint64_t)i);
+    std::memset(R->done_h, 0, sizeof(BCompletion) * kMaxSlots);
+    R->inbox_h->stop = 1;
+    std::atomic_thread_fence(std::memory_order_release);
+    R->inbox_h->count = n;
+    cudaStream_t s = (cudaStream_t)stream;
+    int grid = 0;
+    DGSL_CUDA(R->launch(o.precision == DGSL_PREC_BF16_IR, 0, s, &grid));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    std::vector<char> sh(engine_shared_bytes());
+    DGSL_CUDA(cudaMemcpy(sh.data(), R->P.sh, sh.size(), cudaMemcpyDeviceToHost));
+    const int engine_status = engine_shared_status(sh.data());
+    int worst = DGSL_OK;
+    for (int i = 0; i < n; ++i) {
+      BCompletion c = R->done_h[i];
+      dgsl_solve_info tmp;
+      if (!c.done) {
+        std::memset(&tmp, 0, sizeof(tmp));
+        tmp.status = engine_status ? DGSL_ETIMEOUT : DGSL_ENOTCONV;
+      } else {
+        info_from(c, &tmp);
+      }
+      tmp.grid = grid;
+      if (infos) infos[i] = tmp;
+      if (tmp.status != DGSL_OK && worst == DGSL_OK) worst = tmp.status;
+    }
+    R->inbox_h->count = 0;
+    R->inbox_h->stop = 0;
+    if (worst != DGSL_OK) dgsl_set_last_error("at least one request did not converge (see infos)");
+    return worst;
+  } catch (const Error& e) {
+    dgsl_set_last_error(e.what());
+    return e.code;
+  }
+}
+
+// ------------------------------------------------------------ request loop
+
+namespace {
+
+// First-fit allocator over the server's device workspace arena (host-side
+// bookkeeping only; the arena is one allocation made at create time).
+struct Arena {
+  char* base = nullptr;
+  size_t bytes = 0;
+  std::map<size_t, size_t> free_;  // offset -> size
+  void init(char* b, size_t n) {
+    base = b;
+    bytes = n;
+    free_.clear();
+    free_[0] = n;
+  }
+  char* alloc(size_t n) {
+    n = align256(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        const size_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > n) free_[off + n] = sz - n;
+        return base + off;
+      }
+    return nullptr;
+  }
+  void release(char* p, size_t n) {
+    n = align256(n);
+    size_t off = (size_t)(p - base);
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+};
+
+enum { RQ_QUEUED = 0, RQ_ADMITTED = 1, RQ_DONE = 2 };
+
+struct Request {
+  dgsl_request r{};
+  uint64_t ticket = 0;
+  int state = RQ_QUEUED;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  dgsl_solve_info info{};
+};
+
+}  // namespace
+
+struct dgsl_server {
+  dgsl_engine_opts o{};
+  EngineRes R;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t exited = nullptr;
+  Arena arena;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread th;
+  bool stopping = false;
+  uint64_t next_ticket = 1;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::deque<uint64_t> queue;
+  std::unordered_map<const dgsl_operator*, int> op_refs;  // operators of requests in flight
+  int64_t bytes_in_use = 0;
+  bool running = false;
+  int published = 0;                      // slots published to the current launch
+  std::vector<uint64_t> slot_ticket;      // [kMaxSlots]
+  std::vector<char> collected;            // [kMaxSlots]
+  int64_t submitted = 0, completed = 0, launches = 0;
+
+  int64_t op_cost(const dgsl_operator* op) const { return op_refs.count(op) ? 0 : op->device_bytes; }
+
+  void finish(Request& q) {
+    arena.release(q.ws, q.ws_bytes);
+    bytes_in_use -= (int64_t)q.ws_bytes;
+    if (--op_refs[q.r.op] == 0) {
+      bytes_in_use -= q.r.op->device_bytes;
+      op_refs.erase(q.r.op);
+    }
+    q.state = RQ_DONE;
+    ++completed;
+  }
+
+  // One scheduling round (called with mu held).
+  void round() {
+    // 1. engine exit: requeue slots it never admitted, reset the inbox
+    if (running && cudaEventQuery(exited) == cudaSuccess) {
+      running = false;
+      std::vector<char> sh(engine_shared_bytes());
+      cudaMemcpy(sh.data(), R.P.sh, sh.size(), cudaMemcpyDeviceToHost);
+      const int admitted = engine_shared_admitted(sh.data());
+      collect();
+      for (int i = published - 1; i >= admitted; --i) {
+        Request& q = reqs[slot_ticket[i]];
+        arena.release(q.ws, q.ws_bytes);
+        bytes_in_use -= (int64_t)q.ws_bytes;
+        if (--op_refs[q.r.op] == 0) {
+          bytes_in_use -= q.r.op->device_bytes;
+          op_refs.erase(q.r.op);
+        }
+        q.ws = nullptr;
+        q.state = RQ_QUEUED;
+        queue.push_front(q.ticket);
+      }
+      published = 0;
+      std::memset(R.done_h, 0, sizeof(BCompletion) * kMaxSlots);
+      std::fill(collected.begin(), collected.end(), 0);
+      R.inbox_h->stop = 0;
+      std::atomic_thread_fence(std::memory_order_release);
+      *((volatile int*)&R.inbox_h->count) = 0;
+    }
+    collect();
+    // 2. admission under the budget
+    int added = 0;
+    while (!queue.empty() && published < kMaxSlots) {
+      Request& q = reqs[queue.front()];
+      const int64_t need = (int64_t)q.ws_bytes + op_cost(q.r.op);
+      if (bytes_in_use + need > o.hbm_budget_bytes) break;
+      char* ws = arena.alloc(q.ws_bytes);
+      if (!ws) break;
+      q.ws = ws;
+      bytes_in_use += need;
+      ++op_refs[q.r.op];
+      q.state = RQ_ADMITTED;
+      R.inbox_h->slots[published] = fill_desc(q.r, o, ws, q.ticket);
+      slot_ticket[published] = q.ticket;
+      ++published;
+      ++added;
+      queue.pop_front();
+    }
+    if (added) {
+      std::atomic_thread_fence(std::memory_order_release);
+      *((volatile int*)&R.inbox_h->count) = published;
+    }
+    if (published >= kMaxSlots) R.inbox_h->stop = 1;  // drain this launch, then start a new one
+    // 3. launch when there is published work and no engine
+    if (!running && published > 0) {
+      int grid = 0;
+      if (R.launch(o.precision == DGSL_PREC_BF16_IR, (uint64_t)o.idle_us * 1000ull, stream, &grid) == cudaSuccess &&
+          cudaEventRecord(exited, stream) == cudaSuccess) {
+        running = true;
+        ++launches;
+      }
+    }
+  }
+
+  void collect() {
+    for (int i = 0; i < published; ++i) {
+      if (collected[i]) continue;
+      if (!*((volatile int*)&R.done_h[i].done)) continue;
+      std::atomic_thread_fence(std::memory_order_acquire);
+      Request& q = reqs[slot_ticket[i]];
+      info_from(R.done_h[i], &q.info);
+      collected[i] = 1;
+      finish(q);
+    }
+  }
+
+  void loop() {
+    std::unique_lock<std::mutex> lk(mu);
+    while (true) {
+      round();
+      if (stopping && queue.empty() && !running) break;
+      cv.wait_for(lk, std::chrono::microseconds(running ? 20 : 200));
+    }
+  }
+};
+
+extern "C" int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** out) {
+  if (!out) return dgsl_set_last_error("out must be non-NULL"), DGSL_EINVAL;
+  *out = nullptr;
+  try {
+    auto s = std::make_unique<dgsl_server>();
+    dgsl_default_engine_opts(&s->o);
+    if (opts) s->o = *opts;
+    if (s->o.hbm_budget_bytes <= 0) s->o.hbm_budget_bytes = 150000000000LL;
+    if (s->o.precision != DGSL_PREC_F32_IR && s->o.precision != DGSL_PREC_BF16_IR)
+      throw Error(DGSL_EINVAL, "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR");
+    if (s->o.idle_us < 0 || s->o.idle_us > 1000000) throw Error(DGSL_EINVAL, "idle_us must be in [0, 1e6]");
+    s->R.init(s->o.device);
+    DGSL_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    DGSL_CUDA(cudaEventCreateWithFlags(&s->exited, cudaEventDisableTiming));
+    // workspace arena: the budget minus nothing (operators are owned by the
+    // caller), capped by the memory free on the device
+    size_t free_b = 0, total_b = 0;
+    DGSL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t want = std::min((size_t)s->o.hbm_budget_bytes, free_b / 10 * 9);
+    char* base = nullptr;
+    if (cudaMalloc(&base, want) != cudaSuccess) throw Error(DGSL_ENOMEM, "server workspace arena allocation failed");
+    s->arena.init(base, want);
+    s->slot_ticket.assign(kMaxSlots, 0);
+    s->collected.assign(kMaxSlots, 0);
+    dgsl_server* raw = s.get();
+    s->th = std::thread([raw] { raw->loop(); });
+    *out = s.release();
+    return DGSL_OK;
+  } catch (const Error& e) {
+    dgsl_set_last_error(e.what());
+    return e.code;
+  }
+}
+
+extern "C" int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* ticket) {
+  if (!srv || !req || !ticket) return dgsl_set_last_error("NULL argument"), DGSL_EINVAL;
+  std::string why;
+  if (int e = check_request(*req, srv->o, why)) return dgsl_set_last_error(why), e;
+  Request q;
+  q.r = *req;
+  q.ws_bytes = request_workspace(req->op);
+  if ((int64_t)q.ws_bytes + req->op->device_bytes > srv->o.hbm_budget_bytes ||
+      q.ws_bytes > srv->arena.bytes)
+    return dgsl_set_last_error("request can never fit the memory budget"), DGSL_EBUDGET;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    q.ticket = srv->next_ticket++;
+    *ticket = q.ticket;
+    srv->queue.push_back(q.ticket);
+    srv->reqs.emplace(q.ticket, q);
+    ++srv->submitted;
+  }
+  srv->cv.notify_one();
+  return DGSL_OK;
+}
+
+extern "C" int dgsl_poll(dgsl_server* srv, uint64_t ticket, dgsl_solve_info* info) {
+  if (!srv) return dgsl_set_last_error("NULL server"), DGSL_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return dgsl_set_last_error("unknown ticket"), DGSL_EINVAL;
+  if (it->second.state != RQ_DONE) return DGSL_EPENDING;
+  if (info) *info = it->second.info;
+  srv->reqs.erase(it);
+  return DGSL_OK;
+}
+
+extern "C" int dgsl_cancel(dgsl_server* srv, uint64_t ticket) {
+  if (!srv) return dgsl_set_last_error("NULL server"), DGSL_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return dgsl_set_last_error("unknown ticket"), DGSL_EINVAL;
+  if (it->second.state != RQ_QUEUED) return DGSL_EPENDING;
+  for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+    if (*q == ticket) {
+      srv->queue.erase(q);
+      break;
+    }
+  srv->reqs.erase(it);
+  return DGSL_OK;
+}
+
+extern "C" int dgsl_server_get_stats(dgsl_server* srv, dgsl_server_stats* out) {
+  if (!srv || !out) return dgsl_set_last_error("NULL argument"), DGSL_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  out->submitted = srv->submitted;
+  out->completed = srv->completed;
+  out->queued = (int64_t)srv->queue.size();
+  out->in_flight = srv->submitted - srv->completed - (int64_t)srv->queue.size();
+  out->engine_launches = srv->launches;
+  out->bytes_in_use = srv->bytes_in_use;
+  return DGSL_OK;
+}
+
+extern "C" void dgsl_server_destroy(dgsl_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stopping = true;
+    srv->R.inbox_h->stop = 1;
+  }
+  srv->cv.notify_one();
+  if (srv->th.joinable()) srv->th.join();
+  cudaSetDevice(srv->o.device);
+  cudaStreamSynchronize(srv->stream);
+  cudaFree(srv->arena.base);
+  cudaEventDestroy(srv->exited);
+  cudaStreamDestroy(srv->stream);
+  delete srv;
+}

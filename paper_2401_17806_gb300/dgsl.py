@@ -67,6 +67,22 @@ class dgsl_solve_info(C.Structure):
                 ("grid", C.c_int32), ("pad", C.c_int32)]
 
 
+class dgsl_request(C.Structure):
+    _fields_ = [("op", C.c_void_p), ("kind", C.c_int32), ("pad", C.c_int32), ("coef", C.c_double),
+                ("b", C.c_void_p), ("x", C.c_void_p), ("tol", C.c_double)]
+
+
+class dgsl_engine_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iters", C.c_int32), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int32), ("device", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("idle_us", C.c_int64)]
+
+
+class dgsl_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
+                ("in_flight", C.c_int64), ("engine_launches", C.c_int64), ("bytes_in_use", C.c_int64)]
+
+
 _LIB = None
 
 _SIGS = {
@@ -92,6 +108,15 @@ _SIGS = {
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
+    "dgsl_default_engine_opts": (None, [C.POINTER(dgsl_engine_opts)]),
+    "dgsl_cg_solve_batch": (C.c_int, [C.POINTER(dgsl_request), C.c_int, C.POINTER(dgsl_engine_opts),
+                                      C.POINTER(dgsl_solve_info), C.c_void_p]),
+    "dgsl_server_create": (C.c_int, [C.POINTER(dgsl_engine_opts), C.POINTER(C.c_void_p)]),
+    "dgsl_submit": (C.c_int, [C.c_void_p, C.POINTER(dgsl_request), C.POINTER(C.c_uint64)]),
+    "dgsl_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(dgsl_solve_info)]),
+    "dgsl_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "dgsl_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(dgsl_server_stats)]),
+    "dgsl_server_destroy": (None, [C.c_void_p]),
     "dgsl_cg_solve_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                         C.c_int, C.POINTER(dgsl_solve_opts),
                                         C.POINTER(dgsl_solve_info), C.c_void_p]),
@@ -291,3 +316,77 @@ def solve_opts(**kw):
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def engine_opts(**kw):
+    o = dgsl_engine_opts()
+    load().dgsl_default_engine_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def request(op, kind, coef, b, x, tol=0.0):
+    """dgsl_request for device tensors b, x (float64, op.n_dof elements)."""
+    return dgsl_request(op.h.value, int(kind), 0, float(coef), _dptr(b, "float64", op.n_dof).value,
+                        _dptr(x, "float64", op.n_dof).value, float(tol))
+
+
+def dgsl_cg_solve_batch(reqs, opts=None, stream=None, check=False):
+    """Runs the requests in one persistent launch; returns their solve infos."""
+    n = len(reqs)
+    arr = (dgsl_request * n)(*reqs)
+    infos = (dgsl_solve_info * n)()
+    o = opts if opts is not None else engine_opts()
+    code = load().dgsl_cg_solve_batch(arr, n, C.byref(o), infos, _stream(stream))
+    if check:
+        _check(code)
+    elif code not in (OK, ENOTCONV, ETIMEOUT):
+        _check(code)
+    return list(infos)
+
+
+class Server:
+    """Request loop with continuous batching (dgsl_server_*)."""
+
+    def __init__(self, opts=None):
+        o = opts if opts is not None else engine_opts()
+        h = C.c_void_p()
+        _check(load().dgsl_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+
+    def dgsl_submit(self, req):
+        t = C.c_uint64()
+        _check(load().dgsl_submit(self.h, C.byref(req), C.byref(t)))
+        return t.value
+
+    def dgsl_poll(self, ticket):
+        """None while pending, else the request's dgsl_solve_info."""
+        info = dgsl_solve_info()
+        code = load().dgsl_poll(self.h, C.c_uint64(ticket), C.byref(info))
+        if code == EPENDING:
+            return None
+        _check(code)
+        return info
+
+    def dgsl_cancel(self, ticket):
+        code = load().dgsl_cancel(self.h, C.c_uint64(ticket))
+        if code not in (OK, EPENDING):
+            _check(code)
+        return code == OK
+
+    def stats(self):
+        s = dgsl_server_stats()
+        _check(load().dgsl_server_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in dgsl_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dgsl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
