@@ -56,6 +56,15 @@ def parse_args(argv=None):
     ap.add_argument("--p", type=int, default=WORKLOAD["p"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["stage", "batch", "serve"], default="stage",
+                    help="stage: implicit stage (default line); batch: many solves in one launch; "
+                         "serve: Poisson request sweep through the server")
+    ap.add_argument("--batch-solves", type=int, default=64)
+    ap.add_argument("--batch-nmax", type=int, default=64)
+    ap.add_argument("--rhs", type=int, default=8)
+    ap.add_argument("--serve-nmax", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=10, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -270,6 +279,194 @@ def gpu_leg(args, rank, world, local):
     return res
 
 
+# ---------------------------------------------------------------- batch and serving legs
+
+def fourier_rhs(op, seed, dt):
+    """b = dt^2 Mbar f at the main nodes, f a 32-mode Fourier field (|k| <= 16,
+    amplitude ~ |k|^-2); Mbar applied by the library (Helmholtz with nu_dt = 0)."""
+    import torch
+    from paper_2401_17806_gb300 import synth
+    xy = op.node_coords(0)
+    f = synth.fourier_field(xy[:, 0], xy[:, 1], synth.fourier_modes(seed)) * dt * dt
+    fd = torch.tensor(f, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(fd)
+    op.dgsl_apply_helmholtz(0.0, fd, b)
+    return b
+
+
+def batch_leg(args):
+    """Independent Schur solves of random meshes (N uniform in 8..nmax, p uniform
+    in 1..4, per-solve seeds), each with `rhs` Fourier right-hand sides, all in
+    ONE persistent launch; versus one-solve-at-a-time FP64 CG on a sample."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(1234)
+    nsol, R, dt = args.batch_solves, args.rhs, WORKLOAD["dt"]
+    Ns = rng.integers(8, args.batch_nmax + 1, nsol)
+    ps = rng.integers(1, 5, nsol)
+    store = dgsl.STORE_F64 | dgsl.STORE_F32 | (dgsl.STORE_BF16 if args.precision == "bf16" else 0)
+    t0 = time.time()
+    ops = [dgsl.Operator(*synth.jittered_periodic_mesh(int(N), 1000 + i), int(p), store=store)
+           for i, (N, p) in enumerate(zip(Ns, ps))]
+    build_s = time.time() - t0
+    reqs, bufs = [], []
+    for i, op in enumerate(ops):
+        for j in range(R):
+            b = fourier_rhs(op, 5000 + i * R + j, dt)
+            x = torch.zeros_like(b)
+            bufs.append((op, b, x))
+            reqs.append(dgsl.request(op, dgsl.SCHUR, dt, b, x))
+    prec = dgsl.PREC_BF16_IR if args.precision == "bf16" else dgsl.PREC_F32_IR
+    opts = dgsl.engine_opts(precision=prec)
+    dgsl.dgsl_cg_solve_batch(reqs[:min(8, len(reqs))], opts)   # warm-up
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = dgsl.dgsl_launch_count()
+    ev0.record()
+    infos = dgsl.dgsl_cg_solve_batch(reqs, opts)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = dgsl.dgsl_launch_count() - l0
+    ok = [i.status == dgsl.OK for i in infos]
+    dof_iters = sum(bufs[k][0].n_dof * infos[k].iters for k in range(len(reqs)))
+    # one-solve-at-a-time FP64 CG on a sample of the same requests
+    sample = rng.choice(len(reqs), size=min(16, len(reqs)), replace=False)
+    o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
+    t64 = 0.0
+    for k in sample:
+        op, b, _ = bufs[k]
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        op.dgsl_cg_solve(dgsl.SCHUR, dt, b, x, opts=o64, check=False)
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t
+    base_rate = len(sample) / t64
+    iters = sorted(i.iters for i in infos)
+    line = {
+        "metric": "batched Schur solves/s (one persistent launch)", "workload": "batch",
+        "value": nsol / (ms * 1e-3), "unit": "solves/s",
+        "rhs_solves_per_s": len(reqs) / (ms * 1e-3), "dof_iters_per_s": dof_iters / (ms * 1e-3),
+        "ms_total": ms, "gpu_launches": launches, "dtype": {"bf16": "bf16+f32+f64"}.get(args.precision, "f32+f64"),
+        "config": {"solves": nsol, "rhs_per_solve": R, "N_range": [8, args.batch_nmax], "p_range": [1, 4],
+                   "tol": WORKLOAD["tol"], "dt": dt, "operator_build_s": build_s,
+                   "sample": f"{nsol} solves x {R} RHS (bounded sample of the 512-solve, N<=256 distribution)"},
+        "converged": int(sum(ok)), "requests": len(reqs), "iters_p50": iters[len(iters) // 2],
+        "iters_max": iters[-1], "max_relres": max(i.relres for i in infos),
+        "fp64_one_at_a_time": {"rhs_solves_per_s": base_rate, "sample_requests": len(sample),
+                               "speedup_rhs_solves_per_s": (len(reqs) / (ms * 1e-3)) / base_rate},
+        "data": "synthetic",
+    }
+    print(json.dumps(line))
+
+
+def serve_leg(args):
+    """Open-loop Poisson arrivals through the server: mesh N log-uniform in
+    16..nmax (rounded to a pool of powers of two), p uniform in 1..4, 1..8 RHS
+    per request, FP32 inner CG + FP64 refinement to 1e-10.  Latency = last RHS
+    done - arrival.  Baseline: the same trace served FIFO by one-at-a-time
+    FP64 CG, with service times measured on this GPU for every pool operator."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    dt = WORKLOAD["dt"]
+    sizes = [n for n in (16, 32, 64, 128, 256, 512, 1024) if n <= args.serve_nmax]
+    t0 = time.time()
+    pool = {}
+    for N in sizes:
+        for p in range(1, 5):
+            op = dgsl.Operator(*synth.jittered_periodic_mesh(N, 300 + N + p), p)
+            rhs = [fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)]
+            pool[(N, p)] = (op, rhs)
+    build_s = time.time() - t0
+    # FP64 one-at-a-time service time per pool operator (one solve each)
+    o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
+    svc = {}
+    for key, (op, rhs) in pool.items():
+        x = torch.zeros_like(rhs[0])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        op.dgsl_cg_solve(dgsl.SCHUR, dt, rhs[0], x, opts=o64, check=False)
+        torch.cuda.synchronize()
+        svc[key] = time.perf_counter() - t
+    rng = np.random.default_rng(77)
+    results = []
+    for rate in [float(v) for v in args.serve_rates.split(",")]:
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * args.serve_seconds * 1.5) + 8))
+        arr = arr[arr < args.serve_seconds]
+        lnN = rng.uniform(np.log(16), np.log(args.serve_nmax), len(arr))
+        Nr = [min(sizes, key=lambda s: abs(np.log(s) - v)) for v in lnN]
+        pr = rng.integers(1, 5, len(arr))
+        kr = rng.integers(1, 9, len(arr))
+        xs = [[torch.zeros_like(pool[(int(N), int(p))][1][0]) for _ in range(int(k))]
+              for N, p, k in zip(Nr, pr, kr)]
+        torch.cuda.synchronize()
+        srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=40_000_000_000, idle_us=2000))
+        owner, tickets = {}, []
+        start = time.perf_counter()
+        done_t = np.full(len(arr), np.nan)
+        left = np.array(kr, dtype=np.int64)
+        outstanding = []
+        i = 0
+        while True:
+            now = time.perf_counter() - start
+            while i < len(arr) and arr[i] <= now:
+                op, rhs = pool[(int(Nr[i]), int(pr[i]))]
+                for j in range(int(kr[i])):
+                    t = srv.dgsl_submit(dgsl.request(op, dgsl.SCHUR, dt, rhs[j], xs[i][j]))
+                    owner[t] = i
+                    outstanding.append(t)
+                i += 1
+            if outstanding:
+                flags, infos = srv.dgsl_poll_many(np.array(outstanding, dtype=np.uint64))
+                tnow = time.perf_counter() - start
+                keep = []
+                for t, f in zip(outstanding, flags):
+                    if f == 1:
+                        r = owner[t]
+                        left[r] -= 1
+                        if left[r] == 0:
+                            done_t[r] = tnow
+                    else:
+                        keep.append(t)
+                outstanding = keep
+            if i >= len(arr) and not outstanding:
+                break
+            if time.perf_counter() - start > args.serve_seconds + 120:
+                break
+        stats = srv.stats()
+        srv.close()
+        lat = done_t - arr
+        fin = np.isfinite(lat)
+        end = np.nanmax(done_t) if fin.any() else args.serve_seconds
+        # FIFO one-at-a-time FP64 on the same trace
+        free_at, blat = 0.0, []
+        for a, N, p, k in zip(arr, Nr, pr, kr):
+            begin = max(a, free_at)
+            free_at = begin + int(k) * svc[(int(N), int(p))]
+            blat.append(free_at - a)
+        blat = np.array(blat)
+        results.append({
+            "rate": rate, "requests": int(len(arr)), "completed": int(fin.sum()),
+            "solves_per_s": float(fin.sum() / end), "p50_ms": float(np.nanpercentile(lat, 50) * 1e3),
+            "p99_ms": float(np.nanpercentile(lat, 99) * 1e3), "engine_launches": stats["engine_launches"],
+            "fp64_one_at_a_time": {"solves_per_s": float(len(arr) / free_at),
+                                   "p50_ms": float(np.percentile(blat, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(blat, 99) * 1e3)}})
+    print(json.dumps({
+        "metric": "served Schur solves/s and p50/p99 latency", "workload": "serve", "data": "synthetic",
+        "config": {"N_pool": sizes, "p_range": [1, 4], "rhs_per_request": [1, 8], "tol": WORKLOAD["tol"],
+                   "seconds_per_rate": args.serve_seconds, "operator_pool_build_s": build_s,
+                   "sample": f"N log-uniform in 16..{args.serve_nmax} (bounded sample of 16..1024)"},
+        "sweep": results}))
+
+
 # ---------------------------------------------------------------- oracle legs
 
 def oracle_setup(N, p):
@@ -361,6 +558,12 @@ def main():
         return
     if args.impl == "reference":
         reference_main(args)
+        return
+    if args.workload == "batch":
+        batch_leg(args)
+        return
+    if args.workload == "serve":
+        serve_leg(args)
         return
     rank, world, local = dist_setup(args)
     import torch

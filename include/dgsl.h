@@ -213,7 +213,7 @@ typedef struct {
   int32_t max_iters;     /* cap on CG iterations, all refinements (default 200000) */
   int32_t precision;     /* DGSL_PREC_* */
   int32_t use_x0;        /* 1: x holds the initial guess */
-  double inner_tol;      /* inner CG relative tolerance under refinement (1e-4) */
+  double inner_tol;      /* inner CG relative tolerance under refinement (1e-3) */
   int32_t max_refine;    /* refinement steps cap (default 30) */
   int32_t form;          /* DGSL_FORM_* of the FP64 operator */
 } dgsl_solve_opts;
@@ -286,7 +286,7 @@ typedef struct {
 typedef struct {
   int32_t precision;        /* DGSL_PREC_F32_IR (default) or DGSL_PREC_BF16_IR */
   int32_t max_iters;        /* CG iterations per request (default 200000) */
-  double inner_tol;         /* inner FP32 CG tolerance (default 1e-4) */
+  double inner_tol;         /* inner FP32 CG tolerance (default 1e-3) */
   int32_t max_refine;       /* refinement steps per request (default 30) */
   int32_t device;           /* CUDA device (all operators must live there) */
   int64_t hbm_budget_bytes; /* server: cap on workspace + resident operators (0 = 150e9) */
@@ -301,7 +301,7 @@ void dgsl_default_engine_opts(dgsl_engine_opts* opts);
  * (eq. pressure_final / eq. ad5), all requests advancing together with one grid
  * barrier per pass.  Results and errors per request in infos[n] (host), as for
  * dgsl_cg_solve.  Blocks until all requests finish; allocates its workspace for
- * the call.  n <= 1024.  The BF16 path needs operators built with
+ * the call.  n <= 4096.  The BF16 path needs operators built with
  * DGSL_STORE_BF16.  Returns the first non-OK request status, else DGSL_OK. */
 int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_engine_opts* opts,
                         dgsl_solve_info* infos, void* stream);
@@ -327,6 +327,12 @@ int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* ticket);
  * DGSL_EPENDING, or DGSL_EINVAL for an unknown ticket.  A ticket can be polled
  * until it is reported done once; after that it is forgotten. */
 int dgsl_poll(dgsl_server* srv, uint64_t ticket, dgsl_solve_info* info);
+/* Polls n tickets at once: done[i] = 1 and infos[i] filled for each ticket that
+ * finished (it is then forgotten, as with dgsl_poll), done[i] = 0 if pending,
+ * -1 if unknown.  Returns the number of finished tickets (>= 0) or a negative
+ * status on bad arguments. */
+int dgsl_poll_many(dgsl_server* srv, const uint64_t* tickets, int n, dgsl_solve_info* infos,
+                   int32_t* done);
 /* Removes a request that has not been admitted yet (DGSL_OK); an admitted one
  * runs to completion (DGSL_EPENDING). */
 int dgsl_cancel(dgsl_server* srv, uint64_t ticket);

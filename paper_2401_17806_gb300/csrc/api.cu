@@ -82,7 +82,7 @@ void dgsl_default_solve_opts(dgsl_solve_opts* o) {
   o->max_iters = 200000;
   o->precision = DGSL_PREC_F64;
   o->use_x0 = 0;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-3;
   o->max_refine = 30;
   o->form = DGSL_FORM_ASSEMBLED;
 }
@@ -374,7 +374,7 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
       status = DGSL_ENOTCONV;
       break;
     }
-    if (relres < 0.5 * best) {
+    if (relres < 0.9 * best) {
       best = relres;
       stall = 0;
     } else if (++stall >= 3) {
@@ -562,7 +562,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
       status = DGSL_ENOTCONV;
       break;
     }
-    if (relres < 0.5 * best) {
+    if (relres < 0.9 * best) {
       best = relres;
       stall = 0;
     } else if (++stall >= 3) {

@@ -351,7 +351,7 @@ __device__ __forceinline__ void complete_slot(const EngineParams& E, int sid, co
 }
 
 // Advances slot `sid` after a pass, from the slot's summed partials (thread 0).
-__device__ void slot_transition(const EngineParams& E, int sid, const BSlotDesc& d, const double (&t)[4]) {
+__device__ __noinline__ void slot_transition(const EngineParams& E, int sid, const BSlotDesc& d, const double (&t)[4]) {
   BState* st = &E.state[sid];
   volatile BState* vs = st;
   const double n = (double)d.n;
@@ -385,7 +385,7 @@ __device__ void slot_transition(const EngineParams& E, int sid, const BSlotDesc&
       } else if (vs->iters >= d.max_iters || vs->refinements >= d.max_refine) {
         fin = 1;
         status = 5;  // DGSL_ENOTCONV
-      } else if (rel < 0.5 * vs->best) {
+      } else if (rel < 0.9 * vs->best) {
         st->best = rel;
         st->stall = 0;
       } else if (vs->stall + 1 >= 3) {
@@ -475,7 +475,7 @@ __device__ __forceinline__ void copy_desc(BSlotDesc* dst, const BSlotDesc* src) 
 
 // Admission of newly published slots and rebuild of the active-chunk list
 // (whole CTA of the last arriver).
-__device__ void engine_hook(const EngineParams& E) {
+__device__ __noinline__ void engine_hook(const EngineParams& E) {
   __shared__ int s_count, s_adm, s_dirty, s_run[kBThreads];
   EngineShared* sh = E.sh;
   if (threadIdx.x == 0) {
@@ -496,16 +496,16 @@ __device__ void engine_hook(const EngineParams& E) {
   }
   __syncthreads();
   if (s_count > s_adm || s_dirty) {
-    // active slots in slot order, chunk offsets by a block scan
+    // active slots in slot order, chunk offsets by a block scan; each thread
+    // owns PER consecutive slots and reads their state twice (count, write)
     constexpr int PER = kMaxSlots / kBThreads;
-    int flag[PER], nch[PER], cnt = 0, chunks = 0;
-#pragma unroll
+    int cnt = 0, chunks = 0;
     for (int j = 0; j < PER; ++j) {
       const int sidx = threadIdx.x * PER + j;
-      flag[j] = sidx < s_count && __ldcg(&E.state[sidx].phase) != PH_DONE;
-      nch[j] = flag[j] ? __ldcg(&E.slots[sidx].nchunk) : 0;
-      cnt += flag[j];
-      chunks += nch[j];
+      if (sidx < s_count && __ldcg(&E.state[sidx].phase) != PH_DONE) {
+        ++cnt;
+        chunks += __ldcg(&E.slots[sidx].nchunk);
+      }
     }
     s_run[threadIdx.x] = cnt;
     __shared__ int s_runc[kBThreads];
@@ -526,14 +526,15 @@ __device__ void engine_hook(const EngineParams& E) {
     }
     __syncthreads();
     int k = s_run[threadIdx.x], c0 = s_runc[threadIdx.x];
-#pragma unroll
-    for (int j = 0; j < PER; ++j)
-      if (flag[j]) {
-        E.act_slot[k] = threadIdx.x * PER + j;
+    for (int j = 0; j < PER; ++j) {
+      const int sidx = threadIdx.x * PER + j;
+      if (sidx < s_count && __ldcg(&E.state[sidx].phase) != PH_DONE) {
+        E.act_slot[k] = sidx;
         E.act_chunk0[k] = c0;
         ++k;
-        c0 += nch[j];
+        c0 += __ldcg(&E.slots[sidx].nchunk);
       }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       sh->admitted = s_count;
@@ -581,7 +582,7 @@ __device__ __forceinline__ bool chunk_work(const BSlotDesc& d, const ChunkCtx& c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBThreads, 1) k_engine(EngineParams E) {
+__global__ void __launch_bounds__(kBThreads, 4) k_engine(EngineParams E) {
   extern __shared__ __align__(128) unsigned char stages[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int s_last;
@@ -618,16 +619,24 @@ __global__ void __launch_bounds__(kBThreads, 1) k_engine(EngineParams E) {
       k = lo;
     }
     int cur_sid = -1, chunk0 = 0, next0 = 0;
-    BSlotDesc d;
-    ChunkCtx c;
+    // the slot descriptor and its per-pass scalars live in shared memory
+    // (registers stay free for the tile loop)
+    __shared__ BSlotDesc s_desc;
+    __shared__ ChunkCtx s_ctx;
+    const BSlotDesc& d = s_desc;
+    const ChunkCtx& c = s_ctx;
     for (int cidx = c_begin; cidx < c_end; ++cidx) {
       if (cur_sid < 0 || cidx >= next0) {
         while (k + 1 < n_act && __ldcg(E.act_chunk0 + k + 1) <= cidx) ++k;
         cur_sid = __ldcg(E.act_slot + k);
         chunk0 = __ldcg(E.act_chunk0 + k);
         next0 = __ldcg(E.act_chunk0 + k + 1);
-        load_desc(d, &E.slots[cur_sid]);
-        c = load_ctx(d, &E.state[cur_sid]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          load_desc(s_desc, &E.slots[cur_sid]);
+          s_ctx = load_ctx(s_desc, &E.state[cur_sid]);
+        }
+        __syncthreads();
       }
       const int sid = cur_sid;
       const int lc = cidx - chunk0;

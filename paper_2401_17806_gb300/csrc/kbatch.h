@@ -6,7 +6,7 @@
 
 namespace dgsl {
 
-constexpr int kMaxSlots = 1024;       // slots per engine (admitted over its lifetime)
+constexpr int kMaxSlots = 4096;       // slots per engine (admitted over its lifetime)
 
 // One solve, written by the host and copied into device memory when the engine
 // admits it.  All pointers are device pointers (the inbox itself is mapped host

@@ -138,7 +138,7 @@ extern "C" void dgsl_default_engine_opts(dgsl_engine_opts* o) {
   if (!o) return;
   o->precision = DGSL_PREC_F32_IR;
   o->max_iters = 200000;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-3;
   o->max_refine = 30;
   o->device = 0;
   o->hbm_budget_bytes = 150000000000LL;
@@ -151,7 +151,7 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
   dgsl_default_engine_opts(&o);
   if (opts) o = *opts;
   try {
-    if (!reqs || n < 1 || n > kMaxSlots) throw Error(DGSL_EINVAL, "need 1..1024 requests");
+    if (!reqs || n < 1 || n > kMaxSlots) throw Error(DGSL_EINVAL, "need 1..4096 requests");
     if (o.precision != DGSL_PREC_F32_IR && o.precision != DGSL_PREC_BF16_IR)
       throw Error(DGSL_EINVAL, "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR");
     if (!(o.inner_tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) throw Error(DGSL_EINVAL, "bad engine options");
@@ -453,6 +453,29 @@ extern "C" int dgsl_poll(dgsl_server* srv, uint64_t ticket, dgsl_solve_info* inf
   if (info) *info = it->second.info;
   srv->reqs.erase(it);
   return DGSL_OK;
+}
+
+extern "C" int dgsl_poll_many(dgsl_server* srv, const uint64_t* tickets, int n, dgsl_solve_info* infos,
+                              int32_t* done) {
+  if (!srv || (!tickets && n > 0) || !done || n < 0) return dgsl_set_last_error("bad arguments"), -DGSL_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  int finished = 0;
+  for (int i = 0; i < n; ++i) {
+    auto it = srv->reqs.find(tickets[i]);
+    if (it == srv->reqs.end()) {
+      done[i] = -1;
+      continue;
+    }
+    if (it->second.state != RQ_DONE) {
+      done[i] = 0;
+      continue;
+    }
+    if (infos) infos[i] = it->second.info;
+    done[i] = 1;
+    ++finished;
+    srv->reqs.erase(it);
+  }
+  return finished;
 }
 
 extern "C" int dgsl_cancel(dgsl_server* srv, uint64_t ticket) {

@@ -115,6 +115,7 @@ _SIGS = {
     "dgsl_submit": (C.c_int, [C.c_void_p, C.POINTER(dgsl_request), C.POINTER(C.c_uint64)]),
     "dgsl_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(dgsl_solve_info)]),
     "dgsl_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "dgsl_poll_many": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dgsl_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(dgsl_server_stats)]),
     "dgsl_server_destroy": (None, [C.c_void_p]),
     "dgsl_cg_solve_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
@@ -368,6 +369,18 @@ class Server:
             return None
         _check(code)
         return info
+
+    def dgsl_poll_many(self, tickets):
+        """tickets: numpy uint64 array -> (done int32 array, infos array)."""
+        n = len(tickets)
+        tk = np.ascontiguousarray(tickets, dtype=np.uint64)
+        done = np.zeros(n, dtype=np.int32)
+        infos = (dgsl_solve_info * max(n, 1))()
+        code = load().dgsl_poll_many(self.h, C.c_void_p(tk.ctypes.data), n, C.cast(infos, C.c_void_p),
+                                     C.c_void_p(done.ctypes.data))
+        if code < 0:
+            _check(-code)
+        return done, infos
 
     def dgsl_cancel(self, ticket):
         code = load().dgsl_cancel(self.h, C.c_uint64(ticket))
