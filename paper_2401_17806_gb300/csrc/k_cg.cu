@@ -217,79 +217,136 @@ __device__ __forceinline__ void lds_vals(const unsigned char* p, W (&v)[VEC]) {
   else lds16(p, v);
 }
 
-// Per-CTA state of the two coupling stages (identical in every thread).
+// Per-CTA pipeline state (identical in every thread): tiles are processed in
+// a fixed rotation over kStages shared-memory stages; `done` counts the tiles
+// this CTA has consumed since launch and `issued` the tiles whose copies were
+// issued, so tile g uses stage g % kStages with mbarrier parity (g / kStages) & 1.
+constexpr int kStages = 3;
 struct StageState {
-  int cur;        // stage holding the current tile
-  unsigned ph[2]; // parity of the next phase to wait on, per stage
-  int pend[2];    // a copy is in flight into this stage
+  unsigned done;
+  unsigned issued;
 };
+
+template <int NPHI, typename T, typename V>
+__device__ __forceinline__ void issue_next(const CGParams<T, V>& a, int tile, unsigned char* stages, uint64_t* mbar,
+                                           StageState& st) {
+  using C = TileCfg<NPHI, T>;
+  const int s = (int)(st.issued % kStages);
+  if (threadIdx.x == 0)
+    issue_tile<NPHI, T>(a.vals, a.cols, a.n, a.ne, a.ne_pad, tile, stages + (size_t)s * C::STAGE, &mbar[s]);
+  ++st.issued;
+}
 
 // One fused Chronopoulos-Gear pass over this CTA's tiles.  Reads the "old"
 // buffers (ro, wo, so), writes the "new" ones (rn, wn, sn), updates p and x in
-// place.  acc receives (r.r, w.r, sum w, sum r) of the new vectors.  On entry
-// the copy of this CTA's first tile is in flight into stage st.cur; on exit the
-// copy of the first tile of the next pass is.  Returns false if a stage wait
-// timed out.
+// place.  acc receives (r.r, w.r, sum w, sum r) of the new vectors.
+// Pipeline, for this CTA's q-th tile of the pass: its couplings and indices
+// were copied two tiles ahead (the first two before the pass began, across
+// the previous grid barrier); its neighbour values are gathered into
+// registers while tile q-1 is computed, then combined into shared memory.
+// Returns false if a stage wait timed out.
 template <int NPHI, typename T, typename V>
 __device__ __forceinline__ bool cg_pass(const CGParams<T, V>& a, V alpha, V beta, V muw, const V* ro, const V* wo,
                                         const V* so, V* rn, V* wn, V* sn, V* p, unsigned char* stages,
                                         uint64_t* mbar, StageState& st, double (&acc)[4]) {
   using C = TileCfg<NPHI, T>;
   constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG, TT = C::TT;
-  __shared__ V s_rn[TT * 4 * NPHI];
+  constexpr int NSV = TT * 4 * NPHI;                 // staged neighbour values per tile
+  constexpr int J = (NSV + kCgThreads - 1) / kCgThreads;
+  __shared__ V s_rn[2][NSV];                         // r_new of the 4 blocks per triangle
+  __shared__ V s_own[2][3][TT * NPHI];               // r_old, w_old - mu, s_old of own rows
   const int64_t n = a.n;
   const int ne = a.ne;
   const int ntiles = (ne + TT - 1) / TT;
+  const int nq = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   V g_rr = V(0), g_wr = V(0), g_w = V(0), g_r = V(0);
+  V gr[J], gw[J], gs[J];
+  V p_nx = V(0), x_nx = V(0);
   bool ok = true;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < ntiles) {
-      if (threadIdx.x == 0) issue_tile<NPHI, T>(a.vals, a.cols, n, ne, a.ne_pad, next, stages + (size_t)(st.cur ^ 1) * C::STAGE,
-                                                &mbar[st.cur ^ 1]);
-      st.pend[st.cur ^ 1] = 1;
+
+  auto stage_of = [&](unsigned g) { return stages + (size_t)(g % kStages) * C::STAGE; };
+  auto wait_stage = [&](unsigned g) {
+    const bool got = mbar_wait_bounded(&mbar[g % kStages], (g / kStages) & 1u, a.timeout_ns);
+    return __syncthreads_and(got) != 0;
+  };
+  auto load_tile = [&](unsigned g, int tile) {
+    // neighbour gather (3 L2 loads per value) and own-row p, x of tile `tile`
+    const int tri0 = tile * TT;
+    const int nt = min(TT, ne - tri0);
+    const int32_t* s_col = reinterpret_cast<const int32_t*>(stage_of(g) + C::COLS);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int i = threadIdx.x + j * kCgThreads;
+      if (i < nt * 4 * NPHI) {
+        const int tb = i / NPHI, kk = i - tb * NPHI;
+        const size_t c = (size_t)s_col[(tb & 3) * TT + (tb >> 2)] * NPHI + kk;
+        gr[j] = ldcg(ro + c);
+        gw[j] = ldcg(wo + c);
+        gs[j] = ldcg(so + c);
+      }
+    }
+    if ((int)threadIdx.x < nt * NPHI) {
+      const int64_t row = (int64_t)tri0 * NPHI + threadIdx.x;
+      p_nx = ldcg(p + row);
+      x_nx = ldcg(a.x + row);
+    }
+  };
+  auto combine = [&](int buf, int tile) {
+    const int tri0 = tile * TT;
+    const int nt = min(TT, ne - tri0);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int i = threadIdx.x + j * kCgThreads;
+      if (i < nt * 4 * NPHI) {
+        const int tb = i / NPHI, kk = i - tb * NPHI;
+        const V w1 = gw[j] - muw;
+        s_rn[buf][i] = fma(-alpha, fma(beta, gs[j], w1), gr[j]);
+        if ((tb & 3) == 0) {
+          const int lr = (tb >> 2) * NPHI + kk;
+          s_own[buf][0][lr] = gr[j];
+          s_own[buf][1][lr] = w1;
+          s_own[buf][2][lr] = gs[j];
+        }
+      }
+    }
+  };
+
+  if (nq > 0) {
+    // tile 0: its copy is in flight since before the pass
+    if (!wait_stage(st.done)) return false;
+    load_tile(st.done, (int)blockIdx.x);
+    combine(0, (int)blockIdx.x);
+    __syncthreads();
+  }
+  for (int q = 0; q < nq; ++q) {
+    const int tile = (int)blockIdx.x + q * (int)gridDim.x;
+    const unsigned g = st.done;  // global index of tile q
+    if (q + 2 < nq) issue_next<NPHI, T, V>(a, tile + 2 * (int)gridDim.x, stages, mbar, st);
+    const V p_old = p_nx, x_old = x_nx;
+    const bool more = q + 1 < nq;
+    if (more) {
+      if (!wait_stage(g + 1)) {
+        ok = false;
+        break;
+      }
+      load_tile(g + 1, tile + (int)gridDim.x);  // in flight while tile q is computed
     }
     const int tri0 = tile * TT;
     const int nt = min(TT, ne - tri0);
     const int lt = threadIdx.x / NPHI, k = threadIdx.x - lt * NPHI;
-    const bool active = threadIdx.x < nt * NPHI;
-    const int64_t row = (int64_t)tri0 * NPHI + threadIdx.x;
-    // own-row old values: independent of the staged indices, loaded first
-    V r_old = V(0), w_old = V(0), s_old = V(0), p_old = V(0), x_old = V(0);
-    if (active) {
-      r_old = ldcg(ro + row);
-      w_old = ldcg(wo + row) - muw;
-      s_old = ldcg(so + row);
-      p_old = ldcg(p + row);
-      x_old = ldcg(a.x + row);
-    }
-    const bool got = mbar_wait_bounded(&mbar[st.cur], st.ph[st.cur], a.timeout_ns);
-    if (!__syncthreads_and(got)) {
-      ok = false;
-      break;
-    }
-    st.ph[st.cur] ^= 1u;
-    st.pend[st.cur] = 0;
-    const unsigned char* stage = stages + (size_t)st.cur * C::STAGE;
-    const int32_t* s_col = reinterpret_cast<const int32_t*>(stage + C::COLS);  // [4][TT]
-    // stage r_new = r - alpha (w' + beta s) for the tile's 4 blocks per triangle
-    for (int i = threadIdx.x; i < nt * 4 * NPHI; i += blockDim.x) {
-      const int tb = i / NPHI, kk = i - tb * NPHI;
-      const size_t c = (size_t)s_col[(tb & 3) * TT + (tb >> 2)] * NPHI + kk;
-      s_rn[i] = fma(-alpha, fma(beta, ldcg(so + c), ldcg(wo + c) - muw), ldcg(ro + c));
-    }
-    __syncthreads();
-    if (active) {
-      const unsigned char* sv = stage + (size_t)threadIdx.x * 16;
-      const V* xs = s_rn + lt * 4 * NPHI;
+    const int buf = q & 1;
+    if ((int)threadIdx.x < nt * NPHI) {
+      const int64_t row = (int64_t)tri0 * NPHI + threadIdx.x;
+      const unsigned char* sv = stage_of(g) + (size_t)threadIdx.x * 16;
+      const V* xs = s_rn[buf] + lt * 4 * NPHI;
       V wv = V(0);
 #pragma unroll
-      for (int g = 0; g < NG; ++g) {
+      for (int gg = 0; gg < NG; ++gg) {
         typename ValOf<T>::type v[VEC];
-        lds_vals<T, VEC>(sv + (size_t)g * C::TR * 16, v);
+        lds_vals<T, VEC>(sv + (size_t)gg * C::TR * 16, v);
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const int c = g * VEC + u;
+          const int c = gg * VEC + u;
           if (c < NC) wv = fma((V)v[u], xs[c], wv);
         }
       }
@@ -300,7 +357,9 @@ __device__ __forceinline__ bool cg_pass(const CGParams<T, V>& a, V alpha, V beta
         for (int kk = 0; kk < NPHI; ++kk) mv = fma((V)__ldg(a.Mref + k * NPHI + kk), xs[kk], mv);
         wv = fma(a.coefM * (V)__ldg(a.area + tri0 + lt), mv, wv);
       }
-      // own-row recurrences (the same formula as the staged value)
+      const V r_old = s_own[buf][0][threadIdx.x];
+      const V w_old = s_own[buf][1][threadIdx.x];
+      const V s_old = s_own[buf][2][threadIdx.x];
       const V p_new = fma(beta, p_old, r_old);
       const V s_new = fma(beta, s_old, w_old);
       a.x[row] = fma(alpha, p_new, x_old);
@@ -314,15 +373,15 @@ __device__ __forceinline__ bool cg_pass(const CGParams<T, V>& a, V alpha, V beta
       g_w += wv;
       g_r += r_new;
     }
+    if (more) combine(buf ^ 1, tile + (int)gridDim.x);
     __syncthreads();
-    st.cur ^= 1;
+    ++st.done;
   }
-  if (ok) {
-    // the couplings are constant: prefetch the next pass's first tile now, so
-    // that the copy overlaps the grid barrier
-    if (threadIdx.x == 0)
-      issue_tile<NPHI, T>(a.vals, a.cols, n, ne, a.ne_pad, blockIdx.x, stages + (size_t)st.cur * C::STAGE, &mbar[st.cur]);
-    st.pend[st.cur] = 1;
+  if (ok && nq > 0) {
+    // the couplings are constant: the next pass's first two tiles are copied now,
+    // overlapping the grid barrier
+    issue_next<NPHI, T, V>(a, (int)blockIdx.x, stages, mbar, st);
+    if (nq > 1) issue_next<NPHI, T, V>(a, (int)blockIdx.x + (int)gridDim.x, stages, mbar, st);
   }
   acc[0] = to_d(g_rr);
   acc[1] = to_d(g_wr);
@@ -334,7 +393,7 @@ __device__ __forceinline__ bool cg_pass(const CGParams<T, V>& a, V alpha, V beta
 template <int NPHI, typename T, typename V>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
   extern __shared__ __align__(128) unsigned char stages[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[kStages];
   const unsigned nb = gridDim.x;
   unsigned long long epoch = 0;
   const int64_t n = a.n;
@@ -351,18 +410,21 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
   int it = 0;
   double rr = 0.0, rr0 = 0.0, tot[4];
   StageState st;
-  st.cur = 0;
-  st.ph[0] = st.ph[1] = 0u;
-  st.pend[0] = st.pend[1] = 0;
+  st.done = 0u;
+  st.issued = 0u;
   if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(&mbar[i], 1);
     fence_proxy_async_smem();
   }
   __syncthreads();
-  // the first tile's couplings load while the prologue runs
-  if (threadIdx.x == 0) issue_tile<NPHI, T>(a.vals, a.cols, n, a.ne, a.ne_pad, blockIdx.x, stages, &mbar[0]);
-  st.pend[0] = 1;
+  {
+    // the first two tiles' couplings load while the prologue runs
+    using Cfg = TileCfg<NPHI, T>;
+    const int ntiles = (a.ne + Cfg::TT - 1) / Cfg::TT;
+    if ((int)blockIdx.x < ntiles) issue_next<NPHI, T, V>(a, (int)blockIdx.x, stages, mbar, st);
+    if ((int)blockIdx.x + (int)gridDim.x < ntiles)
+      issue_next<NPHI, T, V>(a, (int)blockIdx.x + (int)gridDim.x, stages, mbar, st);
+  }
   // prologue: mean of r0; x = p = w = s = 0
   {
     V s = V(0);
@@ -422,8 +484,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
 done:
   // no CTA leaves with a bulk copy still writing its shared memory
   if (threadIdx.x == 0)
-    for (int s2 = 0; s2 < 2; ++s2)
-      if (st.pend[s2] && !mbar_wait_bounded(&mbar[s2], st.ph[s2], a.timeout_ns))
+    for (unsigned g = st.done; g < st.issued; ++g)
+      if (!mbar_wait_bounded(&mbar[g % kStages], (g / kStages) & 1u, a.timeout_ns))
         atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -450,7 +512,7 @@ cudaError_t run_cg(const DevOp& op, const T* vals, V coefK, V coefM, int mean_ze
                    int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s, int* grid_used) {
   auto kern = k_cg<NPHI, T, V>;
   using Cfg = TileCfg<NPHI, T>;
-  const size_t dyn = 2 * (size_t)Cfg::STAGE;
+  const size_t dyn = kStages * (size_t)Cfg::STAGE;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (err != cudaSuccess) return err;
   const int ntiles = (op.ne + Cfg::TT - 1) / Cfg::TT;
