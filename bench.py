@@ -551,6 +551,20 @@ def reference_main(args):
 
 # ---------------------------------------------------------------- main
 
+def aggregate_ranks(ms, e2e_ms, dof_iters, e2e_dof_iters, device=None):
+    """Whole-job numbers across ranks (replicas, no data exchange): the slowest
+    rank's times (MAX) and the total work (SUM).  Single process: unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, e2e_ms, dof_iters, e2e_dof_iters
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([dof_iters, e2e_dof_iters], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return t[0].item(), t[1].item(), w[0].item(), w[1].item()
+
+
 def main():
     args = parse_args()
     if args.cpu_leg:
@@ -570,14 +584,8 @@ def main():
     res = gpu_leg(args, rank, world, local)
     ms, e2e_ms = res["ms"], res["e2e_ms"]
     dof_iters, e2e_dof_iters = float(res["dof_iters"]), float(res["e2e_dof_iters"])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = torch.tensor([dof_iters, e2e_dof_iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        ms, e2e_ms = t.tolist()
-        dof_iters, e2e_dof_iters = s.tolist()
+    ms, e2e_ms, dof_iters, e2e_dof_iters = aggregate_ranks(ms, e2e_ms, dof_iters, e2e_dof_iters,
+                                                           device="cuda")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(args)
