@@ -244,6 +244,14 @@ int dgsl_cg_solve(const dgsl_operator* op, int kind, double coef, const double* 
 
 void dgsl_default_solve_opts(dgsl_solve_opts* opts);
 
+/* Failure-detection self-test (no counterpart in the paper; the persistent
+ * solvers' waits are bounded): which = 0 runs the persistent CG's grid barrier
+ * expecting one CTA more than are launched, which = 1 waits on an mbarrier that
+ * no copy completes.  Each wait gives up after timeout_s (0 < timeout_s <= 5),
+ * the kernel records the timeout and returns; *status receives DGSL_ETIMEOUT
+ * if it did (DGSL_OK otherwise) and the device stays usable.  Synchronous. */
+int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* status);
+
 /* Same solve as dgsl_cg_solve, for callers that cannot allocate device memory
  * when they solve: code that runs while a CUDA stream is being captured into a
  * graph, real-time loops and services that reserve all device memory at start-up

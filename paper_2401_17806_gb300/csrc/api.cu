@@ -649,3 +649,23 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     return worst;
   });
 }
+
+// ------------------------------------------------------------ failure-detection self-test
+extern "C" int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* status) {
+  if (!status || (which != 0 && which != 1) || !(timeout_s > 0.0) || timeout_s > 5.0)
+    return fail(DGSL_EINVAL, "which must be 0 or 1 and 0 < timeout_s <= 5");
+  try {
+    DGSL_CUDA(cudaSetDevice(device));
+    GridBarrier* bar = nullptr;
+    DGSL_CUDA(cudaMalloc(&bar, sizeof(GridBarrier)));
+    std::unique_ptr<GridBarrier, void (*)(GridBarrier*)> guard(bar, [](GridBarrier* b) { cudaFree(b); });
+    DGSL_CUDA(launch_selftest_wait(bar, which, (uint64_t)(timeout_s * 1e9), nullptr));
+    DGSL_CUDA(cudaDeviceSynchronize());
+    GridBarrier h;
+    DGSL_CUDA(cudaMemcpy(&h, bar, sizeof(GridBarrier), cudaMemcpyDeviceToHost));
+    *status = h.status == kStatusTimeout ? DGSL_ETIMEOUT : DGSL_OK;
+    return DGSL_OK;
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  }
+}

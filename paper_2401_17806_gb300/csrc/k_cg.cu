@@ -496,6 +496,34 @@ done:
   }
 }
 
+// Self-test of the bounded waits: `which` = 0 runs the grid barrier of this
+// file expecting one CTA more than the launch has; 1 waits on an mbarrier no
+// copy will complete.  Both waits must give up after timeout_ns, record
+// kStatusTimeout in bar->status and return, leaving the context usable.
+__global__ void k_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns) {
+  __shared__ __align__(8) uint64_t mb;
+  if (which == 0) {
+    unsigned long long epoch = 0;
+    grid_sync_epoch(bar, gridDim.x + 1, epoch, timeout_ns);
+  } else {
+    if (threadIdx.x == 0) {
+      mbar_init(&mb, 1);
+      fence_proxy_async_smem();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&mb, 0u, timeout_ns)) atomicCAS(&bar->status, kStatusOk, kStatusTimeout);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+  if (err != cudaSuccess) return err;
+  k_selftest_wait<<<which == 0 ? 2 : 1, 64, 0, s>>>(bar, which, timeout_ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
 namespace {
 template <class KernelT>
 int coop_blocks(KernelT kern, size_t dyn_smem) {

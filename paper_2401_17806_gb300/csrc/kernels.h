@@ -93,6 +93,8 @@ cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, i
                           float* r, double stop_rel, int max_iters, const CGWork& w,
                           uint64_t timeout_ns, cudaStream_t s, int* grid_used);
 int cg_max_blocks(const DevOp& op, int prec);
+// Bounded-wait self-test (see k_cg.cu): records kStatusTimeout in bar->status.
+cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s);
 
 void count_launch(int n = 1);
 uint64_t launch_count();

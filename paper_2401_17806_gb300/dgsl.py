@@ -109,6 +109,7 @@ _SIGS = {
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
     "dgsl_default_engine_opts": (None, [C.POINTER(dgsl_engine_opts)]),
+    "dgsl_selftest_wait_timeout": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
     "dgsl_cg_solve_batch": (C.c_int, [C.POINTER(dgsl_request), C.c_int, C.POINTER(dgsl_engine_opts),
                                       C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_server_create": (C.c_int, [C.POINTER(dgsl_engine_opts), C.POINTER(C.c_void_p)]),
@@ -403,3 +404,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def dgsl_selftest_wait_timeout(which, timeout_s=0.2, device=0):
+    """Status (ETIMEOUT expected) of a bounded wait made to run out."""
+    st = C.c_int(-1)
+    _check(load().dgsl_selftest_wait_timeout(int(device), int(which), float(timeout_s), C.byref(st)))
+    return st.value
