@@ -37,7 +37,7 @@ HBM_FALLBACK_GBS = 6800.0
 # over a 200-iteration launch, 256x256, p = 3, FP32 couplings; the capture and
 # command are summarised in profiles/k_cg_f32_256x256_p3.md).  Keyed by (p,
 # precision); a kernel change invalidates it.
-NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 172.5}
+NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 171.3}
 
 
 def workload_name(args):
@@ -56,9 +56,11 @@ def parse_args(argv=None):
     ap.add_argument("--p", type=int, default=WORKLOAD["p"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve"], default="stage",
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg"], default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
-                         "serve: Poisson request sweep through the server")
+                         "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
+                         "launch capped at --cg-iters iterations (the case the profiles capture)")
+    ap.add_argument("--cg-iters", type=int, default=200)
     ap.add_argument("--batch-solves", type=int, default=64)
     ap.add_argument("--batch-nmax", type=int, default=64)
     ap.add_argument("--rhs", type=int, default=8)
@@ -292,6 +294,24 @@ def fourier_rhs(op, seed, dt):
     b = torch.empty_like(fd)
     op.dgsl_apply_helmholtz(0.0, fd, b)
     return b
+
+
+def cg_leg(args):
+    """One persistent FP32 CG launch (Schur operator, dt = 1e-3, random right-hand
+    side) capped at --cg-iters iterations on the N x N mesh: the case the ncu
+    summaries under profiles/ capture.  Prints the event-timed cost per iteration."""
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    xy, tri, per = synth.jittered_periodic_mesh(args.N, WORKLOAD["seed"])
+    op = dgsl.Operator(xy, tri, per, args.p, store=dgsl.STORE_F64 | dgsl.STORE_F32)
+    b = torch.tensor(synth.standard_normal(op.n_dof, 1), device="cuda")
+    x = torch.zeros_like(b)
+    o = dgsl.solve_opts(tol=1e-30, max_iters=args.cg_iters, max_refine=1, precision=dgsl.PREC_F32_IR)
+    info = op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], b, x, opts=o, check=False)[0]
+    print(json.dumps({"workload": f"one FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
+                      "grid": info.grid, "us_per_iter": 1e3 * info.cg_kernel_ms / max(1, info.iters)}))
 
 
 def batch_leg(args):
@@ -578,6 +598,9 @@ def main():
         return
     if args.workload == "serve":
         serve_leg(args)
+        return
+    if args.workload == "cg":
+        cg_leg(args)
         return
     rank, world, local = dist_setup(args)
     import torch

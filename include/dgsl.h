@@ -257,8 +257,8 @@ int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* sta
  * graph, real-time loops and services that reserve all device memory at start-up
  * under a fixed budget, or hosts whose own allocator owns the GPU.  This entry
  * point calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * is one fixed device array inside the library (about 16.8 MB: eight vectors of
- * 262,144 doubles plus reduction slots), created when the library is loaded and
+ * is one fixed device array inside the library (about 27.3 MB: thirteen vectors
+ * of 262,144 doubles plus reduction slots), created when the library is loaded and
  * held by every GPU that loads it until the process exits.  The paper has no
  * counterpart; this is a deployment convenience.
  *  - Limit: op's n_dof <= 262,144 (per right-hand side); larger operators are

@@ -487,8 +487,11 @@ namespace {
 constexpr int64_t kNoAllocMaxDof = int64_t(1) << 18;   // 262,144 DOFs per right-hand side
 constexpr int kNoAllocMaxParts = 1024;                 // per-CTA partial slots
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxDof * sizeof(double);
-// r64 | d64 (also r32 + d32) | 6 CG vectors | part (4 slots) | part2 (2) | barrier | result
-constexpr size_t kNoAllocBytes = 8 * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
+// CG vectors (cg_vec_bytes: 8 per-triangle padded vectors; at most 32/3 n doubles, for p = 1)
+constexpr size_t kNoAllocCgSlots = 11;
+// r64 | d64 (also r32 + d32) | CG vectors | part (4 slots) | part2 (2) | barrier | result
+constexpr size_t kNoAllocBytes =
+    (2 + kNoAllocCgSlots) * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -517,7 +520,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   float* r32 = reinterpret_cast<float*>(base + kNoAllocVecBytes);
   float* d32 = r32 + kNoAllocMaxDof;
   void* vbuf = base + 2 * kNoAllocVecBytes;
-  double* part = reinterpret_cast<double*>(base + 8 * kNoAllocVecBytes);
+  double* part = reinterpret_cast<double*>(base + (2 + kNoAllocCgSlots) * kNoAllocVecBytes);
   double* part2 = part + 4 * kNoAllocMaxParts;
   unsigned char* tail = reinterpret_cast<unsigned char*>(part2 + 2 * kNoAllocMaxParts);
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(tail);
@@ -625,7 +628,7 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     if (int e = check_vec_args(b, x, n_rhs)) return e;
     if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
     if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
-    if (cop->d.n > kNoAllocMaxDof)
+    if (cop->d.n > kNoAllocMaxDof || cg_vec_bytes(cop->d) > kNoAllocCgSlots * kNoAllocVecBytes)
       return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: operator has " + std::to_string(cop->d.n) +
                                    " DOFs, above the fixed scratch limit of " + std::to_string(kNoAllocMaxDof));
     dgsl_solve_opts o;

@@ -13,22 +13,32 @@
 // r and p stay mean-free).  Reading: x0 = 0, stop when the recursive residual
 // satisfies ||r|| <= stop_rel ||r0||.
 //
-// The pass is tiled by triangles: a CTA stages, for a tile of triangles, the
-// new residual of each triangle and of its three neighbours in shared memory
-// (formed on the fly as r - alpha (w' + beta s) from the previous buffers), so
-// each neighbour block is gathered once per tile instead of once per matrix
-// row; r, w and s are double-buffered because other CTAs still gather the
-// previous values.  Each thread then owns one matrix row: it streams that row's
-// 4 N_phi coupling coefficients (16-byte loads) against the staged values.
-// Partial sums are reduced per CTA and summed by every CTA in the same fixed
-// order, so all CTAs take identical, deterministic decisions.
+// The pass is tiled by triangles and warp-specialised.  Each CTA has three
+// roles working through the same ring of shared-memory stages:
+//  - a coupling warp streams each tile's coupling coefficients with TMA bulk
+//    copies (L2 evict-first), running ahead across pass boundaries (the
+//    couplings are constant);
+//  - a gather warp copies, with 16-byte cp.async, the previous r, w and s of
+//    each tile triangle and its three neighbours and the own p and x, after the
+//    grid all-reduce that opens the pass (they are written by other CTAs);
+//  - four consumer warps form the new residual of the gathered blocks,
+//    r - alpha (w' + beta s), once per tile, then each thread owns one matrix
+//    row: it streams the row's 4 N_phi couplings against those values and
+//    updates p, s, x, r and w.
+// So that every gathered block starts on a 16-byte boundary, the CG's own
+// vectors are stored per triangle with N_phi padded to a multiple of the
+// 16-byte vector width (the caller's r and x stay unpadded).  Partial sums
+// are reduced per CTA and combined by the last CTA to arrive in a fixed order,
+// so all CTAs take identical, deterministic decisions.
 #include "kassembled.cuh"
 #include "kernels.h"
 
 namespace dgsl {
 
-// threads per CTA of the persistent CG (one matrix row per thread in a tile)
-constexpr int kCgThreads = 128;
+constexpr int kCgConsumers = 128;                // 4 warps, one matrix row per thread
+constexpr int kCgThreads = kCgConsumers + 64;    // + coupling warp + gather warp
+constexpr int kCouplingWarp = kCgConsumers / 32;
+constexpr int kGatherWarp = kCouplingWarp + 1;
 
 template <typename T, typename V>
 struct CGParams {
@@ -41,9 +51,9 @@ struct CGParams {
   int64_t n;
   V coefK, coefM;
   int mean_zero;
-  V* x;          // result (starts at 0)
-  V* r0;         // right-hand side on entry; residual buffer 0
-  V* vec;        // 6 n: p | r1 | w0 | w1 | s0 | s1
+  V* x;          // result, unpadded (written at exit)
+  const V* r0;   // right-hand side, unpadded
+  V* vec;        // 8 padded vectors of ne * NPAD: p | x | r0 | r1 | w0 | w1 | s0 | s1
   double* part;  // [max_parts][4]
   int max_parts;
   GridBarrier* bar;
@@ -151,44 +161,143 @@ __device__ __forceinline__ bool grid_allreduce4(GridBarrier* b, double* part, un
 template <typename V>
 __device__ __forceinline__ double to_d(V v) { return (double)v; }
 
+// ---- synchronisation among the consumer warps only (named barrier 1), so
+// the two producer warps are never held by a consumer barrier.
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(kCgConsumers) : "memory"); }
+__device__ __forceinline__ bool cbar_and(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(r)
+      : "r"((unsigned)v), "n"(kCgConsumers)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_addr(bar)) : "memory");
+}
+// 16-byte global -> shared copy through L2 only (no L1: the CG vectors are
+// rewritten by other CTAs during the launch).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// Arrive on `bar` once this thread's earlier cp.async copies have landed (the
+// barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Deterministic sum of v over the consumer threads, in type W; the result is
+// valid in consumer thread 0 (fixed shuffle tree, then the 4 warp sums in order).
+template <typename W>
+__device__ __forceinline__ void consumer_sum4(W (&v)[4], W (*s_red)[4]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s_red[wid][i] = v[i];
+  cbar();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
+  cbar();
+}
+
+// Grid-wide sum of acc[0..3] by the consumer warps (as grid_allreduce4): the
+// CTA's partial (summed over its threads in V, then widened to FP64) is
+// published, the last CTA to arrive sums all partials in CTA order in FP64 and
+// releases the totals; the others wait for the release.  The acq_rel arrival
+// orders this CTA's vector writes (made before the consumer barrier) for every
+// CTA that later sees the count.
+template <typename V>
+__device__ __forceinline__ bool consumer_allreduce4(GridBarrier* b, double* part, unsigned nblocks,
+                                                    unsigned long long& epoch, uint64_t timeout_ns,
+                                                    V (&acc)[4], double (&tot)[4]) {
+  __shared__ V s_redv[4][4];
+  __shared__ double s_red[4][4];
+  __shared__ double s_tot[4];
+  __shared__ int s_state;  // 1: this CTA arrived last, 0: wait, -1: error
+  consumer_sum4<V>(acc, s_redv);
+  ++epoch;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = (double)acc[i];
+    const unsigned long long target = epoch * (unsigned long long)nblocks;
+    unsigned long long v;
+    asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(v) : "l"(&b->count) : "memory");
+    s_state = v + 1 == target ? 1 : 0;
+  }
+  cbar();
+  if (s_state == 1) {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned j = threadIdx.x; j < nblocks; j += kCgConsumers)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] += __ldcg(part + (size_t)j * 4 + i);
+    consumer_sum4<double>(t, s_red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        b->total[i] = t[i];
+        s_tot[i] = t[i];
+      }
+      asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(&b->gen), "l"(epoch) : "memory");
+    }
+  } else if (threadIdx.x == 0) {
+    const uint64_t t0 = globaltimer_ns();
+    unsigned long long g;
+    int st = 0;
+    for (unsigned spins = 1;; ++spins) {
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(g) : "l"(&b->gen) : "memory");
+      if (g >= epoch) break;
+      if (*((volatile int*)&b->status) != kStatusOk) { st = -1; break; }
+      if ((spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+        atomicCAS(&b->status, kStatusOk, kStatusTimeout);
+        st = -1;
+        break;
+      }
+    }
+    if (st == 0)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) s_tot[i] = __ldcg(&b->total[i]);
+    s_state = st;
+  }
+  // one thread decides, so that every consumer thread takes the same branch
+  if (threadIdx.x == 0 && *((volatile int*)&b->status) != kStatusOk) s_state = -1;
+  cbar();
+  const bool ok = s_state >= 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tot[i] = s_tot[i];
+  cbar();
+  return ok;
+}
+
 // Tile geometry: TT triangles (a multiple of 4; TR = TT N_phi matrix rows, one
-// per thread) per tile.  A stage holds the tile's coupling coefficients (NG
-// chunks of TR 16-byte vectors, each contiguous in global memory) and its
-// column indices (4 chunks of TT int32), all brought in by TMA bulk copies; two
-// stages per CTA, at most ~96 KB each.
-template <int NPHI, typename T>
+// per consumer thread) per tile.  A stage holds the tile's couplings (NG
+// chunks of TR 16-byte vectors, each contiguous in global memory), the
+// gathered r, w, s of the 4 TT coupled blocks and the own p, x blocks, and
+// the own triangles' areas (Helmholtz mass term).
+template <int NPHI, typename T, typename V>
 struct TileCfg {
   static constexpr int VEC = Pack<T>::VEC;
   static constexpr int NC = 4 * NPHI;
   static constexpr int NG = (NC + VEC - 1) / VEC;
-  static constexpr int TT0 = kCgThreads / NPHI;
-  static constexpr int TTS = 98304 / (NG * NPHI * 16);
-  static constexpr int TT = (TT0 < TTS ? TT0 : TTS) / 4 * 4;
+  static constexpr int TT = (kCgConsumers / NPHI) / 4 * 4;
   static constexpr int TR = TT * NPHI;
-  static constexpr int COLS = NG * TR * 16;        // byte offset of the indices
-  static constexpr int STAGE = COLS + 16 * TT;     // 4 x TT int32
+  static constexpr int VPC = 16 / (int)sizeof(V);          // vector values per 16 bytes
+  static constexpr int NPAD = (NPHI + VPC - 1) / VPC * VPC;  // padded block length
+  static constexpr int CPB = NPAD / VPC;                     // 16-byte chunks per block
+  static constexpr int NB = 4 * TT;                          // coupled blocks per tile
+  static constexpr int COUPLE = NG * TR * 16;
+  static constexpr int GATHER = COUPLE;                      // byte offset of r | w | s blocks
+  static constexpr int OWN = GATHER + 3 * NB * NPAD * (int)sizeof(V);  // p | x own blocks
+  static constexpr int AREA = OWN + 2 * TT * NPAD * (int)sizeof(V);    // TT doubles
+  static constexpr int STAGE = (AREA + TT * 8 + 127) / 128 * 128;
+  static constexpr int S = 3 * STAGE <= 180 * 1024 ? 3 : 2;           // stages per CTA
 };
-
-// Issue (one thread) the bulk copies of tile `tile`'s couplings into `stage`.
-template <int NPHI, typename T>
-__device__ __forceinline__ void issue_tile(const T* vals, const int32_t* cols, int64_t n, int ne, int ne_pad,
-                                           int tile, unsigned char* stage, uint64_t* bar) {
-  using C = TileCfg<NPHI, T>;
-  const int tri0 = tile * C::TT;                 // multiple of 4
-  const int nt = min(C::TT, ne - tri0);
-  const uint32_t bytes = (uint32_t)(nt * NPHI * 16);
-  const uint32_t cbytes = (uint32_t)(((nt + 3) / 4) * 16);  // padded rows of cols
-  const int64_t row0 = (int64_t)tri0 * NPHI;
-  const uint64_t pol = l2_evict_first_policy();   // couplings stream; vectors stay in L2
-  fence_proxy_async_smem();
-  mbar_expect_tx(bar, bytes * C::NG + 4 * cbytes);
-#pragma unroll 1
-  for (int g = 0; g < C::NG; ++g)
-    bulk_g2s_hint(stage + (size_t)g * C::TR * 16, vals + ((size_t)g * n + row0) * C::VEC, bytes, bar, pol);
-#pragma unroll
-  for (int b = 0; b < 4; ++b)
-    bulk_g2s(stage + C::COLS + b * C::TT * 4, cols + (size_t)b * ne_pad + tri0, cbytes, bar);
-}
 
 __device__ __forceinline__ void lds16(const unsigned char* p, double (&v)[2]) {
   const double2 t = *reinterpret_cast<const double2*>(p);
@@ -217,277 +326,343 @@ __device__ __forceinline__ void lds_vals(const unsigned char* p, W (&v)[VEC]) {
   else lds16(p, v);
 }
 
-// Per-CTA pipeline state (identical in every thread): tiles are processed in
-// a fixed rotation over kStages shared-memory stages; `done` counts the tiles
-// this CTA has consumed since launch and `issued` the tiles whose copies were
-// issued, so tile g uses stage g % kStages with mbarrier parity (g / kStages) & 1.
-constexpr int kStages = 3;
-struct StageState {
-  unsigned done;
-  unsigned issued;
-};
-
-template <int NPHI, typename T, typename V>
-__device__ __forceinline__ void issue_next(const CGParams<T, V>& a, int tile, unsigned char* stages, uint64_t* mbar,
-                                           StageState& st) {
-  using C = TileCfg<NPHI, T>;
-  const int s = (int)(st.issued % kStages);
-  if (threadIdx.x == 0)
-    issue_tile<NPHI, T>(a.vals, a.cols, a.n, a.ne, a.ne_pad, tile, stages + (size_t)s * C::STAGE, &mbar[s]);
-  ++st.issued;
-}
-
-// One fused Chronopoulos-Gear pass over this CTA's tiles.  Reads the "old"
-// buffers (ro, wo, so), writes the "new" ones (rn, wn, sn), updates p and x in
-// place.  acc receives (r.r, w.r, sum w, sum r) of the new vectors.
-// Pipeline, for this CTA's q-th tile of the pass: its couplings and indices
-// were copied two tiles ahead (the first two before the pass began, across
-// the previous grid barrier); its neighbour values are gathered into
-// registers while tile q-1 is computed, then combined into shared memory.
-// Returns false if a stage wait timed out.
-template <int NPHI, typename T, typename V>
-__device__ __forceinline__ bool cg_pass(const CGParams<T, V>& a, V alpha, V beta, V muw, const V* ro, const V* wo,
-                                        const V* so, V* rn, V* wn, V* sn, V* p, unsigned char* stages,
-                                        uint64_t* mbar, StageState& st, double (&acc)[4]) {
-  using C = TileCfg<NPHI, T>;
-  constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG, TT = C::TT;
-  constexpr int NSV = TT * 4 * NPHI;                 // staged neighbour values per tile
-  constexpr int J = (NSV + kCgThreads - 1) / kCgThreads;
-  __shared__ V s_rn[2][NSV];                         // r_new of the 4 blocks per triangle
-  __shared__ V s_own[2][3][TT * NPHI];               // r_old, w_old - mu, s_old of own rows
-  const int64_t n = a.n;
-  const int ne = a.ne;
-  const int ntiles = (ne + TT - 1) / TT;
-  const int nq = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  V g_rr = V(0), g_wr = V(0), g_w = V(0), g_r = V(0);
-  V gr[J], gw[J], gs[J];
-  V p_nx = V(0), x_nx = V(0);
-  bool ok = true;
-
-  auto stage_of = [&](unsigned g) { return stages + (size_t)(g % kStages) * C::STAGE; };
-  auto wait_stage = [&](unsigned g) {
-    const bool got = mbar_wait_bounded(&mbar[g % kStages], (g / kStages) & 1u, a.timeout_ns);
-    return __syncthreads_and(got) != 0;
-  };
-  auto load_tile = [&](unsigned g, int tile) {
-    // neighbour gather (3 L2 loads per value) and own-row p, x of tile `tile`
-    const int tri0 = tile * TT;
-    const int nt = min(TT, ne - tri0);
-    const int32_t* s_col = reinterpret_cast<const int32_t*>(stage_of(g) + C::COLS);
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int i = threadIdx.x + j * kCgThreads;
-      if (i < nt * 4 * NPHI) {
-        const int tb = i / NPHI, kk = i - tb * NPHI;
-        const size_t c = (size_t)s_col[(tb & 3) * TT + (tb >> 2)] * NPHI + kk;
-        gr[j] = ldcg(ro + c);
-        gw[j] = ldcg(wo + c);
-        gs[j] = ldcg(so + c);
-      }
-    }
-    if ((int)threadIdx.x < nt * NPHI) {
-      const int64_t row = (int64_t)tri0 * NPHI + threadIdx.x;
-      p_nx = ldcg(p + row);
-      x_nx = ldcg(a.x + row);
-    }
-  };
-  auto combine = [&](int buf, int tile) {
-    const int tri0 = tile * TT;
-    const int nt = min(TT, ne - tri0);
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int i = threadIdx.x + j * kCgThreads;
-      if (i < nt * 4 * NPHI) {
-        const int tb = i / NPHI, kk = i - tb * NPHI;
-        const V w1 = gw[j] - muw;
-        s_rn[buf][i] = fma(-alpha, fma(beta, gs[j], w1), gr[j]);
-        if ((tb & 3) == 0) {
-          const int lr = (tb >> 2) * NPHI + kk;
-          s_own[buf][0][lr] = gr[j];
-          s_own[buf][1][lr] = w1;
-          s_own[buf][2][lr] = gs[j];
-        }
-      }
-    }
-  };
-
-  if (nq > 0) {
-    // tile 0: its copy is in flight since before the pass
-    if (!wait_stage(st.done)) return false;
-    load_tile(st.done, (int)blockIdx.x);
-    combine(0, (int)blockIdx.x);
-    __syncthreads();
-  }
-  for (int q = 0; q < nq; ++q) {
-    const int tile = (int)blockIdx.x + q * (int)gridDim.x;
-    const unsigned g = st.done;  // global index of tile q
-    if (q + 2 < nq) issue_next<NPHI, T, V>(a, tile + 2 * (int)gridDim.x, stages, mbar, st);
-    const V p_old = p_nx, x_old = x_nx;
-    const bool more = q + 1 < nq;
-    if (more) {
-      if (!wait_stage(g + 1)) {
-        ok = false;
-        break;
-      }
-      load_tile(g + 1, tile + (int)gridDim.x);  // in flight while tile q is computed
-    }
-    const int tri0 = tile * TT;
-    const int nt = min(TT, ne - tri0);
-    const int lt = threadIdx.x / NPHI, k = threadIdx.x - lt * NPHI;
-    const int buf = q & 1;
-    if ((int)threadIdx.x < nt * NPHI) {
-      const int64_t row = (int64_t)tri0 * NPHI + threadIdx.x;
-      const unsigned char* sv = stage_of(g) + (size_t)threadIdx.x * 16;
-      const V* xs = s_rn[buf] + lt * 4 * NPHI;
-      V wv = V(0);
-#pragma unroll
-      for (int gg = 0; gg < NG; ++gg) {
-        typename ValOf<T>::type v[VEC];
-        lds_vals<T, VEC>(sv + (size_t)gg * C::TR * 16, v);
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) {
-          const int c = gg * VEC + u;
-          if (c < NC) wv = fma((V)v[u], xs[c], wv);
-        }
-      }
-      wv *= a.coefK;
-      if (a.coefM != V(0)) {
-        V mv = V(0);
-#pragma unroll
-        for (int kk = 0; kk < NPHI; ++kk) mv = fma((V)__ldg(a.Mref + k * NPHI + kk), xs[kk], mv);
-        wv = fma(a.coefM * (V)__ldg(a.area + tri0 + lt), mv, wv);
-      }
-      const V r_old = s_own[buf][0][threadIdx.x];
-      const V w_old = s_own[buf][1][threadIdx.x];
-      const V s_old = s_own[buf][2][threadIdx.x];
-      const V p_new = fma(beta, p_old, r_old);
-      const V s_new = fma(beta, s_old, w_old);
-      a.x[row] = fma(alpha, p_new, x_old);
-      const V r_new = xs[k];
-      p[row] = p_new;
-      sn[row] = s_new;
-      rn[row] = r_new;
-      wn[row] = wv;
-      g_rr = fma(r_new, r_new, g_rr);
-      g_wr = fma(wv, r_new, g_wr);
-      g_w += wv;
-      g_r += r_new;
-    }
-    if (more) combine(buf ^ 1, tile + (int)gridDim.x);
-    __syncthreads();
-    ++st.done;
-  }
-  if (ok && nq > 0) {
-    // the couplings are constant: the next pass's first two tiles are copied now,
-    // overlapping the grid barrier
-    issue_next<NPHI, T, V>(a, (int)blockIdx.x, stages, mbar, st);
-    if (nq > 1) issue_next<NPHI, T, V>(a, (int)blockIdx.x + (int)gridDim.x, stages, mbar, st);
-  }
-  acc[0] = to_d(g_rr);
-  acc[1] = to_d(g_wr);
-  acc[2] = to_d(g_w);
-  acc[3] = to_d(g_r);
-  return ok;
+__device__ __forceinline__ void cp_async8_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
 template <int NPHI, typename T, typename V>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
+  using C = TileCfg<NPHI, T, V>;
+  constexpr int S = C::S, TT = C::TT, TR = C::TR, NPAD = C::NPAD, NB = C::NB, CPB = C::CPB, VPC = C::VPC;
+  constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG;
   extern __shared__ __align__(128) unsigned char stages[];
-  __shared__ __align__(8) uint64_t mbar[kStages];
+  __shared__ __align__(8) uint64_t full[S], gfull[S], empty[S];
+  __shared__ V s_rn[2][NB * NPHI];
+  __shared__ double s_Mref[NPHI * NPHI];
+  __shared__ volatile int s_stop;
   const unsigned nb = gridDim.x;
+  const int ne = a.ne;
+  const int ntiles = (ne + TT - 1) / TT;
+  const int nq = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)nb + 1 : 0;
+  const int64_t npv = (int64_t)ne * NPAD;
+  V* const pp = a.vec;
+  V* const xp = a.vec + npv;
+  auto rbuf = [&](int k) { return a.vec + (2 + (k & 1)) * npv; };
+  auto wbuf = [&](int k) { return a.vec + (4 + (k & 1)) * npv; };
+  auto sbuf = [&](int k) { return a.vec + (6 + (k & 1)) * npv; };
   unsigned long long epoch = 0;
-  const int64_t n = a.n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  V* p = a.vec;
-  V* const r0b = a.r0;
-  V* const r1b = a.vec + n;
-  V* const w0b = a.vec + 2 * n;
-  V* const w1b = a.vec + 3 * n;
-  V* const s0b = a.vec + 4 * n;
-  V* const s1b = a.vec + 5 * n;
-  double* part = a.part;
-  int it = 0;
-  double rr = 0.0, rr0 = 0.0, tot[4];
-  StageState st;
-  st.done = 0u;
-  st.issued = 0u;
+
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&mbar[i], 1);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&gfull[i], 32);
+      mbar_init(&empty[i], kCgConsumers / 32);
+    }
+    s_stop = 0;
     fence_proxy_async_smem();
   }
-  __syncthreads();
+  for (int i = threadIdx.x; i < NPHI * NPHI; i += blockDim.x) s_Mref[i] = a.Mref[i];
+
+  // prologue (all warps): padded copy of r0 and its sum; x = p = w = s = 0
+  bool pro_ok;
   {
-    // the first two tiles' couplings load while the prologue runs
-    using Cfg = TileCfg<NPHI, T>;
-    const int ntiles = (a.ne + Cfg::TT - 1) / Cfg::TT;
-    if ((int)blockIdx.x < ntiles) issue_next<NPHI, T, V>(a, (int)blockIdx.x, stages, mbar, st);
-    if ((int)blockIdx.x + (int)gridDim.x < ntiles)
-      issue_next<NPHI, T, V>(a, (int)blockIdx.x + (int)gridDim.x, stages, mbar, st);
-  }
-  // prologue: mean of r0; x = p = w = s = 0
-  {
-    V s = V(0);
-    for (int64_t row = t0; row < n; row += stride) {
-      s += r0b[row];
-      a.x[row] = V(0);
-      p[row] = V(0);
-      w0b[row] = V(0);
-      s0b[row] = V(0);
+    V* const r0p = rbuf(0);
+    V* const w0p = wbuf(0);
+    V* const s0p = sbuf(0);
+    const int64_t stride = (int64_t)nb * blockDim.x;
+    V sum = V(0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npv; i += stride) {
+      const int64_t tri = i / NPAD;
+      const int k = (int)(i - tri * NPAD);
+      const V r = k < NPHI ? a.r0[tri * NPHI + k] : V(0);
+      sum += r;
+      r0p[i] = r;
+      pp[i] = V(0);
+      xp[i] = V(0);
+      w0p[i] = V(0);
+      s0p[i] = V(0);
     }
-    double acc[4] = {to_d(s), 0.0, 0.0, 0.0};
-    if (!grid_allreduce4(a.bar, part, nb, epoch, a.timeout_ns, acc, tot)) goto done;
+    double acc[4] = {to_d(sum), 0.0, 0.0, 0.0}, tot[4];
+    pro_ok = __syncthreads_and(grid_allreduce4(a.bar, a.part, nb, epoch, a.timeout_ns, acc, tot)) != 0;
+    if (pro_ok && a.mean_zero) {
+      const V mu = (V)(tot[0] / (double)a.n);
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npv; i += stride)
+        if (i % NPAD < NPHI) r0p[i] -= mu;
+    }
+    if (pro_ok) pro_ok = grid_sync_epoch(a.bar, nb, epoch, a.timeout_ns);
   }
-  if (a.mean_zero) {
-    const V mu = (V)(tot[0] / (double)n);
-    for (int64_t row = t0; row < n; row += stride) r0b[row] -= mu;
-  }
-  if (!grid_sync_epoch(a.bar, nb, epoch, a.timeout_ns)) goto done;
-  {
-    V alpha = V(0), beta = V(0), muw = V(0);
-    double g_old = 0.0, a_old = 0.0, stop = 0.0;
-    int cur = 0;
-    for (int pass = 0;; ++pass) {
-      double acc[4];
-      const bool ok = cur == 0
-          ? cg_pass<NPHI, T, V>(a, alpha, beta, muw, r0b, w0b, s0b, r1b, w1b, s1b, p, stages, mbar, st, acc)
-          : cg_pass<NPHI, T, V>(a, alpha, beta, muw, r1b, w1b, s1b, r0b, w0b, s0b, p, stages, mbar, st, acc);
-      if (!ok) {
-        if (threadIdx.x == 0) atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
-        goto done;
+  // (no CTA-wide barrier below this point: the roles synchronise through mbarriers)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == kCouplingWarp) {
+    // ---- coupling producer (one thread): TMA bulk copies, S tiles ahead
+    if (lane != 0) return;
+    const uint64_t pol = l2_evict_first_policy();
+    unsigned g = 0;
+    if (pro_ok && nq > 0) {
+      for (;; ++g) {
+        const int s = (int)(g % S);
+        if (g >= (unsigned)S) {
+          const unsigned par = ((g / S) - 1u) & 1u;
+          bool got = false;
+          const uint64_t t0 = globaltimer_ns();
+          for (unsigned spins = 1;; ++spins) {
+            if (mbar_try_wait(&empty[s], par)) { got = true; break; }
+            if (s_stop) break;
+            if ((spins & 63u) == 0u && globaltimer_ns() - t0 > a.timeout_ns) {
+              atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
+              break;
+            }
+          }
+          if (!got) break;
+        }
+        const int tri0 = ((int)blockIdx.x + (int)(g % (unsigned)nq) * (int)nb) * TT;
+        const int nt = min(TT, ne - tri0);
+        const uint32_t bytes = (uint32_t)(nt * NPHI * 16);
+        unsigned char* dst = stages + (size_t)s * C::STAGE;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&full[s], bytes * NG);
+#pragma unroll 1
+        for (int c = 0; c < NG; ++c)
+          bulk_g2s_hint(dst + (size_t)c * TR * 16, a.vals + ((size_t)c * a.n + (size_t)tri0 * NPHI) * VEC, bytes,
+                        &full[s], pol);
       }
-      if (!grid_allreduce4(a.bar, part, nb, epoch, a.timeout_ns, acc, tot)) goto done;
-      cur ^= 1;
-      const double g = tot[0];
-      const double mu = a.mean_zero ? tot[2] / (double)n : 0.0;
-      const double d = tot[1] - mu * tot[3];  // (w - mu 1) . r
-      rr = g;
-      double an, bn;
+    }
+    // no CTA leaves with a bulk copy still writing its shared memory
+    for (unsigned h = g > (unsigned)S ? g - S : 0u; h < g; ++h)
+      if (!mbar_wait_bounded(&full[h % S], (h / S) & 1u, a.timeout_ns))
+        atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
+    return;
+  }
+
+  if (warp == kGatherWarp) {
+    // ---- gather producer (32 lanes): cp.async of r, w, s of the coupled
+    // blocks and of the own p, x (and areas), after the pass has been opened
+    constexpr int NBL = (NB + 31) / 32;
+    int cn[NBL];
+    auto load_cols = [&](unsigned gg, int (&c)[NBL]) {
+      const int tri0 = ((int)blockIdx.x + (int)(gg % (unsigned)nq) * (int)nb) * TT;
+      const int nt = min(TT, ne - tri0);
+#pragma unroll
+      for (int j = 0; j < NBL; ++j) {
+        const int b = lane + 32 * j;
+        c[j] = b < 4 * nt ? __ldg(a.cols + (size_t)(b & 3) * a.ne_pad + tri0 + (b >> 2)) : -1;
+      }
+    };
+    bool ok = pro_ok && nq > 0;
+    if (ok) load_cols(0u, cn);
+    for (unsigned g = 0; ok; ++g) {
+      const unsigned q = g % (unsigned)nq;
+      const int pass = (int)(g / (unsigned)nq);
+      if (q == 0) {
+        // The pass may be gathered once every CTA has arrived at the barrier
+        // that ends the previous one (the prologue's for pass 0): their vector
+        // writes are then complete.  The totals (alpha, beta) are not needed
+        // here, so these copies overlap the rest of the reduction.
+        int go = 0;  // 1: gather, 0: stop, -1: error
+        if (lane == 0) {
+          const unsigned long long target = (unsigned long long)(2 + pass) * nb;
+          const uint64_t t0 = globaltimer_ns();
+          for (unsigned spins = 1;; ++spins) {
+            unsigned long long v;
+            asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&a.bar->count) : "memory");
+            if (v >= target) { go = 1; break; }
+            if (s_stop) break;
+            if (*((volatile int*)&a.bar->status) != kStatusOk) break;
+            if ((spins & 63u) == 0u && globaltimer_ns() - t0 > a.timeout_ns) {
+              atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
+              go = -1;
+              break;
+            }
+          }
+        }
+        go = __shfl_sync(0xffffffffu, go, 0);
+        __syncwarp();  // orders the other lanes' copies after lane 0's acquire
+        if (go != 1) break;
+      }
+      const int s = (int)(g % S);
+      if (g >= (unsigned)S) {
+        const unsigned par = ((g / S) - 1u) & 1u;
+        bool got = false;
+        const uint64_t t0 = globaltimer_ns();
+        for (unsigned spins = 1;; ++spins) {
+          if (mbar_try_wait(&empty[s], par)) { got = true; break; }
+          if (s_stop) break;
+          if ((spins & 63u) == 0u && globaltimer_ns() - t0 > a.timeout_ns) break;
+        }
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0 && !s_stop) atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
+          break;
+        }
+      }
+      int cc[NBL];
+#pragma unroll
+      for (int j = 0; j < NBL; ++j) cc[j] = cn[j];
+      load_cols(g + 1u, cn);  // next tile's indices (the same tiles recur every pass)
+      const int tri0 = ((int)blockIdx.x + (int)q * (int)nb) * TT;
+      const int nt = min(TT, ne - tri0);
+      unsigned char* st = stages + (size_t)s * C::STAGE;
+      const V* ro = rbuf(pass);
+      const V* wo = wbuf(pass);
+      const V* so = sbuf(pass);
+#pragma unroll
+      for (int j = 0; j < NBL; ++j) {
+        if (cc[j] < 0) continue;
+        const int b = lane + 32 * j;
+        const int64_t src = (int64_t)cc[j] * NPAD;
+        unsigned char* d = st + C::GATHER + (size_t)b * NPAD * sizeof(V);
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) {
+          cp_async16(d + c * 16, ro + src + c * VPC);
+          cp_async16(d + (size_t)NB * NPAD * sizeof(V) + c * 16, wo + src + c * VPC);
+          cp_async16(d + (size_t)2 * NB * NPAD * sizeof(V) + c * 16, so + src + c * VPC);
+        }
+      }
+      const int own = nt * CPB;  // 16-byte chunks of one own vector
+      for (int c = lane; c < 2 * own; c += 32) {
+        const int v = c >= own ? 1 : 0;
+        const int cx = c - v * own;
+        cp_async16(st + C::OWN + (size_t)v * TT * NPAD * sizeof(V) + cx * 16,
+                   (v ? xp : pp) + (int64_t)tri0 * NPAD + cx * VPC);
+      }
+      if (a.coefM != V(0))
+        for (int c = lane; c < nt; c += 32) cp_async8_ca(st + C::AREA + c * 8, a.area + tri0 + c);
+      cp_async_arrive(&gfull[s]);
+    }
+    cp_async_wait_all();
+    return;
+  }
+
+  // ---- consumer warps: one matrix row per thread
+  int it = 0;
+  double rr = 0.0, rr0 = 0.0;
+  bool ok = pro_ok && nq > 0;
+  if (threadIdx.x == 0 && !ok) s_stop = 1;
+  {
+    V alpha = V(0), beta = V(0), muw = V(0), g_old = V(0), a_old = V(0);
+    double stop = 0.0;
+    const double inv_n = 1.0 / (double)a.n;
+    unsigned g = 0;  // this CTA's tile sequence number (continues across passes)
+    for (int pass = 0; ok; ++pass) {
+      V* const rn = rbuf(pass + 1);
+      V* const wn = wbuf(pass + 1);
+      V* const sn = sbuf(pass + 1);
+      V g_rr = V(0), g_wr = V(0), g_w = V(0), g_r = V(0);
+      for (int q = 0; q < nq; ++q, ++g) {
+        const int s = (int)(g % S);
+        const unsigned par = (g / S) & 1u;
+        const int tri0 = ((int)blockIdx.x + q * (int)nb) * TT;
+        const int nt = min(TT, ne - tri0);
+        bool got = mbar_wait_bounded(&full[s], par, a.timeout_ns);
+        got = got && mbar_wait_bounded(&gfull[s], par, a.timeout_ns);
+        const unsigned char* st = stages + (size_t)s * C::STAGE;
+        const V* gr = reinterpret_cast<const V*>(st + C::GATHER);
+        const V* gw = gr + NB * NPAD;
+        const V* gs = gw + NB * NPAD;
+        V* const xs_all = s_rn[g & 1u];
+        // new residual of the 4 coupled blocks of every tile triangle
+        for (int i = threadIdx.x; i < nt * 4 * NPHI; i += kCgConsumers) {
+          const int tb = i / NPHI, kk = i - tb * NPHI;
+          const int o = tb * NPAD + kk;
+          xs_all[i] = fma(-alpha, fma(beta, gs[o], gw[o] - muw), gr[o]);
+        }
+        if (!cbar_and(got)) {
+          ok = false;
+          break;
+        }
+        if ((int)threadIdx.x < nt * NPHI) {
+          const int lt = threadIdx.x / NPHI, k = threadIdx.x - lt * NPHI;
+          const V* xs = xs_all + lt * 4 * NPHI;
+          const unsigned char* sv = st + (size_t)threadIdx.x * 16;
+          V wv = V(0);
+#pragma unroll
+          for (int gg = 0; gg < NG; ++gg) {
+            typename ValOf<T>::type v[VEC];
+            lds_vals<T, VEC>(sv + (size_t)gg * TR * 16, v);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+              const int c = gg * VEC + u;
+              if (c < NC) wv = fma((V)v[u], xs[c], wv);
+            }
+          }
+          wv *= a.coefK;
+          if (a.coefM != V(0)) {
+            V mv = V(0);
+#pragma unroll
+            for (int kk = 0; kk < NPHI; ++kk) mv = fma((V)s_Mref[k * NPHI + kk], xs[kk], mv);
+            const double ar = reinterpret_cast<const double*>(st + C::AREA)[lt];
+            wv = fma(a.coefM * (V)ar, mv, wv);
+          }
+          const int o = lt * 4 * NPAD + k;  // own block of triangle lt among the gathered
+          const V* own = reinterpret_cast<const V*>(st + C::OWN);
+          const V r_old = gr[o];
+          const V w_old = gw[o] - muw;
+          const V s_old = gs[o];
+          const V p_old = own[lt * NPAD + k];
+          const V x_old = own[TT * NPAD + lt * NPAD + k];
+          const V p_new = fma(beta, p_old, r_old);
+          const V s_new = fma(beta, s_old, w_old);
+          const V r_new = xs[k];
+          const int64_t prow = (int64_t)(tri0 + lt) * NPAD + k;
+          pp[prow] = p_new;
+          xp[prow] = fma(alpha, p_new, x_old);
+          sn[prow] = s_new;
+          rn[prow] = r_new;
+          wn[prow] = wv;
+          g_rr = fma(r_new, r_new, g_rr);
+          g_wr = fma(wv, r_new, g_wr);
+          g_w += wv;
+          g_r += r_new;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+      }
+      if (!ok) break;
+      V acc[4] = {g_rr, g_wr, g_w, g_r};
+      double tot[4];
+      if (!consumer_allreduce4<V>(a.bar, a.part, nb, epoch, a.timeout_ns, acc, tot)) {
+        ok = false;
+        break;
+      }
+      // scalar recurrences in V: FP64 division is slow on this GPU and the
+      // FP32 inner solve carries its scalars in FP32 anyway
+      const double gg = tot[0];
+      const double mu = a.mean_zero ? tot[2] * inv_n : 0.0;
+      const V gv = (V)gg;
+      const V dv = (V)(tot[1] - mu * tot[3]);  // (w - mu 1) . r
+      rr = gg;
+      V an, bn;
       if (pass == 0) {
-        rr0 = g;
+        rr0 = gg;
         stop = a.stop_rel * a.stop_rel * rr0;
-        bn = 0.0;
-        an = g / d;
+        bn = V(0);
+        an = gv / dv;
       } else {
         ++it;
-        bn = g / g_old;
-        an = g / (d - bn * g / a_old);
+        bn = gv / g_old;
+        an = gv / (dv - bn * gv / a_old);
       }
-      if (!(g > stop) || it >= a.max_iters || !(an > 0.0) || !isfinite(an)) break;
-      g_old = g;
+      if (!(gg > stop) || it >= a.max_iters || !(an > V(0)) || !isfinite(an)) break;
+      g_old = gv;
       a_old = an;
-      alpha = (V)an;
-      beta = (V)bn;
+      alpha = an;
+      beta = bn;
       muw = (V)mu;
     }
   }
-done:
-  // no CTA leaves with a bulk copy still writing its shared memory
-  if (threadIdx.x == 0)
-    for (unsigned g = st.done; g < st.issued; ++g)
-      if (!mbar_wait_bounded(&mbar[g % kStages], (g / kStages) & 1u, a.timeout_ns))
-        atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
-  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!ok && pro_ok) atomicCAS(&a.bar->status, kStatusOk, kStatusTimeout);
+    s_stop = 1;  // the producer warps stop at their next wait
+  }
+  // the caller's x, unpadded (each thread wrote these rows itself in the last pass)
+  for (int q = 0; q < nq; ++q) {
+    const int tri0 = ((int)blockIdx.x + q * (int)nb) * TT;
+    const int nt = min(TT, ne - tri0);
+    if ((int)threadIdx.x < nt * NPHI) {
+      const int lt = threadIdx.x / NPHI, k = threadIdx.x - lt * NPHI;
+      a.x[(int64_t)tri0 * NPHI + threadIdx.x] = xp[(int64_t)(tri0 + lt) * NPAD + k];
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.res->iters = it;
     a.res->rr0 = rr0;
@@ -539,8 +714,8 @@ template <int NPHI, typename T, typename V>
 cudaError_t run_cg(const DevOp& op, const T* vals, V coefK, V coefM, int mean_zero, V* x, V* r, double stop_rel,
                    int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s, int* grid_used) {
   auto kern = k_cg<NPHI, T, V>;
-  using Cfg = TileCfg<NPHI, T>;
-  const size_t dyn = kStages * (size_t)Cfg::STAGE;
+  using Cfg = TileCfg<NPHI, T, V>;
+  const size_t dyn = Cfg::S * (size_t)Cfg::STAGE;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (err != cudaSuccess) return err;
   const int ntiles = (op.ne + Cfg::TT - 1) / Cfg::TT;
@@ -586,6 +761,15 @@ int cg_max_blocks(const DevOp& op, int prec) {
   return sms * 8;
 }
 
+// Bytes of the persistent CG's vectors: 8 vectors of ne blocks, each block
+// N_phi values padded to a whole number of 16-byte chunks (the larger of the
+// FP32 and FP64 layouts, so one buffer serves every precision).
+size_t cg_vec_bytes(const DevOp& op) {
+  const size_t pad32 = (size_t)(op.nphi + 3) / 4 * 4 * sizeof(float);
+  const size_t pad64 = (size_t)(op.nphi + 1) / 2 * 2 * sizeof(double);
+  return 8 * (size_t)op.ne * std::max(pad32, pad64) + 256;
+}
+
 #define DGSL_CG_CASES(T, V, VALS)                                                                              \
   switch (op.p) {                                                                                              \
     case 1: return run_cg<3, T, V>(op, VALS, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w, timeout_ns, s, grid_used);  \
@@ -614,3 +798,4 @@ cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, i
 }
 
 }  // namespace dgsl
+

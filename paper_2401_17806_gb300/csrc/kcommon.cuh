@@ -23,15 +23,19 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Barrier state in device memory (zeroed before every persistent launch):
-// a monotonic arrival counter, the epoch released by the last arriver of a
-// reducing barrier, the first error any CTA recorded, and the reduced totals.
-struct GridBarrier {
+// a monotonic arrival counter (alone in its 128-byte line: every CTA adds to
+// it), the epoch released by the last arriver of a reducing barrier, the first
+// error any CTA recorded, and the reduced totals (polled by every CTA).
+struct alignas(128) GridBarrier {
   unsigned long long count;
+  unsigned long long pad0[15];
   unsigned long long gen;
   int status;
   int pad;
   double total[4];
+  unsigned long long pad1[10];
 };
+static_assert(sizeof(GridBarrier) == 256, "GridBarrier is two 128-byte lines");
 
 // Sum of v over the block (blockDim.x a multiple of 32, <= 1024).  The
 // summation order is fixed by thread index, so it is deterministic.

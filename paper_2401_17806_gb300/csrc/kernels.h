@@ -80,7 +80,7 @@ struct CGResult {
   double rr;
 };
 struct CGWork {
-  void* vec = nullptr;    // 6 n vector elements: p, second r buffer, w and s double-buffered
+  void* vec = nullptr;    // cg_vec_bytes(op): p, x, r, w, s (r, w, s double-buffered), per-triangle padded
   double* part = nullptr; // max_parts x 4 partial sums
   GridBarrier* bar = nullptr;
   CGResult* res = nullptr;
@@ -93,6 +93,7 @@ cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, i
                           float* r, double stop_rel, int max_iters, const CGWork& w,
                           uint64_t timeout_ns, cudaStream_t s, int* grid_used);
 int cg_max_blocks(const DevOp& op, int prec);
+size_t cg_vec_bytes(const DevOp& op);
 // Bounded-wait self-test (see k_cg.cu): records kStatusTimeout in bar->status.
 cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s);
 

@@ -46,7 +46,7 @@ struct dgsl_operator {
     double* d64 = nullptr;
     float* r32 = nullptr;
     float* d32 = nullptr;
-    void* vec = nullptr;  // 6n doubles (covers 6n floats): persistent CG vectors
+    void* vec = nullptr;  // cg_vec_bytes(d): persistent CG vectors
     double* part = nullptr;
     double* part2 = nullptr;
     GridBarrier* bar = nullptr;
@@ -91,7 +91,7 @@ struct dgsl_operator {
     w.d64 = dalloc<double>(d.n);
     w.r32 = dalloc<float>(d.n);
     w.d32 = dalloc<float>(d.n);
-    w.vec = dalloc<double>(6 * d.n);
+    w.vec = dalloc<double>((cg_vec_bytes(d) + 7) / 8);
     w.part = dalloc<double>(4 * (size_t)w.max_parts);
     w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
     w.bar = dalloc<GridBarrier>(1);
