@@ -332,53 +332,67 @@ def batch_leg(args):
     ops = [dgsl.Operator(*synth.jittered_periodic_mesh(int(N), 1000 + i), int(p), store=store)
            for i, (N, p) in enumerate(zip(Ns, ps))]
     build_s = time.time() - t0
-    reqs, bufs = [], []
+    # one request per mesh with its R right-hand sides (they share the coupling
+    # stream), and the same right-hand sides as one request each
+    reqs, split, bufs = [], [], []
     for i, op in enumerate(ops):
-        for j in range(R):
-            b = fourier_rhs(op, 5000 + i * R + j, dt)
-            x = torch.zeros_like(b)
-            bufs.append((op, b, x))
-            reqs.append(dgsl.request(op, dgsl.SCHUR, dt, b, x))
+        b = torch.cat([fourier_rhs(op, 5000 + i * R + j, dt) for j in range(R)])
+        x = torch.zeros_like(b)
+        xs = torch.zeros_like(b)
+        bufs.append((op, b, x, xs))  # requests hold raw pointers: keep every tensor alive
+        reqs.append(dgsl.request(op, dgsl.SCHUR, dt, b, x, n_rhs=R))
+        n = op.n_dof
+        split += [dgsl.request(op, dgsl.SCHUR, dt, b[j * n:(j + 1) * n], xs[j * n:(j + 1) * n]) for j in range(R)]
     prec = dgsl.PREC_BF16_IR if args.precision == "bf16" else dgsl.PREC_F32_IR
     opts = dgsl.engine_opts(precision=prec)
-    dgsl.dgsl_cg_solve_batch(reqs[:min(8, len(reqs))], opts)   # warm-up
+    dgsl.dgsl_cg_solve_batch(reqs[:min(2, len(reqs))], opts)   # warm-up
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = dgsl.dgsl_launch_count()
-    ev0.record()
-    infos = dgsl.dgsl_cg_solve_batch(reqs, opts)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    launches = dgsl.dgsl_launch_count() - l0
+
+    def timed(rs):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = dgsl.dgsl_launch_count()
+        ev0.record()
+        out = dgsl.dgsl_cg_solve_batch(rs, opts)
+        ev1.record()
+        torch.cuda.synchronize()
+        return out, ev0.elapsed_time(ev1), dgsl.dgsl_launch_count() - l0
+
+    infos, ms, launches = timed(reqs)
+    sinfos, ms_split, _ = timed(split)
     ok = [i.status == dgsl.OK for i in infos]
-    dof_iters = sum(bufs[k][0].n_dof * infos[k].iters for k in range(len(reqs)))
-    # one-solve-at-a-time FP64 CG on a sample of the same requests
-    sample = rng.choice(len(reqs), size=min(16, len(reqs)), replace=False)
+    nrhs_total = len(split)
+    dof_iters = sum(ops[k // R].n_dof * sinfos[k].iters for k in range(nrhs_total))
+    # one-solve-at-a-time FP64 CG on a sample of the same right-hand sides
+    sample = rng.choice(nrhs_total, size=min(16, nrhs_total), replace=False)
     o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
     t64 = 0.0
     for k in sample:
-        op, b, _ = bufs[k]
-        x = torch.zeros_like(b)
+        op, b, _, _ = bufs[k // R]
+        n = op.n_dof
+        bk = b[(k % R) * n:(k % R + 1) * n].clone()
+        x = torch.zeros_like(bk)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        op.dgsl_cg_solve(dgsl.SCHUR, dt, b, x, opts=o64, check=False)
+        op.dgsl_cg_solve(dgsl.SCHUR, dt, bk, x, opts=o64, check=False)
         torch.cuda.synchronize()
         t64 += time.perf_counter() - t
     base_rate = len(sample) / t64
-    iters = sorted(i.iters for i in infos)
+    iters = sorted(i.iters for i in sinfos)
     line = {
         "metric": "batched Schur solves/s (one persistent launch)", "workload": "batch",
         "value": nsol / (ms * 1e-3), "unit": "solves/s",
-        "rhs_solves_per_s": len(reqs) / (ms * 1e-3), "dof_iters_per_s": dof_iters / (ms * 1e-3),
+        "rhs_solves_per_s": nrhs_total / (ms * 1e-3), "dof_iters_per_s": dof_iters / (ms * 1e-3),
+        "split_rhs_solves_per_s": nrhs_total / (ms_split * 1e-3),
+        "multi_rhs_speedup": ms_split / ms,
         "ms_total": ms, "gpu_launches": launches, "dtype": {"bf16": "bf16+f32+f64"}.get(args.precision, "f32+f64"),
         "config": {"solves": nsol, "rhs_per_solve": R, "N_range": [8, args.batch_nmax], "p_range": [1, 4],
                    "tol": WORKLOAD["tol"], "dt": dt, "operator_build_s": build_s,
                    "sample": f"{nsol} solves x {R} RHS (bounded sample of the 512-solve, N<=256 distribution)"},
-        "converged": int(sum(ok)), "requests": len(reqs), "iters_p50": iters[len(iters) // 2],
+        "converged": int(sum(ok)), "requests": len(reqs), "rhs": nrhs_total, "iters_p50": iters[len(iters) // 2],
         "iters_max": iters[-1], "max_relres": max(i.relres for i in infos),
-        "fp64_one_at_a_time": {"rhs_solves_per_s": base_rate, "sample_requests": len(sample),
-                               "speedup_rhs_solves_per_s": (len(reqs) / (ms * 1e-3)) / base_rate},
+        "split_converged": int(sum(i.status == dgsl.OK for i in sinfos)),
+        "fp64_one_at_a_time": {"rhs_solves_per_s": base_rate, "sample_rhs": len(sample),
+                               "speedup_rhs_solves_per_s": (nrhs_total / (ms * 1e-3)) / base_rate},
         "data": "synthetic",
     }
     print(json.dumps(line))
@@ -387,8 +401,8 @@ def batch_leg(args):
 def serve_leg(args):
     """Open-loop Poisson arrivals through the server: mesh N log-uniform in
     16..nmax (rounded to a pool of powers of two), p uniform in 1..4, 1..8 RHS
-    per request, FP32 inner CG + FP64 refinement to 1e-10.  Latency = last RHS
-    done - arrival.  Baseline: the same trace served FIFO by one-at-a-time
+    per request (one multi-RHS request each), FP32 inner CG + FP64 refinement
+    to 1e-10.  Latency = request done - arrival.  Baseline: the same trace served FIFO by one-at-a-time
     FP64 CG, with service times measured on this GPU for every pool operator."""
     import numpy as np
     import torch
@@ -402,17 +416,18 @@ def serve_leg(args):
     for N in sizes:
         for p in range(1, 5):
             op = dgsl.Operator(*synth.jittered_periodic_mesh(N, 300 + N + p), p)
-            rhs = [fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)]
+            rhs = torch.cat([fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)])
             pool[(N, p)] = (op, rhs)
     build_s = time.time() - t0
     # FP64 one-at-a-time service time per pool operator (one solve each)
     o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
     svc = {}
     for key, (op, rhs) in pool.items():
-        x = torch.zeros_like(rhs[0])
+        b0 = rhs[:op.n_dof].clone()
+        x = torch.zeros_like(b0)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        op.dgsl_cg_solve(dgsl.SCHUR, dt, rhs[0], x, opts=o64, check=False)
+        op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=o64, check=False)
         torch.cuda.synchronize()
         svc[key] = time.perf_counter() - t
     rng = np.random.default_rng(77)
@@ -424,24 +439,23 @@ def serve_leg(args):
         Nr = [min(sizes, key=lambda s: abs(np.log(s) - v)) for v in lnN]
         pr = rng.integers(1, 5, len(arr))
         kr = rng.integers(1, 9, len(arr))
-        xs = [[torch.zeros_like(pool[(int(N), int(p))][1][0]) for _ in range(int(k))]
+        xs = [torch.zeros(int(k) * pool[(int(N), int(p))][0].n_dof, dtype=torch.float64, device="cuda")
               for N, p, k in zip(Nr, pr, kr)]
         torch.cuda.synchronize()
         srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=40_000_000_000, idle_us=2000))
         owner, tickets = {}, []
         start = time.perf_counter()
         done_t = np.full(len(arr), np.nan)
-        left = np.array(kr, dtype=np.int64)
         outstanding = []
         i = 0
         while True:
             now = time.perf_counter() - start
             while i < len(arr) and arr[i] <= now:
                 op, rhs = pool[(int(Nr[i]), int(pr[i]))]
-                for j in range(int(kr[i])):
-                    t = srv.dgsl_submit(dgsl.request(op, dgsl.SCHUR, dt, rhs[j], xs[i][j]))
-                    owner[t] = i
-                    outstanding.append(t)
+                k = int(kr[i])
+                t = srv.dgsl_submit(dgsl.request(op, dgsl.SCHUR, dt, rhs[:k * op.n_dof], xs[i], n_rhs=k))
+                owner[t] = i
+                outstanding.append(t)
                 i += 1
             if outstanding:
                 flags, infos = srv.dgsl_poll_many(np.array(outstanding, dtype=np.uint64))
@@ -449,10 +463,7 @@ def serve_leg(args):
                 keep = []
                 for t, f in zip(outstanding, flags):
                     if f == 1:
-                        r = owner[t]
-                        left[r] -= 1
-                        if left[r] == 0:
-                            done_t[r] = tnow
+                        done_t[owner[t]] = tnow
                     else:
                         keep.append(t)
                 outstanding = keep

@@ -278,13 +278,18 @@ int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const 
 
 /* ------------------------------------------------------------ batched engine and serving */
 /* One solve request: op's Schur (coef = dt) or Helmholtz (coef = nu*dt)
- * system, b and x device double[n_dof] in op's internal order (caller-owned,
- * kept alive until the request completes).  tol <= 0 selects 1e-10.  Several
- * right-hand sides of one operator are several requests. */
+ * system with n_rhs right-hand sides (0 or 1: one; at most 8): b and x device
+ * double[n_rhs][n_dof] in op's internal order (caller-owned, kept alive until
+ * the request completes).  tol <= 0 selects 1e-10.  The right-hand sides of a
+ * request share every pass over op's couplings; each has its own refinement
+ * and inner CG and gets the same result, bit for bit, as when solved alone.
+ * The request's dgsl_solve_info reports the first non-OK status and the
+ * largest iteration count, refinement count and relative residual over its
+ * right-hand sides. */
 typedef struct {
   const dgsl_operator* op;
   int32_t kind;
-  int32_t pad;
+  int32_t n_rhs;
   double coef;
   const double* b;
   double* x;

@@ -122,7 +122,12 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
         for (int b = 1; b < 4; ++b) cols[(size_t)b * d.ne_pad + i] = hb.nbr[(size_t)i * 3 + b - 1];
       }
       d.cols = op->upload(cols);
-      d.area = op->upload(hb.area);
+      {
+        // two trailing zeros: the engine copies a tile's areas in whole 16-byte units
+        std::vector<double> a = hb.area;
+        a.resize(a.size() + 2, 0.0);
+        d.area = op->upload(a);
+      }
       d.Mref = op->upload(op->ro.Mref);
       if (o.store & DGSL_STORE_F64) d.K64 = op->upload(to_ell<double>(hb, d.n, cvt_d));
       if (o.store & DGSL_STORE_F32) d.K32 = op->upload(to_ell<float>(hb, d.n, cvt_f));

@@ -7,13 +7,18 @@
 namespace dgsl {
 
 constexpr int kMaxSlots = 4096;       // slots per engine (admitted over its lifetime)
+constexpr int kMaxRhs = 8;            // right-hand sides per slot
 
-// One solve, written by the host and copied into device memory when the engine
-// admits it.  All pointers are device pointers (the inbox itself is mapped host
-// memory).  fvec holds 8 n floats: r0 | d | p | r1 | w0 | w1 | s0 | s1.
+// One request (1..kMaxRhs right-hand sides of one operator), written by the
+// host and copied into device memory when the engine admits it.  All pointers
+// are device pointers (the inbox itself is mapped host memory).  b, x and r64
+// are [nrhs][n] doubles in the operator's order; fvec holds 8 FP32 vectors
+// d | p | r0 | r1 | w0 | w1 | s0 | s1 of ne blocks of bl floats (per triangle
+// N_phi x rp values, right-hand side innermost); part holds 32 doubles per chunk.
 struct BSlotDesc {
   int p, ne, ne_pad, mean_zero;
   long long n;
+  int nrhs, rp, bl, pad0;
   const double* K64;        // FP64 couplings (refinement residual)
   const void* Kin;          // inner couplings, float or bf16 bits (engine type)
   const int32_t* cols;
@@ -24,14 +29,17 @@ struct BSlotDesc {
   double* x;
   double* r64;
   float* fvec;
-  double* part;             // [nchunk][4]
+  double* part;
   double tol, inner_tol;
   int max_iters, max_refine;
   int nchunk, chunk_tris;
   long long ticket;
 };
+static_assert(sizeof(BSlotDesc) % 8 == 0, "descriptor is copied in 8-byte words");
 
-// Completion record of a slot (mapped host memory, written once by the engine).
+// Completion record of a slot (mapped host memory, written once by the engine);
+// over the slot's right-hand sides: the first non-OK status, the largest
+// iteration and refinement counts and the largest relative residual.
 struct BCompletion {
   int done;                 // 0 while pending; 1 when the fields below are final
   int status;               // DGSL_OK / DGSL_ENOTCONV / DGSL_ETIMEOUT
@@ -68,6 +76,11 @@ struct EngineParams {
 // Triangles per chunk for degree p (a multiple of the CG tile, itself a
 // multiple of 4 triangles).
 int engine_chunk_tris(int p);
+// Device workspace of one request (r64 | fvec | partials) and the descriptor
+// fields that point into it (also sets rp, bl, chunk_tris, nchunk from p, ne,
+// n and nrhs).
+size_t engine_workspace_bytes(int p, int ne, int nrhs);
+void engine_fill_workspace(BSlotDesc& s, char* ws);
 // Device bytes of the engine-owned areas (slot copies, state, shared words,
 // lists) and their layout inside one allocation of that size.
 size_t engine_state_bytes();

@@ -67,12 +67,12 @@ struct EngineRes {
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
-// Device workspace of one request: r64 (8n) | fvec (32n) | partials (32 per chunk).
-size_t request_workspace(const dgsl_operator* op) {
-  const int64_t n = op->d.n;
-  const int ct = engine_chunk_tris(op->d.p);
-  const int nchunk = (op->d.ne + ct - 1) / ct;
-  return align256(8 * (size_t)n) + align256(32 * (size_t)n) + align256(32 * (size_t)nchunk);
+int request_nrhs(const dgsl_request& r) { return r.n_rhs < 1 ? 1 : r.n_rhs; }
+
+// Device workspace of one request (engine_workspace_bytes: FP64 residuals,
+// padded FP32 CG vectors, per-chunk partial sums).
+size_t request_workspace(const dgsl_operator* op, int nrhs) {
+  return align256(engine_workspace_bytes(op->d.p, op->d.ne, nrhs));
 }
 
 int check_request(const dgsl_request& r, const dgsl_engine_opts& o, std::string& why) {
@@ -80,6 +80,7 @@ int check_request(const dgsl_request& r, const dgsl_engine_opts& o, std::string&
   if (r.op->host_only) return why = "operator was built host-only", DGSL_ENODEVICE;
   if (r.op->d.device != o.device) return why = "operator lives on another device", DGSL_EINVAL;
   if (!r.b || !r.x) return why = "request vectors must be non-NULL", DGSL_EINVAL;
+  if (r.n_rhs < 0 || r.n_rhs > kMaxRhs) return why = "n_rhs must be 0..8", DGSL_EINVAL;
   if (r.kind != DGSL_SCHUR && r.kind != DGSL_HELMHOLTZ) return why = "bad request kind", DGSL_EINVAL;
   if (!(r.coef >= 0.0) || !std::isfinite(r.coef)) return why = "coef must be finite and >= 0", DGSL_EINVAL;
   if (!r.op->d.K64) return why = "FP64 couplings are needed", DGSL_EINVAL;
@@ -96,6 +97,7 @@ BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, 
   s.ne_pad = d.ne_pad;
   s.mean_zero = r.kind == DGSL_SCHUR;
   s.n = d.n;
+  s.nrhs = request_nrhs(r);
   s.K64 = d.K64;
   s.Kin = o.precision == DGSL_PREC_BF16_IR ? (const void*)d.K16 : (const void*)d.K32;
   s.cols = d.cols;
@@ -105,16 +107,12 @@ BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, 
   s.coefM = r.kind == DGSL_SCHUR ? 0.0 : 1.0;
   s.b = r.b;
   s.x = r.x;
-  s.r64 = reinterpret_cast<double*>(ws);
-  s.fvec = reinterpret_cast<float*>(ws + align256(8 * (size_t)d.n));
-  s.part = reinterpret_cast<double*>(ws + align256(8 * (size_t)d.n) + align256(32 * (size_t)d.n));
   s.tol = r.tol > 0.0 ? r.tol : 1e-10;
   s.inner_tol = o.inner_tol;
   s.max_iters = o.max_iters;
   s.max_refine = o.max_refine;
-  s.chunk_tris = engine_chunk_tris(d.p);
-  s.nchunk = (d.ne + s.chunk_tris - 1) / s.chunk_tris;
   s.ticket = (long long)ticket;
+  engine_fill_workspace(s, ws);
   return s;
 }
 
@@ -169,7 +167,7 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
     size_t total = 0;
     for (int i = 0; i < n; ++i) {
       off[i] = total;
-      total += request_workspace(reqs[i].op);
+      total += request_workspace(reqs[i].op, request_nrhs(reqs[i]));
     }
     char* ws = nullptr;
     if (cudaMalloc(&ws, total) != cudaSuccess) throw Error(DGSL_ENOMEM, "batch workspace allocation failed");
@@ -428,7 +426,7 @@ extern "C" int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* 
   if (int e = check_request(*req, srv->o, why)) return dgsl_set_last_error(why), e;
   Request q;
   q.r = *req;
-  q.ws_bytes = request_workspace(req->op);
+  q.ws_bytes = request_workspace(req->op, request_nrhs(*req));
   if ((int64_t)q.ws_bytes + req->op->device_bytes > srv->o.hbm_budget_bytes ||
       q.ws_bytes > srv->arena.bytes)
     return dgsl_set_last_error("request can never fit the memory budget"), DGSL_EBUDGET;

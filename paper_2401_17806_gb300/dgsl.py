@@ -67,8 +67,11 @@ class dgsl_solve_info(C.Structure):
                 ("grid", C.c_int32), ("pad", C.c_int32)]
 
 
+MAX_RHS = 8  # right-hand sides per engine request
+
+
 class dgsl_request(C.Structure):
-    _fields_ = [("op", C.c_void_p), ("kind", C.c_int32), ("pad", C.c_int32), ("coef", C.c_double),
+    _fields_ = [("op", C.c_void_p), ("kind", C.c_int32), ("n_rhs", C.c_int32), ("coef", C.c_double),
                 ("b", C.c_void_p), ("x", C.c_void_p), ("tol", C.c_double)]
 
 
@@ -328,10 +331,14 @@ def engine_opts(**kw):
     return o
 
 
-def request(op, kind, coef, b, x, tol=0.0):
-    """dgsl_request for device tensors b, x (float64, op.n_dof elements)."""
-    return dgsl_request(op.h.value, int(kind), 0, float(coef), _dptr(b, "float64", op.n_dof).value,
-                        _dptr(x, "float64", op.n_dof).value, float(tol))
+def request(op, kind, coef, b, x, tol=0.0, n_rhs=1):
+    """dgsl_request for device tensors b, x (float64, n_rhs * op.n_dof elements).
+    The request holds raw device pointers: keep b and x alive until it completes."""
+    if not 1 <= int(n_rhs) <= MAX_RHS:
+        raise DgslError(EINVAL, f"n_rhs must be 1..{MAX_RHS}")
+    m = int(n_rhs) * op.n_dof
+    return dgsl_request(op.h.value, int(kind), int(n_rhs), float(coef), _dptr(b, "float64", m).value,
+                        _dptr(x, "float64", m).value, float(tol))
 
 
 def dgsl_cg_solve_batch(reqs, opts=None, stream=None, check=False):

@@ -1,7 +1,8 @@
 """GPU parity of the batched persistent engine (many solves, different meshes,
-degrees and kinds, in one launch) and of the serving loop (continuous
-batching under a memory budget), through the C-ABI, against the oracle's FP64
-operators; each result must be the same alone and in the mix."""
+degrees and kinds, in one launch; requests with several right-hand sides) and
+of the serving loop (continuous batching under a memory budget), through the
+C-ABI, against the oracle's FP64 operators; each result must be the same alone,
+in the mix and inside a multi-RHS request."""
 import time
 
 import numpy as np
@@ -113,6 +114,56 @@ def test_batch_zero_rhs_and_validation(problems):
     bad = dgsl.request(op, 5, coef, bd, bd.clone())
     with pytest.raises(dgsl.DgslError):
         dgsl.dgsl_cg_solve_batch([bad], dgsl.engine_opts())
+
+
+@pytest.mark.parametrize("R", [3, 8])
+def test_batch_multi_rhs_equals_single(problems, R):
+    """A request with R right-hand sides shares the coupling stream but gives
+    every right-hand side the same result, bit for bit, as a request of its
+    own; results meet the oracle's residual bar."""
+    from paper_2401_17806_gb300 import dgsl
+    opts = dgsl.engine_opts(precision=dgsl.PREC_F32_IR)
+    for k in (1, 3, 5):
+        op, orc, perm, kind, coef, b = problems[k]
+        bs = [synth.standard_normal(op.n_dof, 900 + 17 * k + j) for j in range(R)]
+        if R == 3:
+            bs[1] = np.zeros(op.n_dof)  # a zero right-hand side inside a block
+        bd = torch.tensor(np.concatenate([to_internal(v, perm, op.n_phi) for v in bs]), device="cuda")
+        xd = torch.full_like(bd, np.nan)
+        info = dgsl.dgsl_cg_solve_batch([dgsl.request(op, kind, coef, bd, xd, n_rhs=R)], opts)[0]
+        torch.cuda.synchronize()
+        assert info.status == dgsl.OK, info.status
+        xs = xd.cpu().numpy().reshape(R, -1)
+        singles, keep, reqs = [], [], []
+        for j in range(R):
+            bj = bd[j * op.n_dof:(j + 1) * op.n_dof].clone()
+            xj = torch.full_like(bj, np.nan)
+            keep.append(bj)  # requests hold raw pointers: the tensors must stay alive
+            singles.append(xj)
+            reqs.append(dgsl.request(op, kind, coef, bj, xj))
+        infos = dgsl.dgsl_cg_solve_batch(reqs, opts)
+        torch.cuda.synchronize()
+        for j in range(R):
+            assert infos[j].status == dgsl.OK
+            assert np.array_equal(singles[j].cpu().numpy(), xs[j])
+            if not np.any(bs[j]):
+                assert np.all(xs[j] == 0)
+            else:
+                _check_residual(orc, kind, coef, bs[j], to_natural(xs[j], perm, op.n_phi), 2e-10)
+        assert info.iters == max(i.iters for i in infos)
+        assert info.relres == max(i.relres for i in infos)
+
+
+def test_batch_rejects_bad_n_rhs(problems):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, perm, kind, coef, b = problems[0]
+    bd = torch.zeros(9 * op.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgsl.DgslError):
+        dgsl.request(op, kind, coef, bd, bd.clone(), n_rhs=9)
+    r = dgsl.request(op, kind, coef, bd[:op.n_dof], bd[:op.n_dof].clone())
+    r.n_rhs = 9
+    with pytest.raises(dgsl.DgslError):
+        dgsl.dgsl_cg_solve_batch([r], dgsl.engine_opts())
 
 
 def test_server_continuous_batching(problems):
