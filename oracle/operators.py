@@ -162,6 +162,14 @@ class Operators:
              + np.einsum("jkl,jl->jk", self.bl.U[:, 1], vbar[lr[:, 1]]))
         return np.einsum("jkl,jl->jk", self.Minv, t).ravel()
 
+    # -- velocity update of eq. nc.2 ---------------------------------------
+    def velocity_update(self, F, p, coef):
+        """Eq. nc.2 without its source terms, solved for the new dual velocity:
+        vhat_j = F_j - coef Mhat_j^{-1} (Q_lj p_l + Q_rj p_r), F a vector dual
+        field [2, Nd, Npsi] (flattened), p a main field.  coef is dt for the
+        paper's pressure; dt^2 for the p of S p = G^T F (S = dt^2 G^T Mhat^-1 G)."""
+        return np.asarray(F, dtype=float).ravel() - coef * self.apply_Mhat_inv(self.G @ p)
+
 
 def project_mean(v):
     return v - v.mean()

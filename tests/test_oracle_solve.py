@@ -69,3 +69,34 @@ def test_manufactured_convergence_order(p):
         errs.append(OF.l2_error(c, p, x, lambda X, Y: synth.manufactured_pressure(X, Y)[0]))
     order = np.log2(errs[0] / errs[1])
     assert order >= p + 0.5, (errs, order)
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_velocity_update_is_divergence_free(p):
+    """Projection of eqs. nc.1-nc.2: with S p = G^T F the updated velocity
+    vhat = F - dt^2 Mhat^{-1} G p has zero discrete divergence, both as G^T vhat
+    and with the paper's divergence D assembled on its own (D = -Q^T)."""
+    op = _ops(6, p, seed=5)
+    dt = 0.02
+    F = synth.standard_normal(2 * op.nd * op.npsi, 61)
+    b = op.G.T @ F
+    pr = OP.schur_solve_direct(op.schur_matrix(dt), b)
+    v = op.velocity_update(F, pr, dt * dt)
+    assert np.linalg.norm(op.G.T @ v) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(op.Dm @ v) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(v - F) > 1e-3 * np.linalg.norm(F)  # something was removed
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_velocity_update_removes_discrete_gradients(p):
+    """A dual field that is itself dt^2 Mhat^{-1} G q (a discrete pressure
+    gradient) is projected to zero: the solve recovers q up to a constant and
+    G annihilates constants."""
+    op = _ops(5, p, seed=8)
+    dt = 0.05
+    q = synth.standard_normal(op.n, 62)
+    F = dt * dt * op.apply_Mhat_inv(op.G @ q)
+    pr = OP.schur_solve_direct(op.schur_matrix(dt), op.G.T @ F)
+    np.testing.assert_allclose(pr, q - q.mean(), atol=1e-8 * np.abs(q).max())
+    v = op.velocity_update(F, pr, dt * dt)
+    assert np.linalg.norm(v) <= 1e-9 * np.linalg.norm(F)
