@@ -41,7 +41,7 @@ NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 171.3}
 
 
 def workload_name(args):
-    return (f"pressure Schur + 2 viscous Helmholtz solves to 1e-10, {args.N}x{args.N} jittered "
+    return (f"pressure Schur solve + velocity update + 2 viscous Helmholtz solves to 1e-10, {args.N}x{args.N} jittered "
             f"periodic mesh, p={args.p}")
 
 
@@ -165,7 +165,9 @@ def bytes_per_row_iter(nphi, coupling_bytes, vec_bytes):
 
 
 class Stage:
-    """Device buffers and the calls of one implicit stage."""
+    """Device buffers and the calls of one implicit stage: divergence of the dual
+    velocity, the two d2m right-hand sides, the pressure Schur solve, the velocity
+    update of the projection and the two viscous Helmholtz solves."""
 
     def __init__(self, op, vhat_np, precision):
         import torch
@@ -178,6 +180,7 @@ class Stage:
         self.bH = torch.empty(2 * n, dtype=torch.float64, device="cuda")
         self.p = torch.empty(n, dtype=torch.float64, device="cuda")
         self.vbar = torch.empty(2 * n, dtype=torch.float64, device="cuda")
+        self.vnew = torch.empty_like(self.vhat)
         prec = {"f32": dgsl.PREC_F32_IR, "bf16": dgsl.PREC_BF16_IR, "f64": dgsl.PREC_F64}[precision]
         self.opts = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=prec)
 
@@ -187,6 +190,8 @@ class Stage:
         op.dgsl_apply_div(self.vhat, self.bS, stream=stream)
         op.dgsl_project_d2m_rhs(self.vhat, self.bH, n_rhs=2, stream=stream)
         infos = op.dgsl_cg_solve(d.SCHUR, WORKLOAD["dt"], self.bS, self.p, opts=o, stream=stream)
+        # velocity update of the projection (eq. nc.2): vnew = vhat - dt^2 Mhat^-1 G p
+        op.dgsl_velocity_update(WORKLOAD["dt"] ** 2, self.vhat, self.p, self.vnew, stream=stream)
         infos += op.dgsl_cg_solve(d.HELMHOLTZ, WORKLOAD["nu"] * WORKLOAD["dt"], self.bH, self.vbar,
                                   n_rhs=2, opts=o, stream=stream)
         for i in infos:
@@ -246,10 +251,17 @@ def gpu_leg(args, rank, world, local):
                cg_launches=sum(i.cg_launches for i in infos), grid=infos[0].grid,
                clocks=clk, build_s=build_s, op=op, stage=st, stream=stream,
                iters_total=sum(i.iters for i in infos), device_bytes=op.device_bytes)
+    # divergence of the projected velocity relative to that of the input (eq. nc.1)
+    with torch.cuda.stream(stream):
+        ydiv = torch.empty_like(st.bS)
+        op.dgsl_apply_div(st.vnew, ydiv, stream=stream)
+    stream.synchronize()
+    res["div_rel"] = float(torch.linalg.norm(ydiv) / torch.linalg.norm(st.bS))
     # ---- end to end: pinned host input -> device, stage, device -> pinned host
     vh_host = torch.from_numpy(vhat.ravel().copy()).pin_memory()
     p_host = torch.empty(op.n_dof, dtype=torch.float64).pin_memory()
     v_host = torch.empty(2 * op.n_dof, dtype=torch.float64).pin_memory()
+    vn_host = torch.empty(st.vnew.numel(), dtype=torch.float64).pin_memory()
     barrier()
     e_infos = []
     with torch.cuda.stream(stream):
@@ -259,13 +271,14 @@ def gpu_leg(args, rank, world, local):
             e_infos += st.run(stream)
             p_host.copy_(st.p, non_blocking=True)
             v_host.copy_(st.vbar, non_blocking=True)
+            vn_host.copy_(st.vnew, non_blocking=True)
         ev1.record(stream)
     stream.synchronize()
     barrier()
     res["e2e_ms"] = ev0.elapsed_time(ev1)
     res["e2e_dof_iters"] = sum(op.n_dof * i.iters for i in e_infos)
     res["h2d"] = vh_host.numel() * 8
-    res["d2h"] = (p_host.numel() + v_host.numel()) * 8
+    res["d2h"] = (p_host.numel() + v_host.numel() + vn_host.numel()) * 8
     # ---- one-solve-at-a-time FP64 CG on the same stage
     if not args.no_fp64_baseline and args.precision != "f64":
         o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
@@ -661,6 +674,7 @@ def main():
             "helmholtz_iters_per_step": res["helm_iters_per_step"],
             "refinements_per_step": res["refinements"],
             "max_relres": res["relres_max"],
+            "projected_velocity_div_rel": res["div_rel"],
             "operator_build_s": res["build_s"],
             "cg_grid_ctas": res["grid"],
         },

@@ -200,6 +200,18 @@ int dgsl_project_m2d(const dgsl_operator* op, const double* vbar, double* vhat, 
 int dgsl_apply_div(const dgsl_operator* op, const double* vhat, double* y, int n_rhs,
                    void* stream);
 
+/* Velocity update of the pressure projection (eq. nc.2 solved for the new
+ * dual velocity, its gravity / buoyancy source terms left to the caller):
+ *   v_j = F_j - coef Mhat_j^{-1} (Q_lj p_l + Q_rj p_r)
+ * for n_rhs vector dual fields F, v [n_rhs][2][n_edge][n_psi] and main fields
+ * p [n_rhs][n_dof] (device, internal orders; v may be F).  coef = dt for the
+ * paper's pressure; for the p of dgsl_cg_solve(DGSL_SCHUR, dt, b = G^T F)
+ * (S = dt^2 G^T Mhat^-1 G) coef = dt^2, and then G^T v = b - S p: the
+ * divergence of v is the pressure solve's residual (eq. nc.1).  Needs an
+ * operator built with opts.factored (DGSL_EINVAL otherwise). */
+int dgsl_velocity_update(const dgsl_operator* op, double coef, const double* F, const double* p,
+                         double* v, int n_rhs, void* stream);
+
 /* ------------------------------------------------------------ solves */
 enum { DGSL_SCHUR = 0, DGSL_HELMHOLTZ = 1 };
 enum {

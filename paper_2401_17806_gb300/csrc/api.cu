@@ -318,6 +318,23 @@ int dgsl_apply_div(const dgsl_operator* op, const double* vhat, double* y, int n
   });
 }
 
+int dgsl_velocity_update(const dgsl_operator* op, double coef, const double* F, const double* p, double* v,
+                         int n_rhs, void* stream) {
+  DGSL_TRY({
+    check_dev(op);
+    if (int e = check_vec_args(F, v, n_rhs)) return e;
+    if (!p) return fail(DGSL_EINVAL, "p must be non-NULL");
+    if (!std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite");
+    if (!op->d.G || !op->d.Minv) return fail(DGSL_EINVAL, "the velocity update needs opts.factored");
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    const size_t nv = (size_t)2 * op->d.nd * op->d.npsi;
+    for (int k = 0; k < n_rhs; ++k)
+      DGSL_CUDA(launch_velocity_update(op->d, coef, F + k * nv, p + (size_t)k * op->d.n, v + k * nv,
+                                       (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ solve driver

@@ -340,6 +340,63 @@ cudaError_t launch_d2m_rhs(const DevOp& op, const double* vhat, double* b, cudaS
   return cudaGetLastError();
 }
 
+// Velocity update of eq. nc.2 (source terms left to the caller), one warp per
+// edge:  vhat[c][e] = F[c][e] - coef Mhat_e^{-1} (G_l[c] p_l + G_r[c] p_r).
+// Every element is read and written by one thread, so v may be F.
+template <int P, int NPHI, int NPSI>
+__global__ void __launch_bounds__(128) k_vel_update(const double* __restrict__ G, const double* __restrict__ Minv,
+                                                    const int32_t* __restrict__ elr, int nd, double coef,
+                                                    const double* F, const double* __restrict__ pr, double* v) {
+  __shared__ double t_s[4][2 * NPSI];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int e = blockIdx.x * wpb + w; e < nd; e += gridDim.x * wpb) {
+    const int tl = __ldg(elr + 2 * e), tr = __ldg(elr + 2 * e + 1);
+    for (int o = lane; o < 2 * NPSI; o += 32) {
+      const int c = o / NPSI, l = o % NPSI;
+      const int ml = c_dl[P][l], mr = c_dr[P][l];
+      double acc = 0.0;
+      if (ml >= 0) {
+        const double* row = G + (((size_t)e * 2 + 0) * 2 + c) * NPHI * NPHI + ml * NPHI;
+#pragma unroll
+        for (int k = 0; k < NPHI; ++k) acc = fma(__ldg(row + k), __ldg(pr + (size_t)tl * NPHI + k), acc);
+      }
+      if (mr >= 0) {
+        const double* row = G + (((size_t)e * 2 + 1) * 2 + c) * NPHI * NPHI + mr * NPHI;
+#pragma unroll
+        for (int k = 0; k < NPHI; ++k) acc = fma(__ldg(row + k), __ldg(pr + (size_t)tr * NPHI + k), acc);
+      }
+      t_s[w][o] = acc;
+    }
+    __syncwarp();
+    for (int o = lane; o < 2 * NPSI; o += 32) {
+      const int c = o / NPSI, l = o % NPSI;
+      const double* Mi = Minv + (size_t)e * NPSI * NPSI + l * NPSI;
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < NPSI; ++q) acc = fma(__ldg(Mi + q), t_s[w][c * NPSI + q], acc);
+      const size_t idx = ((size_t)c * nd + e) * NPSI + l;
+      v[idx] = F[idx] - coef * acc;
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_velocity_update(const DevOp& op, double coef, const double* F, const double* pr, double* v,
+                                   cudaStream_t s) {
+  if (!op.G || !op.Minv) return cudaErrorInvalidValue;
+  const int wpb = 4;
+  const int blocks = std::max(1, std::min((op.nd + wpb - 1) / wpb, 152 * 16));
+  switch (op.p) {
+    case 1: k_vel_update<1, 3, 4><<<blocks, 32 * wpb, 0, s>>>(op.G, op.Minv, op.elr, op.nd, coef, F, pr, v); break;
+    case 2: k_vel_update<2, 6, 9><<<blocks, 32 * wpb, 0, s>>>(op.G, op.Minv, op.elr, op.nd, coef, F, pr, v); break;
+    case 3: k_vel_update<3, 10, 16><<<blocks, 32 * wpb, 0, s>>>(op.G, op.Minv, op.elr, op.nd, coef, F, pr, v); break;
+    case 4: k_vel_update<4, 15, 25><<<blocks, 32 * wpb, 0, s>>>(op.G, op.Minv, op.elr, op.nd, coef, F, pr, v); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_m2d(const DevOp& op, const double* vbar, double* vhat, cudaStream_t s) {
   if (!op.Uloc || !op.Minv) return cudaErrorInvalidValue;
   const int g = std::max(1, std::min((op.nd + 3) / 4, 152 * 16));

@@ -51,6 +51,8 @@ cudaError_t launch_apply_factored_f64(const DevOp& op, double coefK, double coef
 cudaError_t launch_d2m_rhs(const DevOp& op, const double* vhat, double* b, cudaStream_t s);
 cudaError_t launch_m2d(const DevOp& op, const double* vbar, double* vhat, cudaStream_t s);
 cudaError_t launch_div(const DevOp& op, const double* vhat, double* y, cudaStream_t s);
+cudaError_t launch_velocity_update(const DevOp& op, double coef, const double* F, const double* pr, double* v,
+                                   cudaStream_t s);
 
 // ---- vector helpers for the refinement loop
 // r = b - A x (FP64 assembled form, A = coefM Mbar + coefK K), optional mean

@@ -108,6 +108,8 @@ _SIGS = {
     "dgsl_project_d2m_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dgsl_project_m2d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dgsl_apply_div": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dgsl_velocity_update": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_void_p]),
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
@@ -283,6 +285,13 @@ class Operator:
         _check(load().dgsl_apply_div(self.h, _dptr(vhat, "float64", 2 * self.n_dual * n_rhs),
                                      _dptr(y, "float64", self.n_dof * n_rhs), int(n_rhs),
                                      _stream(stream)))
+
+    def dgsl_velocity_update(self, coef, F, p, v, n_rhs=1, stream=None):
+        """v = F - coef Mhat^-1 G p (eq. nc.2); F, v vector dual fields, p main fields."""
+        _check(load().dgsl_velocity_update(self.h, float(coef), _dptr(F, "float64", 2 * self.n_dual * n_rhs),
+                                           _dptr(p, "float64", self.n_dof * n_rhs),
+                                           _dptr(v, "float64", 2 * self.n_dual * n_rhs), int(n_rhs),
+                                           _stream(stream)))
 
     def dgsl_cg_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, check=True):
         """Returns a list of dgsl_solve_info (one per right-hand side)."""

@@ -119,6 +119,67 @@ def test_projections_and_divergence(dgsl_lib, N, p):
     assert rel(got_y, -(orc.Dm @ vv.ravel())) <= 1e-13
 
 
+@pytest.mark.parametrize("N,p", [(8, 1), (9, 2), (10, 3), (7, 4)])
+def test_velocity_update_parity(dgsl_lib, N, p):
+    """v = F - c Mhat^-1 G p (eq. nc.2) against the oracle, out of place and in place."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(N, p, 12)
+    ep = m["edge_perm"]
+    F = synth.standard_normal((2, op.n_edge, op.n_psi), 31)
+    pr = synth.standard_normal(op.n_dof, 32)
+    c = 0.37
+    Fd = dev(F[:, ep].ravel())
+    pd = dev(to_internal(pr, m["perm"], op.n_phi))
+    vd = torch.empty_like(Fd)
+    op.dgsl_velocity_update(c, Fd, pd, vd)
+    torch.cuda.synchronize()
+    got = np.empty_like(F)
+    got[:, ep] = vd.cpu().numpy().reshape(2, op.n_edge, op.n_psi)
+    want = orc.velocity_update(F.ravel(), pr, c)
+    assert rel(got.ravel(), want) <= 1e-13
+    op.dgsl_velocity_update(c, Fd, pd, Fd)  # in place
+    torch.cuda.synchronize()
+    assert torch.equal(Fd, vd)
+
+
+def test_pressure_projection_divergence_free(dgsl_lib):
+    """The whole projection on the device: b = G^T F, S p = b (FP32 CG + FP64
+    refinement to 1e-12), v = F - dt^2 Mhat^-1 G p; the divergence of v is the
+    solve's residual, checked on the device and with the oracle's separately
+    assembled divergence D."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(14, 3, 13)
+    ep = m["edge_perm"]
+    dt = 1e-2
+    F = synth.standard_normal((2, op.n_edge, op.n_psi), 33)
+    Fd = dev(F[:, ep].ravel())
+    b = torch.empty(op.n_dof, dtype=torch.float64, device="cuda")
+    op.dgsl_apply_div(Fd, b)
+    pd = torch.zeros_like(b)
+    info = op.dgsl_cg_solve(dgsl.SCHUR, dt, b, pd, opts=dgsl.solve_opts(tol=1e-12, precision=dgsl.PREC_F32_IR))[0]
+    assert info.status == dgsl.OK
+    vd = torch.empty_like(Fd)
+    op.dgsl_velocity_update(dt * dt, Fd, pd, vd)
+    y = torch.empty_like(b)
+    op.dgsl_apply_div(vd, y)
+    torch.cuda.synchronize()
+    bn = float(torch.linalg.norm(b))
+    assert float(torch.linalg.norm(y)) <= 2e-12 * bn
+    v = np.empty_like(F)
+    v[:, ep] = vd.cpu().numpy().reshape(2, op.n_edge, op.n_psi)
+    assert np.linalg.norm(orc.Dm @ v.ravel()) <= 2e-12 * bn
+    assert np.linalg.norm(v - F) > 1e-3 * np.linalg.norm(F)
+
+
+def test_velocity_update_needs_factored_blocks(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(6, 2, 14, factored=False)
+    Fd = torch.zeros(2 * op.n_dual, dtype=torch.float64, device="cuda")
+    pd = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(dgsl.DgslError):
+        op.dgsl_velocity_update(1.0, Fd, pd, Fd.clone())
+
+
 def test_full_size_sampled_rows(dgsl_lib):
     """256 x 256 mesh, p = 3 (131,072 triangles): sampled output blocks of the
     FP64 Schur and Helmholtz applies against the oracle, row by row."""
