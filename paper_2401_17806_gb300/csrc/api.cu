@@ -88,6 +88,7 @@ void dgsl_default_solve_opts(dgsl_solve_opts* o) {
 }
 
 int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* opts, dgsl_operator** out) {
+  NvtxRange nvtx("dgsl_build_operators");
   if (!mesh || !out) return fail(DGSL_EINVAL, "mesh and out must be non-NULL");
   *out = nullptr;
   dgsl_build_opts o{0, 0, 0, 0};
@@ -360,6 +361,7 @@ Sums read_sums(dgsl_operator* op, const double* dev_part, int nparts, cudaStream
 // couplings with FP32 vectors; x += d in FP64.
 int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double* x, const dgsl_solve_opts& o,
               dgsl_solve_info* info, cudaStream_t s) {
+  NvtxRange nvtx(kind == DGSL_SCHUR ? "dgsl_cg_solve Schur" : "dgsl_cg_solve Helmholtz");
   DevOp& d = op->d;
   auto& w = op->w;
   const int64_t n = d.n;

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "host.h"
 #include "kernels.h"
 
@@ -28,6 +30,15 @@ using dgsl::GridBarrier;
 using dgsl::HostBlocks;
 using dgsl::HostMesh;
 using dgsl::RefOps;
+
+// NVTX range around a library phase (build, solve, batch, serving round), for
+// Nsight timelines; header-only NVTX 3, inert unless a profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct dgsl_operator {
   HostMesh hm;

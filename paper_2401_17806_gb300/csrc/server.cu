@@ -145,6 +145,7 @@ extern "C" void dgsl_default_engine_opts(dgsl_engine_opts* o) {
 
 extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_engine_opts* opts,
                                    dgsl_solve_info* infos, void* stream) {
+  NvtxRange nvtx("dgsl_cg_solve_batch");
   dgsl_engine_opts o;
   dgsl_default_engine_opts(&o);
   if (opts) o = *opts;
@@ -303,6 +304,7 @@ struct dgsl_server {
 
   // One scheduling round (called with mu held).
   void round() {
+    NvtxRange nvtx("dgsl server round");
     // 1. engine exit: requeue slots it never admitted, reset the inbox
     if (running && cudaEventQuery(exited) == cudaSuccess) {
       running = false;
