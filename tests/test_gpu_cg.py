@@ -168,3 +168,25 @@ def test_full_size_solve_sampled_residual(dgsl_lib):
     # a global relative residual of 1e-10 bounds the sampled block's norm by
     # ||r||; compare against the same sample of b
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b64)
+
+
+def test_bf16_couplings_refined_to_fp64(dgsl_lib):
+    """BF16-stored couplings with FP32 inner CG under FP64 refinement: the
+    well-conditioned Helmholtz system converges to 1e-10 (checked with the
+    oracle); the Schur system either converges or reports DGSL_ENOTCONV with a
+    relative residual the oracle confirms."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(12, 3, 15, store=dgsl.STORE_F64 | dgsl.STORE_BF16)
+    b = synth.standard_normal(op.n_dof, 71)
+    x, info, _ = _solve(op, m, dgsl.HELMHOLTZ, 1e-3, b, tol=1e-10, precision=dgsl.PREC_BF16_IR)
+    assert info.status == dgsl.OK
+    H = orc.helmholtz_matrix(1e-3)
+    assert np.linalg.norm(b - H @ x) / np.linalg.norm(b) <= 2e-10
+    x, info, _ = _solve(op, m, dgsl.SCHUR, 1e-2, b, tol=1e-10, precision=dgsl.PREC_BF16_IR, max_refine=60)
+    assert info.status in (dgsl.OK, dgsl.ENOTCONV)
+    S = orc.schur_matrix(1e-2)
+    pb = OP.project_mean(b)
+    r = np.linalg.norm(pb - S @ x) / np.linalg.norm(pb)
+    assert r <= max(2e-10, 1.01 * info.relres + 1e-12)
+    if info.status == dgsl.OK:
+        assert r <= 2e-10
