@@ -513,9 +513,9 @@ constexpr int kNoAllocMaxParts = 1024;                 // per-CTA partial slots
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxDof * sizeof(double);
 // CG vectors (cg_vec_bytes: 8 per-triangle padded vectors; at most 32/3 n doubles, for p = 1)
 constexpr size_t kNoAllocCgSlots = 11;
-// r64 | d64 (also r32 + d32) | CG vectors | part (4 slots) | part2 (2) | barrier | result
+// r64 | d64 (also r32 + d32) | CG vectors | part (2 x 4 slots) | part2 (2) | barrier | result
 constexpr size_t kNoAllocBytes =
-    (2 + kNoAllocCgSlots) * kNoAllocVecBytes + 6 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
+    (2 + kNoAllocCgSlots) * kNoAllocVecBytes + 10 * (size_t)kNoAllocMaxParts * sizeof(double) + 256 + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -545,7 +545,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   float* d32 = r32 + kNoAllocMaxDof;
   void* vbuf = base + 2 * kNoAllocVecBytes;
   double* part = reinterpret_cast<double*>(base + (2 + kNoAllocCgSlots) * kNoAllocVecBytes);
-  double* part2 = part + 4 * kNoAllocMaxParts;
+  double* part2 = part + 8 * kNoAllocMaxParts;
   unsigned char* tail = reinterpret_cast<unsigned char*>(part2 + 2 * kNoAllocMaxParts);
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(tail);
   CGResult* res = reinterpret_cast<CGResult*>(tail + 256);

@@ -28,8 +28,8 @@
 // So that every gathered block starts on a 16-byte boundary, the CG's own
 // vectors are stored per triangle with N_phi padded to a multiple of the
 // 16-byte vector width (the caller's r and x stay unpadded).  Partial sums
-// are reduced per CTA and combined by the last CTA to arrive in a fixed order,
-// so all CTAs take identical, deterministic decisions.
+// are reduced per CTA and, once every CTA has arrived, summed by every CTA in
+// the same fixed order, so all CTAs take identical, deterministic decisions.
 #include "kassembled.cuh"
 #include "kernels.h"
 
@@ -54,7 +54,7 @@ struct CGParams {
   V* x;          // result, unpadded (written at exit)
   const V* r0;   // right-hand side, unpadded
   V* vec;        // 8 padded vectors of ne * NPAD: p | x | r0 | r1 | w0 | w1 | s0 | s1
-  double* part;  // [max_parts][4]
+  double* part;  // [2][max_parts][4] (epoch parity)
   int max_parts;
   GridBarrier* bar;
   CGResult* res;
@@ -207,12 +207,15 @@ __device__ __forceinline__ void consumer_sum4(W (&v)[4], W (*s_red)[4]) {
   cbar();
 }
 
-// Grid-wide sum of acc[0..3] by the consumer warps (as grid_allreduce4): the
-// CTA's partial (summed over its threads in V, then widened to FP64) is
-// published, the last CTA to arrive sums all partials in CTA order in FP64 and
-// releases the totals; the others wait for the release.  The acq_rel arrival
-// orders this CTA's vector writes (made before the consumer barrier) for every
-// CTA that later sees the count.
+// Grid-wide sum of acc[0..3] by the consumer warps.  Each CTA publishes its
+// partial (summed over its threads in V, widened to FP64) and arrives on the
+// counter; once every CTA has arrived, every CTA sums all partials itself in
+// CTA order (FP64), so all obtain bit-identical totals one round trip after
+// the last arrival.  The partials alternate between two halves of part[] by
+// epoch parity: a CTA that has moved on to the next epoch writes the other
+// half, never a partial that a slower CTA is still reading.  The acq_rel
+// arrival also orders this CTA's vector writes (made before the consumer
+// barrier) for every CTA that later sees the count.
 template <typename V>
 __device__ __forceinline__ bool consumer_allreduce4(GridBarrier* b, double* part, unsigned nblocks,
                                                     unsigned long long& epoch, uint64_t timeout_ns,
@@ -220,55 +223,45 @@ __device__ __forceinline__ bool consumer_allreduce4(GridBarrier* b, double* part
   __shared__ V s_redv[4][4];
   __shared__ double s_red[4][4];
   __shared__ double s_tot[4];
-  __shared__ int s_state;  // 1: this CTA arrived last, 0: wait, -1: error
+  __shared__ int s_state;
   consumer_sum4<V>(acc, s_redv);
   ++epoch;
+  double* pe = part + (size_t)(epoch & 1ull) * 4 * nblocks;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) part[4 * blockIdx.x + i] = (double)acc[i];
+    for (int i = 0; i < 4; ++i) pe[4 * blockIdx.x + i] = (double)acc[i];
     const unsigned long long target = epoch * (unsigned long long)nblocks;
     unsigned long long v;
     asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(v) : "l"(&b->count) : "memory");
-    s_state = v + 1 == target ? 1 : 0;
-  }
-  cbar();
-  if (s_state == 1) {
-    double t[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned j = threadIdx.x; j < nblocks; j += kCgConsumers)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) t[i] += __ldcg(part + (size_t)j * 4 + i);
-    consumer_sum4<double>(t, s_red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        b->total[i] = t[i];
-        s_tot[i] = t[i];
-      }
-      asm volatile("st.release.gpu.u64 [%0], %1;" ::"l"(&b->gen), "l"(epoch) : "memory");
-    }
-  } else if (threadIdx.x == 0) {
-    const uint64_t t0 = globaltimer_ns();
-    unsigned long long g;
     int st = 0;
-    for (unsigned spins = 1;; ++spins) {
-      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(g) : "l"(&b->gen) : "memory");
-      if (g >= epoch) break;
-      if (*((volatile int*)&b->status) != kStatusOk) { st = -1; break; }
-      if ((spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
-        atomicCAS(&b->status, kStatusOk, kStatusTimeout);
-        st = -1;
-        break;
+    if (v + 1 < target) {
+      const uint64_t t0 = globaltimer_ns();
+      for (unsigned spins = 1;; ++spins) {
+        asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&b->count) : "memory");
+        if (v >= target) break;
+        if (*((volatile int*)&b->status) != kStatusOk) { st = -1; break; }
+        if ((spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+          atomicCAS(&b->status, kStatusOk, kStatusTimeout);
+          st = -1;
+          break;
+        }
       }
     }
-    if (st == 0)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) s_tot[i] = __ldcg(&b->total[i]);
-    s_state = st;
+    if (*((volatile int*)&b->status) != kStatusOk) st = -1;
+    s_state = st;  // one thread decides, so that every consumer thread takes the same branch
   }
-  // one thread decides, so that every consumer thread takes the same branch
-  if (threadIdx.x == 0 && *((volatile int*)&b->status) != kStatusOk) s_state = -1;
   cbar();
   const bool ok = s_state >= 0;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  if (ok)
+    for (unsigned j = threadIdx.x; j < nblocks; j += kCgConsumers)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] += __ldcg(pe + (size_t)j * 4 + i);
+  consumer_sum4<double>(t, s_red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s_tot[i] = t[i];
+  cbar();
 #pragma unroll
   for (int i = 0; i < 4; ++i) tot[i] = s_tot[i];
   cbar();

@@ -83,7 +83,7 @@ struct CGResult {
 };
 struct CGWork {
   void* vec = nullptr;    // cg_vec_bytes(op): p, x, r, w, s (r, w, s double-buffered), per-triangle padded
-  double* part = nullptr; // max_parts x 4 partial sums
+  double* part = nullptr; // 2 x max_parts x 4 partial sums (epoch parity)
   GridBarrier* bar = nullptr;
   CGResult* res = nullptr;
   int max_parts = 0;

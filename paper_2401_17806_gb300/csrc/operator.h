@@ -103,7 +103,7 @@ struct dgsl_operator {
     w.r32 = dalloc<float>(d.n);
     w.d32 = dalloc<float>(d.n);
     w.vec = dalloc<double>((cg_vec_bytes(d) + 7) / 8);
-    w.part = dalloc<double>(4 * (size_t)w.max_parts);
+    w.part = dalloc<double>(8 * (size_t)w.max_parts);  // two halves of 4 sums per CTA
     w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
     w.bar = dalloc<GridBarrier>(1);
     w.res = dalloc<CGResult>(1);
