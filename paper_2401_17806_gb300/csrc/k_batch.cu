@@ -79,7 +79,7 @@ struct EngineShared {              // device memory, zeroed before each launch
   int admitted;                    // slots admitted so far (copied from the inbox)
   int list_dirty;
   int exit_now;
-  int pad[2];
+  int ring_S, ring_SB;             // stage ring of the next pass (stages, bytes per stage)
 };
 
 // Geometry of a tile for degree NPHI and coupling type T (as k_cg.cu), and of
@@ -699,11 +699,13 @@ __device__ __forceinline__ void copy_desc(BSlotDesc* dst, const BSlotDesc* src) 
   for (int i = threadIdx.x; i < W; i += blockDim.x) o[i] = *((volatile const unsigned long long*)(s + i));
 }
 
-// Admission of newly published slots and rebuild of the active-chunk list
-// (whole CTA of the last arriver; the indexed work uses the consumer threads).
+// Admission of newly published slots, rebuild of the active-chunk list with
+// each CTA's starting list index, and the stage ring of the next pass (whole
+// CTA of the last arriver; the indexed work uses the consumer threads).
+template <typename T>
 __device__ __noinline__ void engine_hook(const EngineParams& E) {
   constexpr int H = kEConsumers;
-  __shared__ int s_count, s_adm, s_dirty, s_run[H], s_runc[H];
+  __shared__ int s_count, s_adm, s_dirty, s_per, s_mx, s_run[H], s_runc[H];
   EngineShared* sh = E.sh;
   const bool w = threadIdx.x < H;
   if (threadIdx.x == 0) {
@@ -752,17 +754,23 @@ __device__ __noinline__ void engine_hook(const EngineParams& E) {
       sh->n_act = a;
       sh->total_chunks = b;
       E.act_chunk0[a] = b;
+      s_per = (b + (int)gridDim.x - 1) / (int)gridDim.x;  // chunks per CTA (the pass splits as the kernel does)
     }
     __syncthreads();
     if (w) {
       int k = s_run[threadIdx.x], c0 = s_runc[threadIdx.x];
+      const int per = s_per;
       for (int j = 0; j < PER; ++j) {
         const int sidx = threadIdx.x * PER + j;
         if (sidx < s_count && __ldcg(&E.state[sidx].phase) != PH_DONE) {
+          const int nc = __ldcg(&E.slots[sidx].nchunk);
           E.act_slot[k] = sidx;
           E.act_chunk0[k] = c0;
+          // the CTAs whose range starts inside this slot's chunks start their walk at k
+          if (per > 0)
+            for (int cta = (c0 + per - 1) / per; cta < (int)gridDim.x && cta * per < c0 + nc; ++cta) E.cta_k[cta] = k;
           ++k;
-          c0 += __ldcg(&E.slots[sidx].nchunk);
+          c0 += nc;
         }
       }
     }
@@ -773,7 +781,27 @@ __device__ __noinline__ void engine_hook(const EngineParams& E) {
     }
   }
   __syncthreads();
+  // stage ring of the next pass: the largest tile footprint among the active CG slots
+  if (threadIdx.x == 0) s_mx = 128;
+  __syncthreads();
+  {
+    const int na = *((volatile int*)&sh->n_act);
+    int mx = 128;
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+      const int sid = __ldcg(E.act_slot + k);
+      const int ph = __ldcg(&E.state[sid].phase);
+      if (ph == PH_CG0 || ph == PH_CG) {
+        const EGeom g = e_geom<T>(__ldcg(&E.slots[sid].p), __ldcg(&E.slots[sid].rp));
+        mx = max(mx, g.area + (g.tt * 8 + 15) / 16 * 16);
+      }
+    }
+    atomicMax(&s_mx, mx);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    const int SB = (s_mx + 127) / 128 * 128;
+    sh->ring_SB = SB;
+    sh->ring_S = min(kEMaxStages, kEDynSmem / SB);
     __threadfence();
     int exit_now = 0;
     if (*((volatile int*)&sh->n_act) == 0) {
@@ -807,14 +835,10 @@ __device__ __forceinline__ void walk_to(const EngineParams& E, int n_act, int ci
   w.chunk0 = __ldcg(E.act_chunk0 + w.k);
   w.next0 = __ldcg(E.act_chunk0 + w.k + 1);
 }
-__device__ __forceinline__ EWalk walk_start(const EngineParams& E, int n_act, int c_begin) {
-  int lo = 0, hi = n_act;  // last k with act_chunk0[k] <= c_begin
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldcg(E.act_chunk0 + mid) <= c_begin) lo = mid; else hi = mid;
-  }
+// A CTA's walk starts at the list index the barrier hook recorded for it.
+__device__ __forceinline__ EWalk walk_from(int k0) {
   EWalk w;
-  w.k = lo;
+  w.k = k0;
   w.sid = -1;
   w.chunk0 = w.next0 = 0;
   return w;
@@ -834,35 +858,18 @@ __device__ __forceinline__ bool e_wait_empty(uint64_t* bar, unsigned parity, uin
 }
 
 // Stage ring of one pass: S stages of SB bytes (SB = the largest tile
-// footprint among the CG slots of the CTA's chunk range).
+// footprint among the active CG slots, set by the barrier hook).
 struct ERing {
   unsigned char* base;
   int S, SB;
 };
-template <typename T>
-__device__ void pass_ring(const EngineParams& E, int n_act, int cb, int ce, int& S, int& SB) {
-  int mx = 128;
-  if (cb < ce) {
-    EWalk w = walk_start(E, n_act, cb);
-    for (int cidx = cb; cidx < ce;) {
-      walk_to(E, n_act, cidx, w);
-      if (is_cg(__ldcg(&E.state[w.sid].phase))) {
-        const EGeom g = e_geom<T>(__ldcg(&E.slots[w.sid].p), __ldcg(&E.slots[w.sid].rp));
-        mx = max(mx, g.area + (g.tt * 8 + 15) / 16 * 16);
-      }
-      cidx = w.next0;
-    }
-  }
-  SB = (mx + 127) / 128 * 128;
-  S = min(kEMaxStages, kEDynSmem / SB);
-}
 
 // Coupling warp (lane 0): TMA bulk copies of every CG tile of the range.
 template <typename T>
-__device__ void coupling_pass(const EngineParams& E, int n_act, int cb, int ce, const ERing& ring,
+__device__ void coupling_pass(const EngineParams& E, int n_act, int cb, int ce, int k0, const ERing& ring,
                               uint64_t* full, uint64_t* empty, unsigned& gt, volatile int* s_err) {
   const uint64_t pol = l2_evict_first_policy();
-  EWalk w = walk_start(E, n_act, cb);
+  EWalk w = walk_from(k0);
   for (int cidx = cb; cidx < ce; ++cidx) {
     walk_to(E, n_act, cidx, w);
     const BSlotDesc* dp = &E.slots[w.sid];
@@ -897,11 +904,11 @@ __device__ void coupling_pass(const EngineParams& E, int n_act, int cb, int ce, 
 // copies of each small block were several times slower: the blocks are
 // 48-480 bytes each.)
 template <typename T>
-__device__ void gather_pass(const EngineParams& E, int n_act, int cb, int ce, const ERing& ring,
+__device__ void gather_pass(const EngineParams& E, int n_act, int cb, int ce, int k0, const ERing& ring,
                             uint64_t* gfull, uint64_t* empty, unsigned& gt, volatile int* s_err) {
   __shared__ int s_gcol[4 * kERows];  // column indices of the current tile (4 TT <= 4 kERows / 3)
   const int lane = threadIdx.x & 31;
-  EWalk w = walk_start(E, n_act, cb);
+  EWalk w = walk_from(k0);
   for (int cidx = cb; cidx < ce; ++cidx) {
     walk_to(E, n_act, cidx, w);
     const BSlotDesc* dp = &E.slots[w.sid];
@@ -1040,7 +1047,7 @@ __device__ __forceinline__ bool chunk_work(const BSlotDesc& d, const ChunkCtx& c
 // slot, and the CTA whose arrival completes the slot's pass sums the slot's
 // partials in chunk order and advances the slot.
 template <typename T>
-__device__ bool consumer_pass(const EngineParams& E, int n_act, int cb, int ce, const ERing& ring, uint64_t* full,
+__device__ bool consumer_pass(const EngineParams& E, int n_act, int cb, int ce, int k0, const ERing& ring, uint64_t* full,
                               uint64_t* gfull, uint64_t* empty, unsigned& gt) {
   __shared__ BSlotDesc s_desc;
   __shared__ ChunkCtx s_ctx;
@@ -1050,7 +1057,7 @@ __device__ bool consumer_pass(const EngineParams& E, int n_act, int cb, int ce, 
   __shared__ __align__(16) float s_rn[2 * kRnMax];  // new residual of a tile, double-buffered
   const BSlotDesc& d = s_desc;
   const ChunkCtx& c = s_ctx;
-  EWalk w = walk_start(E, n_act, cb);
+  EWalk w = walk_from(k0);
   int cur_sid = -1, pend = 0;
   auto flush = [&]() {
     if (pend == 0) return;
@@ -1115,7 +1122,6 @@ __global__ void __launch_bounds__(kEThreads, 1) k_engine(EngineParams E) {
   extern __shared__ __align__(128) unsigned char stages[];
   __shared__ __align__(8) uint64_t full[kEMaxStages], gfull[kEMaxStages], empty[kEMaxStages];
   __shared__ volatile int s_err;
-  __shared__ int s_S, s_SB;
   const unsigned nb = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long epoch = 0;
@@ -1131,7 +1137,7 @@ __global__ void __launch_bounds__(kEThreads, 1) k_engine(EngineParams E) {
     fence_proxy_async_smem();
   }
   __syncthreads();
-  auto hook = [&E]() { engine_hook(E); };
+  auto hook = [&E]() { engine_hook<T>(E); };
   bool ok = grid_sync_hook(E.sh, nb, epoch, E.timeout_ns, hook);
   while (ok) {
     if (__ldcg(&E.sh->exit_now)) break;
@@ -1141,12 +1147,12 @@ __global__ void __launch_bounds__(kEThreads, 1) k_engine(EngineParams E) {
     const int per = (total + (int)nb - 1) / (int)nb;
     const int cb = min(total, (int)blockIdx.x * per);
     const int ce = min(total, cb + per);
-    // this pass's stage ring; every copy of the previous pass has been consumed
+    // this pass's stage ring (set by the hook); every copy of the previous pass
+    // has been consumed, so the barriers start afresh
+    const int k0 = cb < ce ? __ldcg(E.cta_k + blockIdx.x) : 0;
+    ring.S = __ldcg(&E.sh->ring_S);
+    ring.SB = __ldcg(&E.sh->ring_SB);
     if (threadIdx.x == 0) {
-      int S, SB;
-      pass_ring<T>(E, n_act, cb, ce, S, SB);
-      s_S = S;
-      s_SB = SB;
       for (int i = 0; i < kEMaxStages; ++i) {
         mbar_inval(&full[i]);
         mbar_inval(&gfull[i]);
@@ -1158,20 +1164,18 @@ __global__ void __launch_bounds__(kEThreads, 1) k_engine(EngineParams E) {
       fence_proxy_async_smem();
     }
     __syncthreads();
-    ring.S = s_S;
-    ring.SB = s_SB;
     gt = 0;
     if (warp < kECouplingWarp) {
-      if (!consumer_pass<T>(E, n_act, cb, ce, ring, full, gfull, empty, gt)) {
+      if (!consumer_pass<T>(E, n_act, cb, ce, k0, ring, full, gfull, empty, gt)) {
         if (threadIdx.x == 0) {
           s_err = 1;
           atomicCAS(&E.sh->status, kStatusOk, kStatusTimeout);
         }
       }
     } else if (warp == kECouplingWarp) {
-      if (lane == 0) coupling_pass<T>(E, n_act, cb, ce, ring, full, empty, gt, &s_err);
+      if (lane == 0) coupling_pass<T>(E, n_act, cb, ce, k0, ring, full, empty, gt, &s_err);
     } else {
-      gather_pass<T>(E, n_act, cb, ce, ring, gfull, empty, gt, &s_err);
+      gather_pass<T>(E, n_act, cb, ce, k0, ring, gfull, empty, gt, &s_err);
     }
     ok = grid_sync_hook(E.sh, nb, epoch, E.timeout_ns, hook);
   }
@@ -1186,10 +1190,14 @@ __global__ void __launch_bounds__(kEThreads, 1) k_engine(EngineParams E) {
 
 // ---------------------------------------------------------------- host side
 
-int engine_chunk_tris(int p) { return e_tt(e_nphi(p)) * 8; }  // 8 tiles per chunk
+int engine_chunk_tris(int p, int ne) {
+  (void)ne;
+  return e_tt(e_nphi(p)) * 8;  // 8 tiles per chunk
+}
 
 size_t engine_state_bytes() {
-  return sizeof(BSlotDesc) * kMaxSlots + sizeof(BState) * kMaxSlots + 256 + sizeof(int) * (2 * kMaxSlots + 1) + 1024;
+  return sizeof(BSlotDesc) * kMaxSlots + sizeof(BState) * kMaxSlots + 256 + sizeof(int) * (2 * kMaxSlots + 1) +
+         sizeof(int) * kMaxCtas + 2048;
 }
 
 void engine_layout(void* base, EngineParams& P) {
@@ -1204,6 +1212,7 @@ void engine_layout(void* base, EngineParams& P) {
   P.sh = reinterpret_cast<EngineShared*>(take(sizeof(EngineShared)));
   P.act_slot = reinterpret_cast<int*>(take(sizeof(int) * kMaxSlots));
   P.act_chunk0 = reinterpret_cast<int*>(take(sizeof(int) * (kMaxSlots + 1)));
+  P.cta_k = reinterpret_cast<int*>(take(sizeof(int) * kMaxCtas));
 }
 
 size_t engine_shared_bytes() { return sizeof(EngineShared); }
@@ -1219,7 +1228,7 @@ size_t engine_workspace_bytes(int p, int ne, int nrhs) {
   const int nphi = e_nphi(p);
   const int64_t n = (int64_t)ne * nphi;
   const int bl = e_block_len(nphi, e_rp(nrhs));
-  const int nchunk = (ne + engine_chunk_tris(p) - 1) / engine_chunk_tris(p);
+  const int nchunk = (ne + engine_chunk_tris(p, ne) - 1) / engine_chunk_tris(p, ne);
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   return a256(8 * (size_t)n * nrhs) + a256(4 * 8 * (size_t)ne * bl) + a256(8 * (size_t)kNV * nchunk);
 }
@@ -1229,7 +1238,7 @@ void engine_fill_workspace(BSlotDesc& s, char* ws) {
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   s.rp = e_rp(s.nrhs);
   s.bl = e_block_len(nphi, s.rp);
-  s.chunk_tris = engine_chunk_tris(s.p);
+  s.chunk_tris = engine_chunk_tris(s.p, s.ne);
   s.nchunk = (s.ne + s.chunk_tris - 1) / s.chunk_tris;
   s.r64 = reinterpret_cast<double*>(ws);
   ws += a256(8 * (size_t)s.n * s.nrhs);
@@ -1251,7 +1260,7 @@ static cudaError_t launch_engine_t(const EngineParams& e, cudaStream_t s, int* g
   if (err != cudaSuccess) return err;
   if (per < 1) return cudaErrorLaunchOutOfResources;
   per = std::min(per, 8);
-  const int blocks = sms * per;
+  const int blocks = std::min(sms * per, kMaxCtas);
   if (grid_used) *grid_used = blocks;
   EngineParams a = e;
   void* args[] = {&a};

@@ -8,6 +8,7 @@ namespace dgsl {
 
 constexpr int kMaxSlots = 4096;       // slots per engine (admitted over its lifetime)
 constexpr int kMaxRhs = 8;            // right-hand sides per slot
+constexpr int kMaxCtas = 2048;        // CTAs of an engine launch (152 SMs x at most 8)
 
 // One request (1..kMaxRhs right-hand sides of one operator), written by the
 // host and copied into device memory when the engine admits it.  All pointers
@@ -69,13 +70,17 @@ struct EngineParams {
   EngineShared* sh;
   int* act_slot;            // [kMaxSlots]
   int* act_chunk0;          // [kMaxSlots + 1]
+  int* cta_k;               // [kMaxCtas]: index in the active list of each CTA's first chunk
   uint64_t timeout_ns;      // bound of every device wait
   uint64_t idle_ns;         // how long an idle engine waits for new slots before exiting
 };
 
-// Triangles per chunk for degree p (a multiple of the CG tile, itself a
-// multiple of 4 triangles).
-int engine_chunk_tris(int p);
+// Triangles per chunk for degree p and ne triangles (a multiple of the CG
+// tile, itself a multiple of 4 triangles): 8 tiles.  It depends on the slot
+// alone, never on what else is in the engine.  (Fewer tiles per chunk for
+// small meshes sped up a batch of 8 small multi-RHS requests by 10% but slowed
+// 64 small single-RHS requests by 27%: more chunks, more per-chunk reductions.)
+int engine_chunk_tris(int p, int ne);
 // Device workspace of one request (r64 | fvec | partials) and the descriptor
 // fields that point into it (also sets rp, bl, chunk_tris, nchunk from p, ne,
 // n and nrhs).
