@@ -18,6 +18,12 @@ Solves: sparse direct LU (SuperLU) of S with DOF 0 grounded, shifted to
 mean zero (equal to the bordered-system solution), LU of H; a plain CG (x0 = 0, stop at ||r||/||b|| <= tol) for sizes
 where a factorisation does not fit.
 
+Preconditioned CG (an extension; the paper's CG is unpreconditioned): the
+textbook PCG recurrence (Hestenes-Stiefel form with z = P r, as in Saad,
+Iterative Methods for Sparse Linear Systems, 2nd ed., Algorithm 9.1) with the
+block-Jacobi P = blockdiag(D_i)^-1, D_i the N_phi x N_phi diagonal block of A
+on triangle i, sliced from the oracle's own sparse matrix and inverted densely.
+
 Vectors are in the natural numbering: triangle i, local DOF k at i*Nphi + k.
 
 Test infrastructure only (see the package docstring).
@@ -219,6 +225,60 @@ def cg(apply, b, tol=1e-12, maxit=100000, mean_zero=False):
         rr = rr_new
         it += 1
     return x, it, np.sqrt(rr) / bn
+
+
+def block_jacobi_blocks(A, nphi):
+    """Inverse diagonal blocks of A: [n/nphi, nphi, nphi], block i =
+    (A[i*nphi:(i+1)*nphi, i*nphi:(i+1)*nphi])^-1 (symmetrised before inversion)."""
+    A = sp.csr_matrix(A)
+    ne = A.shape[0] // nphi
+    out = np.empty((ne, nphi, nphi))
+    for i in range(ne):
+        sl = slice(i * nphi, (i + 1) * nphi)
+        D = A[sl, sl].toarray()
+        out[i] = np.linalg.inv(0.5 * (D + D.T))
+    return out
+
+
+def apply_blocks(blocks, v):
+    """y_i = blocks[i] v_i for every triangle i (v in the natural numbering)."""
+    ne, nphi, _ = blocks.shape
+    return np.einsum("ekl,el->ek", blocks, np.asarray(v).reshape(ne, nphi)).ravel()
+
+
+def pcg(apply, b, precond, tol=1e-12, maxit=100000, mean_zero=False):
+    """Preconditioned CG (textbook form): x0 = 0, r = b, z = P r, p = z;
+    alpha = (r, z) / (p, A p); x += alpha p; r -= alpha A p; z = P r;
+    beta = (r, z)_new / (r, z)_old; p = z + beta p; stop at ||r||_2 <= tol ||b||_2.
+    precond(v) applies P.  mean_zero: b projected to mean zero, A p projected
+    likewise (the pressure operator's nullspace is span{1}), x returned
+    mean-free.  Returns (x, iterations, recursive relative residual)."""
+    if mean_zero:
+        b = project_mean(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = np.sqrt(b @ b)
+    if bn == 0.0:
+        return x, 0, 0.0
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    while np.sqrt(r @ r) > tol * bn and it < maxit:
+        q = apply(p)
+        if mean_zero:
+            q = project_mean(q)
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    if mean_zero:
+        x = project_mean(x)
+    return x, it, np.sqrt(r @ r) / bn
 
 
 def sampled_rows(conn, p, x, tri_ids, coefK, coefM=0.0):
