@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--p", type=int, default=WORKLOAD["p"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-precond", action="store_true",
+                    help="skip the block-Jacobi preconditioned run of the same stage")
     ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg"], default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
@@ -156,11 +158,15 @@ def dual_velocity(op, seed):
     return np.stack([u, v]) + noise
 
 
-def bytes_per_row_iter(nphi, coupling_bytes, vec_bytes):
+def bytes_per_row_iter(nphi, coupling_bytes, vec_bytes, precond=False):
     """Algorithmic bytes per matrix row per CG iteration of the persistent
     kernel: the row's 4*N_phi coupling coefficients, its share of the column
-    indices (4 int32 per triangle), and 10 vector accesses (phase A: read r and
-    p_old, write p_new and q; phase B: read p_new, q, r, x, write x and r)."""
+    indices (4 int32 per triangle), and its vector accesses: 10 for plain CG
+    (read p, x, r, w, s; write them), 12 with the block-Jacobi preconditioner
+    (read p, x, u, r, w, s; write them) plus the row of P (N_phi values in the
+    vector precision); the couplings are then those of A P, of the same size."""
+    if precond:
+        return 4 * nphi * coupling_bytes + nphi * vec_bytes + 16.0 / nphi + 12 * vec_bytes
     return 4 * nphi * coupling_bytes + 16.0 / nphi + 10 * vec_bytes
 
 
@@ -291,6 +297,28 @@ def gpu_leg(args, rank, world, local):
         res["fp64"] = dict(ms=ev0.elapsed_time(ev1), iters=sum(i.iters for i in f_infos),
                            dof_iters=sum(op.n_dof * i.iters for i in f_infos),
                            kern_ms=sum(i.cg_kernel_ms for i in f_infos))
+    # ---- the same stage with block-Jacobi preconditioned CG (an extension);
+    # the first run builds and keeps the blocks of both systems
+    if not args.no_precond:
+        ob = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=st.opts.precision,
+                             precond=dgsl.PRECOND_BLOCK_JACOBI)
+        with torch.cuda.stream(stream):
+            st.run(stream, ob)
+        stream.synchronize()
+        barrier()
+        b_infos = []
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                b_infos += st.run(stream, ob)
+            ev1.record(stream)
+        stream.synchronize()
+        bs = sum(i.iters for k, i in enumerate(b_infos) if k % 3 == 0)
+        res["bj"] = dict(ms=ev0.elapsed_time(ev1), schur_iters=bs / args.steps,
+                         helm_iters=(sum(i.iters for i in b_infos) - bs) / args.steps,
+                         iters_total=sum(i.iters for i in b_infos),
+                         kern_ms=sum(i.cg_kernel_ms for i in b_infos),
+                         relres_max=max(i.relres for i in b_infos))
     return res
 
 
@@ -704,6 +732,20 @@ def main():
                                     "ms_per_step": f["ms"], "iters_per_step": f["iters"],
                                     "speedup_of_value": (dof_iters / ms) / (f["dof_iters"] / f["ms"]),
                                     "stage_time_ratio": f["ms"] / (ms / args.steps)}
+    if "bj" in res:
+        bj = res["bj"]
+        per_row_bj = bytes_per_row_iter(op.n_phi, cb, vb, precond=True)
+        ach = bj["iters_total"] * op.n_dof * per_row_bj / (bj["kern_ms"] * 1e-3) / 1e9
+        line["block_jacobi"] = {
+            "what": "same stage, CG preconditioned by the inverse diagonal blocks (extension)",
+            "ms_per_step": bj["ms"] / args.steps,
+            "stage_speedup": (ms / args.steps) / (bj["ms"] / args.steps),
+            "schur_iters_per_step": bj["schur_iters"],
+            "helmholtz_iters_per_step": bj["helm_iters"],
+            "max_relres": bj["relres_max"],
+            "kernel_achieved_gbs": ach, "kernel_frac": ach / peak if peak else None,
+            "bytes_per_row_iter": per_row_bj,
+        }
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

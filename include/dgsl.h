@@ -220,6 +220,12 @@ enum {
   DGSL_PREC_BF16_IR = 2    /* BF16-stored blocks, FP32 inner CG, FP64 refinement */
 };
 
+enum {
+  DGSL_PRECOND_NONE = 0,         /* plain CG, as the paper runs it (default) */
+  DGSL_PRECOND_BLOCK_JACOBI = 1  /* CG preconditioned by the inverse N_phi x N_phi
+                                    diagonal blocks of A (one per triangle) */
+};
+
 typedef struct {
   double tol;            /* target ||b - A x||_2 / ||b||_2 (default 1e-10) */
   int32_t max_iters;     /* cap on CG iterations, all refinements (default 200000) */
@@ -228,6 +234,8 @@ typedef struct {
   double inner_tol;      /* inner CG relative tolerance under refinement (1e-3) */
   int32_t max_refine;    /* refinement steps cap (default 30) */
   int32_t form;          /* DGSL_FORM_* of the FP64 operator */
+  int32_t precond;       /* DGSL_PRECOND_* (default NONE) */
+  int32_t pad;
 } dgsl_solve_opts;
 
 typedef struct {
@@ -245,7 +253,13 @@ typedef struct {
 /* Solves A x = b for kind DGSL_SCHUR (A = S with dt = coef) or
  * DGSL_HELMHOLTZ (A = H with nu_dt = coef) by matrix-free CG (Sec. 2.3,
  * after eq. pressure_final), with x0 = 0 unless use_x0, stopping at the
- * relative residual tol.  For DGSL_SCHUR, b is projected to mean zero and x
+ * relative residual tol.  With precond = DGSL_PRECOND_BLOCK_JACOBI the inner
+ * CG is preconditioned by P = blockdiag(D_i)^-1, D_i the diagonal block of A on
+ * triangle i (an extension; the paper's CG is unpreconditioned): the operator
+ * builds P on first use for each (kind, coef, precision) and keeps the blocks
+ * of the last four such systems (N_phi values per row, rounded up to 4 in
+ * FP32 or 2 in FP64; about 48 / 80 bytes per DOF at p = 3); DGSL_EINVAL if a
+ * diagonal block is not positive definite.  For DGSL_SCHUR, b is projected to mean zero and x
  * is returned with sum(x) = 0 (coefficient space).  b, x: device
  * double[n_rhs][n_dof] in internal order; info: host array [n_rhs] or NULL.
  * Blocks the calling thread until the solves finish (it reads the status
@@ -264,7 +278,9 @@ void dgsl_default_solve_opts(dgsl_solve_opts* opts);
  * if it did (DGSL_OK otherwise) and the device stays usable.  Synchronous. */
 int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* status);
 
-/* Same solve as dgsl_cg_solve, for callers that cannot allocate device memory
+/* Same solve as dgsl_cg_solve (precond must be DGSL_PRECOND_NONE: the fixed
+ * scratch has no room for the preconditioner's blocks; else DGSL_EINVAL), for
+ * callers that cannot allocate device memory
  * when they solve: code that runs while a CUDA stream is being captured into a
  * graph, real-time loops and services that reserve all device memory at start-up
  * under a fixed budget, or hosts whose own allocator owns the GPU.  This entry

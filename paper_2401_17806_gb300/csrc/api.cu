@@ -85,6 +85,8 @@ void dgsl_default_solve_opts(dgsl_solve_opts* o) {
   o->inner_tol = 1e-3;
   o->max_refine = 30;
   o->form = DGSL_FORM_ASSEMBLED;
+  o->precond = DGSL_PRECOND_NONE;
+  o->pad = 0;
 }
 
 int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* opts, dgsl_operator** out) {
@@ -385,6 +387,8 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
   cw.bar = w.bar;
   cw.res = w.res;
   cw.max_parts = w.max_parts;
+  const int ptype = o.precision == DGSL_PREC_F64 ? 1 : o.precision == DGSL_PREC_BF16_IR ? 2 : 0;
+  const dgsl::PrecondOp* pre = o.precond == DGSL_PRECOND_BLOCK_JACOBI ? op->precond(coefK, coefM, ptype, s) : nullptr;
   for (;;) {
     DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, w.r64, w.part2, w.max_parts, &nparts, s));
     Sums sr = read_sums(op, w.part2, nparts, s);
@@ -412,13 +416,14 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
     DGSL_CUDA(cudaEventRecord(w.ev0, s));
     if (o.precision == DGSL_PREC_F64) {
       const double stop_rel = std::max(need, 1e-15);
-      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, w.d64, w.r64, stop_rel, budget, cw, timeout_ns, s, &grid));
+      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, w.d64, w.r64, pre, stop_rel, budget, cw, timeout_ns, s,
+                              &grid));
     } else {
       const int bf16 = o.precision == DGSL_PREC_BF16_IR;
       const double stop_rel = std::min(1.0, std::max(o.inner_tol, need));
       DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
-      DGSL_CUDA(launch_cg_f32(d, bf16, (float)coefK, (float)coefM, mean_zero, w.d32, w.r32, stop_rel, budget, cw,
-                              timeout_ns, s, &grid));
+      DGSL_CUDA(launch_cg_f32(d, bf16, (float)coefK, (float)coefM, mean_zero, w.d32, w.r32, pre, stop_rel, budget,
+                              cw, timeout_ns, s, &grid));
     }
     DGSL_CUDA(cudaEventRecord(w.ev1, s));
     DGSL_CUDA(cudaMemcpyAsync(w.h_res, w.res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
@@ -480,6 +485,8 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
     if (opts) o = *opts;
     if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
     if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
+      return fail(DGSL_EINVAL, "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI");
     dgsl_operator* op = const_cast<dgsl_operator*>(cop);
     if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
     if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
@@ -600,12 +607,12 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
     const double need = 0.5 * o.tol / relres;
     int grid = 0;
     if (o.precision == DGSL_PREC_F64) {
-      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, d64, r64, std::max(need, 1e-15), budget, cw, timeout_ns, s,
-                              &grid));
+      DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, d64, r64, nullptr, std::max(need, 1e-15), budget, cw,
+                              timeout_ns, s, &grid));
     } else {
       DGSL_CUDA(launch_scale_to_f32(r64, 1.0 / rnorm, r32, n, s));
       DGSL_CUDA(launch_cg_f32(d, o.precision == DGSL_PREC_BF16_IR, (float)coefK, (float)coefM, mean_zero, d32, r32,
-                              std::min(1.0, std::max(o.inner_tol, need)), budget, cw, timeout_ns, s, &grid));
+                              nullptr, std::min(1.0, std::max(o.inner_tol, need)), budget, cw, timeout_ns, s, &grid));
     }
     DGSL_CUDA(cudaMemcpyAsync(&h_res, res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
     DGSL_CUDA(cudaStreamSynchronize(s));
@@ -652,7 +659,7 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     if (int e = check_vec_args(b, x, n_rhs)) return e;
     if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
     if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
-    if (cop->d.n > kNoAllocMaxDof || cg_vec_bytes(cop->d) > kNoAllocCgSlots * kNoAllocVecBytes)
+    if (cop->d.n > kNoAllocMaxDof || cg_vec_bytes(cop->d, 0) > kNoAllocCgSlots * kNoAllocVecBytes)
       return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: operator has " + std::to_string(cop->d.n) +
                                    " DOFs, above the fixed scratch limit of " + std::to_string(kNoAllocMaxDof));
     dgsl_solve_opts o;
@@ -660,6 +667,8 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     if (opts) o = *opts;
     if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
     if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (o.precond != DGSL_PRECOND_NONE)
+      return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: no preconditioner (its blocks do not fit the fixed scratch)");
     if (!cop->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
     if (o.precision == DGSL_PREC_F32_IR && !cop->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
     if (o.precision == DGSL_PREC_BF16_IR && !cop->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");

@@ -525,6 +525,167 @@ cudaError_t launch_axpy_f64(double a, const double* d, double* x, int64_t n, cud
   return cudaGetLastError();
 }
 
+// ---- block-Jacobi preconditioner (an extension): P_i = D_i^-1 for the diagonal blocks
+// D_i = coefK K_0(i) + coefM A_i Mref of A (symmetrised), one triangle per
+// thread in FP64: Cholesky D = L L^T, W = L^-1 by forward substitution, then
+// P = W^T W, written symmetric into the interleaved layout of the couplings.
+template <int NPHI, typename V>
+__global__ void __launch_bounds__(64) k_block_jacobi(const double* __restrict__ K64, const double* __restrict__ area,
+                                                     const double* __restrict__ Mref, int ne, int64_t n,
+                                                     double coefK, double coefM, V* __restrict__ out, int* bad) {
+  constexpr int VP = 16 / (int)sizeof(V);
+  constexpr int NGP = (NPHI + VP - 1) / VP;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const int64_t row0 = (int64_t)i * NPHI;
+  auto kd = [&](int k, int kk) { return K64[((int64_t)(kk / 2) * n + row0 + k) * 2 + kk % 2]; };
+  const double am = coefM != 0.0 ? coefM * area[i] : 0.0;
+  double L[NPHI][NPHI];
+  for (int k = 0; k < NPHI; ++k)
+    for (int kk = 0; kk < NPHI; ++kk)
+      L[k][kk] = 0.5 * (coefK * (kd(k, kk) + kd(kk, k)) + am * (Mref[k * NPHI + kk] + Mref[kk * NPHI + k]));
+  bool spd = true;
+  for (int j = 0; j < NPHI; ++j) {
+    double d = L[j][j];
+    for (int m = 0; m < j; ++m) d -= L[j][m] * L[j][m];
+    if (!(d > 0.0) || !isfinite(d)) {
+      spd = false;
+      d = 1.0;
+    }
+    const double ljj = sqrt(d);
+    L[j][j] = ljj;
+    for (int r = j + 1; r < NPHI; ++r) {
+      double v = L[r][j];
+      for (int m = 0; m < j; ++m) v -= L[r][m] * L[j][m];
+      L[r][j] = v / ljj;
+    }
+  }
+  if (!spd) atomicExch(bad, 1);
+  double W[NPHI][NPHI];  // L^-1, lower triangular
+  for (int c = 0; c < NPHI; ++c)
+    for (int r = 0; r < NPHI; ++r) {
+      if (r < c) {
+        W[r][c] = 0.0;
+        continue;
+      }
+      double v = r == c ? 1.0 : 0.0;
+      for (int m = c; m < r; ++m) v -= L[r][m] * W[m][c];
+      W[r][c] = v / L[r][r];
+    }
+  for (int k = 0; k < NPHI; ++k)
+    for (int l = k; l < NPHI; ++l) {
+      double v = 0.0;
+      for (int m = l; m < NPHI; ++m) v += W[m][k] * W[m][l];
+      out[((int64_t)(l / VP) * n + row0 + k) * VP + l % VP] = (V)v;
+      out[((int64_t)(k / VP) * n + row0 + l) * VP + k % VP] = (V)v;
+    }
+  for (int k = 0; k < NPHI; ++k)
+    for (int l = NPHI; l < NGP * VP; ++l) out[((int64_t)(l / VP) * n + row0 + k) * VP + l % VP] = V(0);
+}
+
+// Couplings of A P: thread (row, b) forms the row's block b, sum_m A_b(i)[k][m]
+// P_j[m][l] (j the block's triangle), in FP64 from the FP64 couplings and P,
+// rounded once to the coupling type.
+__device__ __forceinline__ void store_cvt(double v, double* o) { *o = v; }
+__device__ __forceinline__ void store_cvt(double v, float* o) { *o = (float)v; }
+__device__ __forceinline__ void store_cvt(double v, uint16_t* o) {  // BF16, round to nearest even
+  const float f = (float)v;
+  uint32_t u = __float_as_uint(f);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+  *o = (uint16_t)(u >> 16);
+}
+
+template <int NPHI, typename T>
+__global__ void __launch_bounds__(128) k_fold_ap(const double* __restrict__ K64, const int32_t* __restrict__ cols,
+                                                 int ne_pad, const double* __restrict__ area,
+                                                 const double* __restrict__ Mref, const double* __restrict__ P64,
+                                                 int64_t n, double coefK, double coefM, T* __restrict__ out) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int NC = 4 * NPHI;
+  constexpr int NG = (NC + VEC - 1) / VEC;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * n) return;
+  const int b = (int)(t / n);
+  const int64_t row = t - (int64_t)b * n;
+  const int i = (int)(row / NPHI), k = (int)(row % NPHI);
+  const int64_t j0 = (int64_t)cols[(size_t)b * ne_pad + i] * NPHI;
+  double a[NPHI];
+#pragma unroll
+  for (int m = 0; m < NPHI; ++m) {
+    const int c = b * NPHI + m;
+    a[m] = coefK * K64[((int64_t)(c / 2) * n + row) * 2 + c % 2];
+    if (b == 0 && coefM != 0.0) a[m] += coefM * area[i] * Mref[k * NPHI + m];
+  }
+  for (int l = 0; l < NPHI; ++l) {
+    double v = 0.0;
+#pragma unroll
+    for (int m = 0; m < NPHI; ++m) v += a[m] * P64[((int64_t)(l / 2) * n + j0 + m) * 2 + l % 2];
+    const int c = b * NPHI + l;
+    store_cvt(v, out + ((int64_t)(c / VEC) * n + row) * VEC + c % VEC);
+  }
+  if (b == 3)
+    for (int c = NC; c < NG * VEC; ++c) store_cvt(0.0, out + ((int64_t)(c / VEC) * n + row) * VEC + c % VEC);
+}
+
+// P from the FP64 layout (2 values per 16 bytes) to the FP32 one (4).
+template <int NPHI>
+__global__ void k_p64_to_f32(const double* __restrict__ P64, int64_t n, float* __restrict__ out) {
+  constexpr int W = (NPHI + 3) / 4 * 4;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= W * n) return;
+  const int l = (int)(t / n);
+  const int64_t row = t - (int64_t)l * n;
+  out[((int64_t)(l / 4) * n + row) * 4 + l % 4] =
+      l < NPHI ? (float)P64[((int64_t)(l / 2) * n + row) * 2 + l % 2] : 0.0f;
+}
+
+size_t precond_ap_bytes(const DevOp& op, int type) {
+  const int vec = type == 1 ? 2 : type == 2 ? 8 : 4;
+  const int ng = (4 * op.nphi + vec - 1) / vec;
+  return (size_t)ng * (size_t)op.n * 16;
+}
+size_t precond_pinv_bytes(const DevOp& op, int type) {
+  const int vp = type == 1 ? 2 : 4;
+  return (size_t)((op.nphi + vp - 1) / vp) * (size_t)op.n * 16;
+}
+
+template <int NPHI>
+static void run_build_precond(const DevOp& op, double coefK, double coefM, int type, void* ap, void* pinv,
+                              double* p64, int* bad, cudaStream_t s) {
+  k_block_jacobi<NPHI, double><<<(op.ne + 63) / 64, 64, 0, s>>>(op.K64, op.area, op.Mref, op.ne, op.n, coefK, coefM,
+                                                                p64, bad);
+  const int gf = (int)((4 * op.n + 127) / 128);
+  if (type == 1)
+    k_fold_ap<NPHI, double><<<gf, 128, 0, s>>>(op.K64, op.cols, op.ne_pad, op.area, op.Mref, p64, op.n, coefK,
+                                               coefM, static_cast<double*>(ap));
+  else if (type == 2)
+    k_fold_ap<NPHI, uint16_t><<<gf, 128, 0, s>>>(op.K64, op.cols, op.ne_pad, op.area, op.Mref, p64, op.n, coefK,
+                                                 coefM, static_cast<uint16_t*>(ap));
+  else
+    k_fold_ap<NPHI, float><<<gf, 128, 0, s>>>(op.K64, op.cols, op.ne_pad, op.area, op.Mref, p64, op.n, coefK,
+                                              coefM, static_cast<float*>(ap));
+  if (type == 1) {
+    if (pinv != p64) cudaMemcpyAsync(pinv, p64, precond_pinv_bytes(op, 1), cudaMemcpyDeviceToDevice, s);
+  } else {
+    constexpr int W = (NPHI + 3) / 4 * 4;
+    k_p64_to_f32<NPHI><<<(int)((W * op.n + 255) / 256), 256, 0, s>>>(p64, op.n, static_cast<float*>(pinv));
+  }
+}
+
+cudaError_t launch_build_precond(const DevOp& op, double coefK, double coefM, int type, void* ap, void* pinv,
+                                 double* p64, int* bad, cudaStream_t s) {
+  if (!op.K64 || op.ne < 1 || type < 0 || type > 2 || !ap || !pinv || !p64) return cudaErrorInvalidValue;
+  switch (op.p) {
+    case 1: run_build_precond<3>(op, coefK, coefM, type, ap, pinv, p64, bad, s); break;
+    case 2: run_build_precond<6>(op, coefK, coefM, type, ap, pinv, p64, bad, s); break;
+    case 3: run_build_precond<10>(op, coefK, coefM, type, ap, pinv, p64, bad, s); break;
+    case 4: run_build_precond<15>(op, coefK, coefM, type, ap, pinv, p64, bad, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch(type == 1 ? 2 : 3);
+  return cudaGetLastError();
+}
+
 __global__ void k_sum_to_first(double* part, int nparts) {
   double v[1] = {0.0};
   for (int j = threadIdx.x; j < nparts; j += blockDim.x) v[0] += part[2 * j];

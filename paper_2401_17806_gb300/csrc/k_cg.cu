@@ -30,6 +30,22 @@
 // 16-byte vector width (the caller's r and x stay unpadded).  Partial sums
 // are reduced per CTA and, once every CTA has arrived, summed by every CTA in
 // the same fixed order, so all CTAs take identical, deterministic decisions.
+//
+// Block-Jacobi preconditioned variant (PRE; an extension, the paper runs CG
+// unpreconditioned): u = P r with P = blockdiag(D_i)^-1, D_i the N_phi x N_phi
+// diagonal block of A on triangle i.  The preconditioned Chronopoulos-Gear
+// iteration needs w = A u; since A u = (A P) r and A P has the sparsity of A
+// (block (i, j) = A_ij P_j), the couplings streamed are those of A P, so the
+// pass still gathers r, w, s and recomputes the coupled residual blocks as
+// above, and u = P_i r is formed for the own block only, from the residual
+// block already in shared memory and the streamed rows of P.  u is thus
+// explicit (a recurrence for u loses the attainable accuracy of the FP32
+// inner solve).  One reduction per pass carries (r.u, w.u, sum w, sum u, r.r,
+// sum r); gamma = r.u replaces r.r in the scalar recurrences.  For the
+// periodic pressure operator the preconditioner is Pi P Pi (Pi: projection
+// to mean zero; symmetric and positive definite on the mean-free vectors), u
+// being projected by its mean from that reduction where it is used, so p and
+// x stay mean-free.
 #include "kassembled.cuh"
 #include "kernels.h"
 
@@ -53,8 +69,10 @@ struct CGParams {
   int mean_zero;
   V* x;          // result, unpadded (written at exit)
   const V* r0;   // right-hand side, unpadded
-  V* vec;        // 8 padded vectors of ne * NPAD: p | x | r0 | r1 | w0 | w1 | s0 | s1
-  double* part;  // [2][max_parts][4] (epoch parity)
+  const V* pinv; // PRE: inverse diagonal blocks, element (row, l) at ((l / VP) n + row) VP + l % VP
+  V* vec;        // padded vectors of ne * NPAD: p | x | r0 | r1 | w0 | w1 | s0 | s1, with PRE
+                 // p | x | u | r0 | r1 | w0 | w1 | s0 | s1
+  double* part;  // [2][max_parts][4 or 6 (PRE)] (epoch parity)
   int max_parts;
   GridBarrier* bar;
   CGResult* res;
@@ -188,26 +206,26 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Deterministic sum of v over the consumer threads, in type W; the result is
-// valid in consumer thread 0 (fixed shuffle tree, then the 4 warp sums in order).
-template <typename W>
-__device__ __forceinline__ void consumer_sum4(W (&v)[4], W (*s_red)[4]) {
+// Deterministic sum of v[NW] over the consumer threads, in type W; the result
+// is valid in consumer thread 0 (fixed shuffle tree, then the 4 warp sums in order).
+template <int NW, typename W>
+__device__ __forceinline__ void consumer_sum(W (&v)[NW], W (*s_red)[NW]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < NW; ++i)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
   if (lane == 0)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) s_red[wid][i] = v[i];
+    for (int i = 0; i < NW; ++i) s_red[wid][i] = v[i];
   cbar();
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
+    for (int i = 0; i < NW; ++i) v[i] = ((s_red[0][i] + s_red[1][i]) + s_red[2][i]) + s_red[3][i];
   cbar();
 }
 
-// Grid-wide sum of acc[0..3] by the consumer warps.  Each CTA publishes its
+// Grid-wide sum of acc[0..NW-1] by the consumer warps.  Each CTA publishes its
 // partial (summed over its threads in V, widened to FP64) and arrives on the
 // counter; once every CTA has arrived, every CTA sums all partials itself in
 // CTA order (FP64), so all obtain bit-identical totals one round trip after
@@ -216,20 +234,20 @@ __device__ __forceinline__ void consumer_sum4(W (&v)[4], W (*s_red)[4]) {
 // half, never a partial that a slower CTA is still reading.  The acq_rel
 // arrival also orders this CTA's vector writes (made before the consumer
 // barrier) for every CTA that later sees the count.
-template <typename V>
-__device__ __forceinline__ bool consumer_allreduce4(GridBarrier* b, double* part, unsigned nblocks,
-                                                    unsigned long long& epoch, uint64_t timeout_ns,
-                                                    V (&acc)[4], double (&tot)[4]) {
-  __shared__ V s_redv[4][4];
-  __shared__ double s_red[4][4];
-  __shared__ double s_tot[4];
+template <int NW, typename V>
+__device__ __forceinline__ bool consumer_allreduce(GridBarrier* b, double* part, unsigned nblocks,
+                                                   unsigned long long& epoch, uint64_t timeout_ns,
+                                                   V (&acc)[NW], double (&tot)[NW]) {
+  __shared__ V s_redv[4][NW];
+  __shared__ double s_red[4][NW];
+  __shared__ double s_tot[NW];
   __shared__ int s_state;
-  consumer_sum4<V>(acc, s_redv);
+  consumer_sum<NW, V>(acc, s_redv);
   ++epoch;
-  double* pe = part + (size_t)(epoch & 1ull) * 4 * nblocks;
+  double* pe = part + (size_t)(epoch & 1ull) * NW * nblocks;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) pe[4 * blockIdx.x + i] = (double)acc[i];
+    for (int i = 0; i < NW; ++i) pe[NW * blockIdx.x + i] = (double)acc[i];
     const unsigned long long target = epoch * (unsigned long long)nblocks;
     unsigned long long v;
     asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(v) : "l"(&b->count) : "memory");
@@ -252,28 +270,31 @@ __device__ __forceinline__ bool consumer_allreduce4(GridBarrier* b, double* part
   }
   cbar();
   const bool ok = s_state >= 0;
-  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  double t[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) t[i] = 0.0;
   if (ok)
     for (unsigned j = threadIdx.x; j < nblocks; j += kCgConsumers)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) t[i] += __ldcg(pe + (size_t)j * 4 + i);
-  consumer_sum4<double>(t, s_red);
+      for (int i = 0; i < NW; ++i) t[i] += __ldcg(pe + (size_t)j * NW + i);
+  consumer_sum<NW, double>(t, s_red);
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) s_tot[i] = t[i];
+    for (int i = 0; i < NW; ++i) s_tot[i] = t[i];
   cbar();
 #pragma unroll
-  for (int i = 0; i < 4; ++i) tot[i] = s_tot[i];
+  for (int i = 0; i < NW; ++i) tot[i] = s_tot[i];
   cbar();
   return ok;
 }
 
 // Tile geometry: TT triangles (a multiple of 4; TR = TT N_phi matrix rows, one
 // per consumer thread) per tile.  A stage holds the tile's couplings (NG
-// chunks of TR 16-byte vectors, each contiguous in global memory), the
-// gathered r, w, s of the 4 TT coupled blocks and the own p, x blocks, and
-// the own triangles' areas (Helmholtz mass term).
-template <int NPHI, typename T, typename V>
+// chunks of TR 16-byte vectors, each contiguous in global memory), with PRE
+// the rows of P (NGP more chunks), the gathered r, w, s of the 4 TT coupled
+// blocks, the own p, x (PRE: p, x, u) blocks, and the own triangles' areas
+// (Helmholtz mass term).
+template <int NPHI, typename T, typename V, bool PRE = false>
 struct TileCfg {
   static constexpr int VEC = Pack<T>::VEC;
   static constexpr int NC = 4 * NPHI;
@@ -285,11 +306,16 @@ struct TileCfg {
   static constexpr int CPB = NPAD / VPC;                     // 16-byte chunks per block
   static constexpr int NB = 4 * TT;                          // coupled blocks per tile
   static constexpr int COUPLE = NG * TR * 16;
-  static constexpr int GATHER = COUPLE;                      // byte offset of r | w | s blocks
-  static constexpr int OWN = GATHER + 3 * NB * NPAD * (int)sizeof(V);  // p | x own blocks
-  static constexpr int AREA = OWN + 2 * TT * NPAD * (int)sizeof(V);    // TT doubles
+  static constexpr int VP = 16 / (int)sizeof(V);                      // P values per 16 bytes
+  static constexpr int NGP = PRE ? (NPHI + VP - 1) / VP : 0;         // P chunks per row
+  static constexpr int PBLK = COUPLE;                                 // byte offset of the P rows
+  static constexpr int GATHER = COUPLE + NGP * TR * 16;               // r | w | s blocks
+  static constexpr int NOWN = PRE ? 3 : 2;                            // own p | x (PRE: | u)
+  static constexpr int OWN = GATHER + 3 * NB * NPAD * (int)sizeof(V);
+  static constexpr int AREA = OWN + NOWN * TT * NPAD * (int)sizeof(V);  // TT doubles
   static constexpr int STAGE = (AREA + TT * 8 + 127) / 128 * 128;
-  static constexpr int S = 3 * STAGE <= 180 * 1024 ? 3 : 2;           // stages per CTA
+  // stages per CTA; PRE keeps two CTAs per SM where three stages allow it
+  static constexpr int S = PRE ? (3 * STAGE <= 104 * 1024 ? 3 : 2) : (3 * STAGE <= 180 * 1024 ? 3 : 2);
 };
 
 __device__ __forceinline__ void lds16(const unsigned char* p, double (&v)[2]) {
@@ -323,11 +349,11 @@ __device__ __forceinline__ void cp_async8_ca(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-template <int NPHI, typename T, typename V>
+template <int NPHI, typename T, typename V, bool PRE>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
-  using C = TileCfg<NPHI, T, V>;
+  using C = TileCfg<NPHI, T, V, PRE>;
   constexpr int S = C::S, TT = C::TT, TR = C::TR, NPAD = C::NPAD, NB = C::NB, CPB = C::CPB, VPC = C::VPC;
-  constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG;
+  constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG, VP = C::VP, NGP = C::NGP, NOWN = C::NOWN;
   extern __shared__ __align__(128) unsigned char stages[];
   __shared__ __align__(8) uint64_t full[S], gfull[S], empty[S];
   __shared__ V s_rn[2][NB * NPHI];
@@ -340,9 +366,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
   const int64_t npv = (int64_t)ne * NPAD;
   V* const pp = a.vec;
   V* const xp = a.vec + npv;
-  auto rbuf = [&](int k) { return a.vec + (2 + (k & 1)) * npv; };
-  auto wbuf = [&](int k) { return a.vec + (4 + (k & 1)) * npv; };
-  auto sbuf = [&](int k) { return a.vec + (6 + (k & 1)) * npv; };
+  V* const up = a.vec + 2 * npv;  // PRE: u (own rows only)
+  constexpr int G0 = PRE ? 3 : 2;  // first gathered (double-buffered) vector
+  auto rbuf = [&](int k) { return a.vec + (G0 + (k & 1)) * npv; };
+  auto wbuf = [&](int k) { return a.vec + (G0 + 2 + (k & 1)) * npv; };
+  auto sbuf = [&](int k) { return a.vec + (G0 + 4 + (k & 1)) * npv; };
   unsigned long long epoch = 0;
 
   if (threadIdx.x == 0) {
@@ -374,6 +402,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
       xp[i] = V(0);
       w0p[i] = V(0);
       s0p[i] = V(0);
+      if constexpr (PRE) up[i] = V(0);
     }
     double acc[4] = {to_d(sum), 0.0, 0.0, 0.0}, tot[4];
     pro_ok = __syncthreads_and(grid_allreduce4(a.bar, a.part, nb, epoch, a.timeout_ns, acc, tot)) != 0;
@@ -414,11 +443,15 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
         const uint32_t bytes = (uint32_t)(nt * NPHI * 16);
         unsigned char* dst = stages + (size_t)s * C::STAGE;
         fence_proxy_async_smem();
-        mbar_expect_tx(&full[s], bytes * NG);
+        mbar_expect_tx(&full[s], bytes * (NG + NGP));
 #pragma unroll 1
         for (int c = 0; c < NG; ++c)
           bulk_g2s_hint(dst + (size_t)c * TR * 16, a.vals + ((size_t)c * a.n + (size_t)tri0 * NPHI) * VEC, bytes,
                         &full[s], pol);
+#pragma unroll 1
+        for (int c = 0; c < NGP; ++c)
+          bulk_g2s_hint(dst + C::PBLK + (size_t)c * TR * 16, a.pinv + ((size_t)c * a.n + (size_t)tri0 * NPHI) * VP,
+                        bytes, &full[s], pol);
       }
     }
     // no CTA leaves with a bulk copy still writing its shared memory
@@ -430,7 +463,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
 
   if (warp == kGatherWarp) {
     // ---- gather producer (32 lanes): cp.async of r, w, s of the coupled
-    // blocks and of the own p, x (and areas), after the pass has been opened
+    // blocks and of the own p, x (PRE: p, x, u) and areas, after the pass has
+    // been opened
     constexpr int NBL = (NB + 31) / 32;
     int cn[NBL];
     auto load_cols = [&](unsigned gg, int (&c)[NBL]) {
@@ -512,11 +546,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
         }
       }
       const int own = nt * CPB;  // 16-byte chunks of one own vector
-      for (int c = lane; c < 2 * own; c += 32) {
-        const int v = c >= own ? 1 : 0;
+      for (int c = lane; c < NOWN * own; c += 32) {
+        const int v = c >= 2 * own ? 2 : c >= own ? 1 : 0;  // own vector v: p, x, u
         const int cx = c - v * own;
         cp_async16(st + C::OWN + (size_t)v * TT * NPAD * sizeof(V) + cx * 16,
-                   (v ? xp : pp) + (int64_t)tri0 * NPAD + cx * VPC);
+                   a.vec + (int64_t)v * npv + (int64_t)tri0 * NPAD + cx * VPC);
       }
       if (a.coefM != V(0))
         for (int c = lane; c < nt; c += 32) cp_async8_ca(st + C::AREA + c * 8, a.area + tri0 + c);
@@ -532,7 +566,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
   bool ok = pro_ok && nq > 0;
   if (threadIdx.x == 0 && !ok) s_stop = 1;
   {
-    V alpha = V(0), beta = V(0), muw = V(0), g_old = V(0), a_old = V(0);
+    V alpha = V(0), beta = V(0), muw = V(0), muu = V(0), g_old = V(0), a_old = V(0);
     double stop = 0.0;
     const double inv_n = 1.0 / (double)a.n;
     unsigned g = 0;  // this CTA's tile sequence number (continues across passes)
@@ -540,7 +574,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
       V* const rn = rbuf(pass + 1);
       V* const wn = wbuf(pass + 1);
       V* const sn = sbuf(pass + 1);
-      V g_rr = V(0), g_wr = V(0), g_w = V(0), g_r = V(0);
+      // partial sums: r.r, w.r, sum w, sum r  (PRE: r.u, w.u, sum w, sum u, r.r, sum r)
+      V g0 = V(0), g1 = V(0), g2 = V(0), g3 = V(0), g4 = V(0), g5 = V(0);
       for (int q = 0; q < nq; ++q, ++g) {
         const int s = (int)(g % S);
         const unsigned par = (g / S) & 1u;
@@ -587,13 +622,16 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
             wv = fma(a.coefM * (V)ar, mv, wv);
           }
           const int o = lt * 4 * NPAD + k;  // own block of triangle lt among the gathered
-          const V* own = reinterpret_cast<const V*>(st + C::OWN);
-          const V r_old = gr[o];
+          const V* own = reinterpret_cast<const V*>(st + C::OWN) + lt * NPAD + k;
           const V w_old = gw[o] - muw;
           const V s_old = gs[o];
-          const V p_old = own[lt * NPAD + k];
-          const V x_old = own[TT * NPAD + lt * NPAD + k];
-          const V p_new = fma(beta, p_old, r_old);
+          const V p_old = own[0];
+          const V x_old = own[TT * NPAD];
+          // p = r + beta p  (PRE: p = Pi u + beta p)
+          V d_old;
+          if constexpr (PRE) d_old = own[2 * TT * NPAD] - muu;
+          else d_old = gr[o];
+          const V p_new = fma(beta, p_old, d_old);
           const V s_new = fma(beta, s_old, w_old);
           const V r_new = xs[k];
           const int64_t prow = (int64_t)(tri0 + lt) * NPAD + k;
@@ -602,31 +640,65 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
           sn[prow] = s_new;
           rn[prow] = r_new;
           wn[prow] = wv;
-          g_rr = fma(r_new, r_new, g_rr);
-          g_wr = fma(wv, r_new, g_wr);
-          g_w += wv;
-          g_r += r_new;
+          if constexpr (PRE) {
+            // u = P_i r from the streamed rows of P and the own residual block
+            const unsigned char* pv = st + C::PBLK + (size_t)threadIdx.x * 16;
+            V u = V(0);
+#pragma unroll
+            for (int gg = 0; gg < NGP; ++gg) {
+              V v[VP];
+              lds16(pv + (size_t)gg * TR * 16, v);
+#pragma unroll
+              for (int l4 = 0; l4 < VP; ++l4) {
+                const int l = gg * VP + l4;
+                if (l < NPHI) u = fma(v[l4], xs[l], u);
+              }
+            }
+            up[prow] = u;
+            g0 = fma(r_new, u, g0);
+            g1 = fma(wv, u, g1);
+            g2 += wv;
+            g3 += u;
+            g4 = fma(r_new, r_new, g4);
+            g5 += r_new;
+          } else {
+            g0 = fma(r_new, r_new, g0);
+            g1 = fma(wv, r_new, g1);
+            g2 += wv;
+            g3 += r_new;
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
       }
       if (!ok) break;
-      V acc[4] = {g_rr, g_wr, g_w, g_r};
-      double tot[4];
-      if (!consumer_allreduce4<V>(a.bar, a.part, nb, epoch, a.timeout_ns, acc, tot)) {
+      constexpr int NW = PRE ? 6 : 4;
+      V acc[NW];
+      acc[0] = g0;
+      acc[1] = g1;
+      acc[2] = g2;
+      acc[3] = g3;
+      if constexpr (NW > 4) {
+        acc[4] = g4;
+        acc[NW - 1] = g5;
+      }
+      double tot[NW];
+      if (!consumer_allreduce<NW, V>(a.bar, a.part, nb, epoch, a.timeout_ns, acc, tot)) {
         ok = false;
         break;
       }
       // scalar recurrences in V: FP64 division is slow on this GPU and the
       // FP32 inner solve carries its scalars in FP32 anyway
-      const double gg = tot[0];
-      const double mu = a.mean_zero ? tot[2] * inv_n : 0.0;
+      const double mu = a.mean_zero ? tot[2] * inv_n : 0.0;  // mean of w
+      // PRE: u enters as Pi u = u - mu_u 1
+      const double mu_u = PRE && a.mean_zero ? tot[3] * inv_n : 0.0;
+      const double gg = PRE ? tot[0] - mu_u * tot[NW - 1] : tot[0];  // gamma: r.r (PRE: r . Pi u)
       const V gv = (V)gg;
-      const V dv = (V)(tot[1] - mu * tot[3]);  // (w - mu 1) . r
-      rr = gg;
+      const V dv = (V)(tot[1] - mu * tot[3]);  // (w - mu 1) . r  (PRE: . Pi u)
+      rr = PRE ? tot[4 % NW] : gg;             // r.r
       V an, bn;
       if (pass == 0) {
-        rr0 = gg;
+        rr0 = rr;
         stop = a.stop_rel * a.stop_rel * rr0;
         bn = V(0);
         an = gv / dv;
@@ -635,12 +707,13 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
         bn = gv / g_old;
         an = gv / (dv - bn * gv / a_old);
       }
-      if (!(gg > stop) || it >= a.max_iters || !(an > V(0)) || !isfinite(an)) break;
+      if (!(rr > stop) || it >= a.max_iters || !(an > V(0)) || !isfinite(an)) break;
       g_old = gv;
       a_old = an;
       alpha = an;
       beta = bn;
       muw = (V)mu;
+      muu = (V)mu_u;
     }
   }
   if (threadIdx.x == 0) {
@@ -703,11 +776,12 @@ int coop_blocks(KernelT kern, size_t dyn_smem) {
   return sms * per;
 }
 
-template <int NPHI, typename T, typename V>
-cudaError_t run_cg(const DevOp& op, const T* vals, V coefK, V coefM, int mean_zero, V* x, V* r, double stop_rel,
-                   int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s, int* grid_used) {
-  auto kern = k_cg<NPHI, T, V>;
-  using Cfg = TileCfg<NPHI, T, V>;
+template <int NPHI, typename T, typename V, bool PRE>
+cudaError_t run_cg(const DevOp& op, const T* vals, const V* pinv, V coefK, V coefM, int mean_zero, V* x, V* r,
+                   double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
+                   int* grid_used) {
+  auto kern = k_cg<NPHI, T, V, PRE>;
+  using Cfg = TileCfg<NPHI, T, V, PRE>;
   const size_t dyn = Cfg::S * (size_t)Cfg::STAGE;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (err != cudaSuccess) return err;
@@ -728,6 +802,7 @@ cudaError_t run_cg(const DevOp& op, const T* vals, V coefK, V coefM, int mean_ze
   a.mean_zero = mean_zero;
   a.x = x;
   a.r0 = r;
+  a.pinv = pinv;
   a.vec = static_cast<V*>(w.vec);
   a.part = w.part;
   a.max_parts = w.max_parts;
@@ -754,40 +829,62 @@ int cg_max_blocks(const DevOp& op, int prec) {
   return sms * 8;
 }
 
-// Bytes of the persistent CG's vectors: 8 vectors of ne blocks, each block
-// N_phi values padded to a whole number of 16-byte chunks (the larger of the
-// FP32 and FP64 layouts, so one buffer serves every precision).
-size_t cg_vec_bytes(const DevOp& op) {
+// Bytes of the persistent CG's vectors: 8 vectors of ne blocks (9 with the
+// block-Jacobi preconditioner), each block N_phi values padded to a whole
+// number of 16-byte chunks (the larger of the FP32 and FP64 layouts, so one
+// buffer serves every precision).
+size_t cg_vec_bytes(const DevOp& op, int precond) {
   const size_t pad32 = (size_t)(op.nphi + 3) / 4 * 4 * sizeof(float);
   const size_t pad64 = (size_t)(op.nphi + 1) / 2 * 2 * sizeof(double);
-  return 8 * (size_t)op.ne * std::max(pad32, pad64) + 256;
+  return (precond ? 9 : 8) * (size_t)op.ne * std::max(pad32, pad64) + 256;
 }
 
-#define DGSL_CG_CASES(T, V, VALS)                                                                              \
-  switch (op.p) {                                                                                              \
-    case 1: return run_cg<3, T, V>(op, VALS, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w, timeout_ns, s, grid_used);  \
-    case 2: return run_cg<6, T, V>(op, VALS, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w, timeout_ns, s, grid_used);  \
-    case 3: return run_cg<10, T, V>(op, VALS, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w, timeout_ns, s, grid_used); \
-    case 4: return run_cg<15, T, V>(op, VALS, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w, timeout_ns, s, grid_used); \
-  }                                                                                                            \
+#define DGSL_CG_RUN(NPHI, T, V, VALS)                                                                           \
+  (pinv ? run_cg<NPHI, T, V, true>(op, VALS, pinv, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w,      \
+                                   timeout_ns, s, grid_used)                                                   \
+        : run_cg<NPHI, T, V, false>(op, VALS, nullptr, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w,  \
+                                    timeout_ns, s, grid_used))
+#define DGSL_CG_CASES(T, V, VALS)          \
+  switch (op.p) {                          \
+    case 1: return DGSL_CG_RUN(3, T, V, VALS);  \
+    case 2: return DGSL_CG_RUN(6, T, V, VALS);  \
+    case 3: return DGSL_CG_RUN(10, T, V, VALS); \
+    case 4: return DGSL_CG_RUN(15, T, V, VALS); \
+  }                                        \
   return cudaErrorInvalidValue;
 
+// With a preconditioned operator the couplings are those of A P, which
+// include coefK and the mass term: the kernel then runs with coefK = 1, coefM = 0.
 cudaError_t launch_cg_f64(const DevOp& op, double coefK, double coefM, int mean_zero, double* x, double* r,
-                          double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
-                          int* grid_used) {
-  if (!op.K64) return cudaErrorInvalidValue;
-  DGSL_CG_CASES(double, double, op.K64)
+                          const PrecondOp* pre, double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns,
+                          cudaStream_t s, int* grid_used) {
+  if (!op.K64 || (pre && (!pre->ap || !pre->pinv))) return cudaErrorInvalidValue;
+  const double* pinv = pre ? static_cast<const double*>(pre->pinv) : nullptr;
+  const double* vals = pre ? static_cast<const double*>(pre->ap) : op.K64;
+  if (pre) {
+    coefK = 1.0;
+    coefM = 0.0;
+  }
+  DGSL_CG_CASES(double, double, vals)
 }
 
 cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, int mean_zero, float* x, float* r,
-                          double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
-                          int* grid_used) {
-  if (bf16) {
-    if (!op.K16) return cudaErrorInvalidValue;
-    DGSL_CG_CASES(uint16_t, float, op.K16)
+                          const PrecondOp* pre, double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns,
+                          cudaStream_t s, int* grid_used) {
+  if (pre && (!pre->ap || !pre->pinv)) return cudaErrorInvalidValue;
+  const float* pinv = pre ? static_cast<const float*>(pre->pinv) : nullptr;
+  if (pre) {
+    coefK = 1.0f;
+    coefM = 0.0f;
   }
-  if (!op.K32) return cudaErrorInvalidValue;
-  DGSL_CG_CASES(float, float, op.K32)
+  if (bf16) {
+    const uint16_t* vals = pre ? static_cast<const uint16_t*>(pre->ap) : op.K16;
+    if (!vals) return cudaErrorInvalidValue;
+    DGSL_CG_CASES(uint16_t, float, vals)
+  }
+  const float* vals = pre ? static_cast<const float*>(pre->ap) : op.K32;
+  if (!vals) return cudaErrorInvalidValue;
+  DGSL_CG_CASES(float, float, vals)
 }
 
 }  // namespace dgsl

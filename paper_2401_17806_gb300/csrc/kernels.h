@@ -82,20 +82,44 @@ struct CGResult {
   double rr;
 };
 struct CGWork {
-  void* vec = nullptr;    // cg_vec_bytes(op): p, x, r, w, s (r, w, s double-buffered), per-triangle padded
-  double* part = nullptr; // 2 x max_parts x 4 partial sums (epoch parity)
+  void* vec = nullptr;    // cg_vec_bytes(op, precond): p, x, r, w, s (r, w, s double-buffered; with the
+                          // preconditioner also u), per-triangle padded
+  double* part = nullptr; // 2 x max_parts x 4 partial sums (6 with the preconditioner; epoch parity)
   GridBarrier* bar = nullptr;
   CGResult* res = nullptr;
   int max_parts = 0;
 };
+// ---- block-Jacobi preconditioner (an extension)
+// P = blockdiag(P_i), P_i = D_i^-1 with D_i = coefK K_0(i) + coefM A_i Mref,
+// the diagonal N_phi x N_phi block of A on triangle i, by Cholesky in FP64.
+// The preconditioned CG streams the couplings of A P (block (i, j) = A_ij P_j,
+// the mass term folded into the diagonal block; the layout of DevOp's K
+// arrays) and P itself (element (row, l) at ((l / VP) n + row) VP + l % VP,
+// VP = 16 / sizeof(value), padding columns 0).
+struct PrecondOp {
+  const void* ap = nullptr;    // couplings of A P: FP32, FP64 or BF16 bits (the CG's coupling type)
+  const void* pinv = nullptr;  // P: FP32, or FP64 for the FP64 CG
+};
+// type: 0 FP32 couplings, 1 FP64, 2 BF16 (P in FP32 for 0 and 2, FP64 for 1)
+size_t precond_ap_bytes(const DevOp& op, int type);
+size_t precond_pinv_bytes(const DevOp& op, int type);
+// Builds P in FP64 into p64 (precond_pinv_bytes(op, 1) bytes), A P into ap and
+// P in the vector type into pinv (for type 1 pinv may be p64).  *bad (device
+// int, zeroed by the caller) becomes 1 if a diagonal block is not positive
+// definite.  Needs the FP64 couplings.
+cudaError_t launch_build_precond(const DevOp& op, double coefK, double coefM, int type, void* ap, void* pinv,
+                                 double* p64, int* bad, cudaStream_t s);
+
+// pre: nullptr for plain CG, else the preconditioned operator built by
+// launch_build_precond for the same coefK, coefM and coupling type.
 cudaError_t launch_cg_f64(const DevOp& op, double coefK, double coefM, int mean_zero, double* x,
-                          double* r, double stop_rel, int max_iters, const CGWork& w,
+                          double* r, const PrecondOp* pre, double stop_rel, int max_iters, const CGWork& w,
                           uint64_t timeout_ns, cudaStream_t s, int* grid_used);
 cudaError_t launch_cg_f32(const DevOp& op, int bf16, float coefK, float coefM, int mean_zero, float* x,
-                          float* r, double stop_rel, int max_iters, const CGWork& w,
+                          float* r, const PrecondOp* pre, double stop_rel, int max_iters, const CGWork& w,
                           uint64_t timeout_ns, cudaStream_t s, int* grid_used);
 int cg_max_blocks(const DevOp& op, int prec);
-size_t cg_vec_bytes(const DevOp& op);
+size_t cg_vec_bytes(const DevOp& op, int precond);
 // Bounded-wait self-test (see k_cg.cu): records kStatusTimeout in bar->status.
 cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s);
 

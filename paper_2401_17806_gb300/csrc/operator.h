@@ -66,6 +66,22 @@ struct dgsl_operator {
     CGResult* h_res = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int max_parts = 0;
+    // block-Jacobi preconditioned operators (A P and P) of the last few
+    // systems (coefficients and coupling type), least recently used replaced first
+    struct Precond {
+      dgsl::PrecondOp op;
+      void* ap = nullptr;
+      void* pinv = nullptr;
+      size_t ap_bytes = 0, pinv_bytes = 0;
+      double coefK = 0.0, coefM = 0.0;
+      int type = 0;
+      uint64_t used = 0;
+      bool valid = false;
+    } pj[4];
+    uint64_t pj_clock = 0;
+    double* p64 = nullptr;  // FP64 P while building (FP32 / BF16 systems)
+    int* pj_bad = nullptr;
+    int* h_pj_bad = nullptr;  // pinned
   } w;
 
   template <class T>
@@ -90,6 +106,7 @@ struct dgsl_operator {
       for (void* p : allocs) cudaFree(p);
       if (w.h_part) cudaFreeHost(w.h_part);
       if (w.h_res) cudaFreeHost(w.h_res);
+      if (w.h_pj_bad) cudaFreeHost(w.h_pj_bad);
       if (w.ev0) cudaEventDestroy(w.ev0);
       if (w.ev1) cudaEventDestroy(w.ev1);
     }
@@ -102,8 +119,8 @@ struct dgsl_operator {
     w.d64 = dalloc<double>(d.n);
     w.r32 = dalloc<float>(d.n);
     w.d32 = dalloc<float>(d.n);
-    w.vec = dalloc<double>((cg_vec_bytes(d) + 7) / 8);
-    w.part = dalloc<double>(8 * (size_t)w.max_parts);  // two halves of 4 sums per CTA
+    w.vec = dalloc<double>((cg_vec_bytes(d, 1) + 7) / 8);
+    w.part = dalloc<double>(12 * (size_t)w.max_parts);  // two halves of up to 6 sums per CTA
     w.part2 = dalloc<double>(2 * (size_t)w.max_parts);
     w.bar = dalloc<GridBarrier>(1);
     w.res = dalloc<CGResult>(1);
@@ -111,6 +128,51 @@ struct dgsl_operator {
     DGSL_CUDA(cudaMallocHost(&w.h_res, sizeof(CGResult)));
     DGSL_CUDA(cudaEventCreate(&w.ev0));
     DGSL_CUDA(cudaEventCreate(&w.ev1));
+  }
+  // Block-Jacobi preconditioned operator for A = coefM Mbar + coefK K with
+  // couplings of type 0 (FP32), 1 (FP64) or 2 (BF16), built on stream s unless
+  // kept from an earlier solve; call after ensure_work.
+  const dgsl::PrecondOp* precond(double coefK, double coefM, int type, cudaStream_t s) {
+    ++w.pj_clock;
+    Work::Precond* slot = nullptr;
+    for (auto& c : w.pj)
+      if (c.valid && c.coefK == coefK && c.coefM == coefM && c.type == type) {
+        c.used = w.pj_clock;
+        return &c.op;
+      }
+    for (auto& c : w.pj)
+      if (!slot || (!c.valid && slot->valid) || (c.valid == slot->valid && c.used < slot->used)) slot = &c;
+    Work::Precond& c = *slot;
+    c.valid = false;
+    // (a buffer too small for a new type is replaced; the old one stays allocated until destroy)
+    const size_t need_ap = dgsl::precond_ap_bytes(d, type), need_p = dgsl::precond_pinv_bytes(d, type);
+    if (c.ap_bytes < need_ap) {
+      c.ap = dalloc<double>((need_ap + 7) / 8);
+      c.ap_bytes = need_ap;
+    }
+    if (c.pinv_bytes < need_p) {
+      c.pinv = dalloc<double>((need_p + 7) / 8);
+      c.pinv_bytes = need_p;
+    }
+    if (type != 1 && !w.p64) w.p64 = dalloc<double>((dgsl::precond_pinv_bytes(d, 1) + 7) / 8);
+    if (!w.pj_bad) {
+      w.pj_bad = dalloc<int>(1);
+      DGSL_CUDA(cudaMallocHost(&w.h_pj_bad, sizeof(int)));
+    }
+    double* p64 = type == 1 ? static_cast<double*>(c.pinv) : w.p64;
+    DGSL_CUDA(cudaMemsetAsync(w.pj_bad, 0, sizeof(int), s));
+    DGSL_CUDA(dgsl::launch_build_precond(d, coefK, coefM, type, c.ap, c.pinv, p64, w.pj_bad, s));
+    DGSL_CUDA(cudaMemcpyAsync(w.h_pj_bad, w.pj_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*w.h_pj_bad) throw Error(DGSL_EINVAL, "block-Jacobi: a diagonal block of A is not positive definite");
+    c.op.ap = c.ap;
+    c.op.pinv = c.pinv;
+    c.coefK = coefK;
+    c.coefM = coefM;
+    c.type = type;
+    c.used = w.pj_clock;
+    c.valid = true;
+    return &c.op;
   }
 };
 

@@ -22,6 +22,7 @@ MAIN, DUAL = 0, 1
 FORM_ASSEMBLED, FORM_FACTORED = 0, 1
 SCHUR, HELMHOLTZ = 0, 1
 PREC_F64, PREC_F32_IR, PREC_BF16_IR = 0, 1, 2
+PRECOND_NONE, PRECOND_BLOCK_JACOBI = 0, 1
 
 
 class DgslError(RuntimeError):
@@ -58,7 +59,7 @@ class dgsl_maps(C.Structure):
 class dgsl_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int32), ("precision", C.c_int32),
                 ("use_x0", C.c_int32), ("inner_tol", C.c_double), ("max_refine", C.c_int32),
-                ("form", C.c_int32)]
+                ("form", C.c_int32), ("precond", C.c_int32), ("pad", C.c_int32)]
 
 
 class dgsl_solve_info(C.Structure):
@@ -325,19 +326,23 @@ def _noalloc_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, chec
 Operator.dgsl_cg_solve_noalloc = _noalloc_solve
 
 
-def solve_opts(**kw):
-    o = dgsl_default_solve_opts()
+def _set_fields(o, kw):
+    names = {f for f, _ in type(o)._fields_}
     for k, v in kw.items():
+        if k not in names:  # ctypes would add a plain attribute the library never sees
+            raise TypeError(f"{type(o).__name__} has no field {k!r}")
         setattr(o, k, v)
     return o
+
+
+def solve_opts(**kw):
+    return _set_fields(dgsl_default_solve_opts(), kw)
 
 
 def engine_opts(**kw):
     o = dgsl_engine_opts()
     load().dgsl_default_engine_opts(C.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
-    return o
+    return _set_fields(o, kw)
 
 
 def request(op, kind, coef, b, x, tol=0.0, n_rhs=1):
