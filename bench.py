@@ -63,6 +63,8 @@ def parse_args(argv=None):
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
     ap.add_argument("--cg-iters", type=int, default=200)
+    ap.add_argument("--precond", action="store_true",
+                    help="cg workload: block-Jacobi preconditioned CG")
     ap.add_argument("--batch-solves", type=int, default=64)
     ap.add_argument("--batch-nmax", type=int, default=64)
     ap.add_argument("--rhs", type=int, default=8)
@@ -339,9 +341,10 @@ def fourier_rhs(op, seed, dt):
 
 def cg_leg(args):
     """One persistent FP32 CG launch (Schur operator, dt = 1e-3, random right-hand
-    side) capped at --cg-iters iterations on the N x N mesh: the case the ncu
-    summaries under profiles/ capture.  Runs it twice and prints the event-timed
-    cost per iteration of the second (warm) launch."""
+    side) capped at --cg-iters iterations on the N x N mesh, block-Jacobi
+    preconditioned with --precond: the case the ncu summaries under profiles/
+    capture.  Runs it twice (the first launch also builds the preconditioned
+    operator) and prints the event-timed cost per iteration of the second."""
     import torch
     from paper_2401_17806_gb300 import build, dgsl, synth
     build.build()
@@ -350,10 +353,12 @@ def cg_leg(args):
     op = dgsl.Operator(xy, tri, per, args.p, store=dgsl.STORE_F64 | dgsl.STORE_F32)
     b = torch.tensor(synth.standard_normal(op.n_dof, 1), device="cuda")
     x = torch.zeros_like(b)
-    o = dgsl.solve_opts(tol=1e-30, max_iters=args.cg_iters, max_refine=1, precision=dgsl.PREC_F32_IR)
+    o = dgsl.solve_opts(tol=1e-30, max_iters=args.cg_iters, max_refine=1, precision=dgsl.PREC_F32_IR,
+                        precond=dgsl.PRECOND_BLOCK_JACOBI if args.precond else dgsl.PRECOND_NONE)
     for _ in range(2):  # the first launch warms up (module load, attributes); the second is reported
         info = op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], b, x, opts=o, check=False)[0]
-    print(json.dumps({"workload": f"one FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
+    kind = "block-Jacobi preconditioned " if args.precond else ""
+    print(json.dumps({"workload": f"one {kind}FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
                       "grid": info.grid, "us_per_iter": 1e3 * info.cg_kernel_ms / max(1, info.iters)}))
 
 
