@@ -332,6 +332,10 @@ typedef struct {
   int32_t device;           /* CUDA device (all operators must live there) */
   int64_t hbm_budget_bytes; /* server: cap on workspace + resident operators (0 = 150e9) */
   int64_t idle_us;          /* server: how long an idle engine waits for work (default 500) */
+  int32_t precond;          /* DGSL_PRECOND_* for every request (default NONE); with
+                               BLOCK_JACOBI each operator keeps the couplings of A P and
+                               P of its systems (see dgsl_cg_solve), counted in the budget */
+  int32_t pad;
 } dgsl_engine_opts;
 
 void dgsl_default_engine_opts(dgsl_engine_opts* opts);

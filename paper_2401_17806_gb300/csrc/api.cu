@@ -388,7 +388,10 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
   cw.res = w.res;
   cw.max_parts = w.max_parts;
   const int ptype = o.precision == DGSL_PREC_F64 ? 1 : o.precision == DGSL_PREC_BF16_IR ? 2 : 0;
-  const dgsl::PrecondOp* pre = o.precond == DGSL_PRECOND_BLOCK_JACOBI ? op->precond(coefK, coefM, ptype, s) : nullptr;
+  auto* held = o.precond == DGSL_PRECOND_BLOCK_JACOBI ? op->acquire_precond(coefK, coefM, ptype, s) : nullptr;
+  std::unique_ptr<dgsl_operator::Work::Precond, void (*)(dgsl_operator::Work::Precond*)> hold(
+      held, dgsl_operator::release_precond);
+  const dgsl::PrecondOp* pre = held ? &held->op : nullptr;
   for (;;) {
     DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, w.r64, w.part2, w.max_parts, &nparts, s));
     Sums sr = read_sums(op, w.part2, nparts, s);

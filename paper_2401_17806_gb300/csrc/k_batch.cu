@@ -16,7 +16,10 @@
 //            p = r + beta p;  s = w' + beta s;  d += alpha p;  r <- r - alpha s;
 //            w <- A r;  sums (r.r, w.r, sum w, sum r);
 //            beta' = g'/g, alpha' = g' / (dw' - beta' g'/alpha)   (CG0: beta' = 0)
-//          (w' = w - mean w for the periodic pressure operator)
+//          (w' = w - mean w for the periodic pressure operator); with the
+//          block-Jacobi preconditioner (as in k_cg.cu) p = u' + beta p,
+//          w <- (A P) r, u = P_i r on the own block, sums (r.u, w.u, sum w,
+//          sum u, r.r, sum r), u' = u - mean u for the pressure operator
 //   UPDATE x += ||r64|| d  (FP64), then RESID again
 //   XSUM / XFIX  final mean removal (pressure), then DONE
 // The right-hand sides of a slot share every coupling tile; a right-hand side
@@ -51,7 +54,7 @@ constexpr int kECouplingWarp = kECWarps;
 constexpr int kEGatherWarp = kECouplingWarp + 1;
 constexpr int kEMaxStages = 8;
 constexpr int kEDynSmem = 184 * 1024;             // the stage ring; each pass divides it into stages
-constexpr int kNV = 4 * kMaxRhs;                  // partial sums per chunk (4 per right-hand side)
+constexpr int kNV = kEngineSums;                  // partial sums per chunk (4, or 6 preconditioned, per RHS)
 
 // ---------------------------------------------------------------- state
 enum : int { PH_BSUM = 0, PH_RESID, PH_SCALE, PH_CG0, PH_CG, PH_UPDATE, PH_XSUM, PH_XFIX, PH_DONE };
@@ -61,7 +64,7 @@ struct BRhs {                      // per right-hand side (kernel-owned)
   int done;                        // refinement finished (converged or failed)
   int inner;                       // inner CG running in the current refinement step
   double bmean, bnorm, rnorm, rmean, relres, best, xmean, stop;
-  float alpha, beta, muw, g_old, a_old, pad;
+  float alpha, beta, muw, g_old, a_old, muu;  // muu: mean of u (preconditioned pressure solves)
 };
 
 struct BState {                    // kernel-owned, one per slot (device memory)
@@ -99,15 +102,19 @@ struct ETile {
 __host__ __device__ constexpr int e_block_len(int nphi, int rp) { return (nphi * rp + 3) / 4 * 4; }
 __host__ __device__ constexpr int e_nphi(int p) { return (p + 1) * (p + 2) / 2; }
 __host__ __device__ constexpr int e_tt(int nphi) { return (kERows / nphi) / 4 * 4; }
-// Stage byte offsets for (NPHI, T, RP): couplings | gathered r, w, s of the
-// 4 TT coupled blocks | own blocks of d, p (TT each) | areas (TT doubles).
-template <int NPHI, typename T, int RP>
+// Stage byte offsets for (NPHI, T, RP, PRE): couplings | PRE: rows of P (NGP
+// chunks of TR 16-byte vectors) | gathered r, w, s of the 4 TT coupled blocks |
+// own blocks of d, p (PRE: and u; TT each) | areas (TT doubles).
+__host__ __device__ constexpr int e_ngp(int nphi, bool pre) { return pre ? (nphi + 3) / 4 : 0; }
+template <int NPHI, typename T, int RP, bool PRE>
 struct EStage {
   using C = ETile<NPHI, T>;
   static constexpr int BL = e_block_len(NPHI, RP);
-  static constexpr int GATHER = C::COUPLE;
+  static constexpr int NGP = e_ngp(NPHI, PRE);
+  static constexpr int PBLK = C::COUPLE;
+  static constexpr int GATHER = C::COUPLE + NGP * C::TR * 16;
   static constexpr int OWN = GATHER + 3 * C::NB * BL * 4;
-  static constexpr int AREA = OWN + 2 * C::TT * BL * 4;
+  static constexpr int AREA = OWN + (PRE ? 3 : 2) * C::TT * BL * 4;
 };
 // New-residual values of one tile (4 TT padded blocks) for every degree and RP.
 constexpr int kRnMax = 4 * kERows * kMaxRhs;
@@ -187,7 +194,7 @@ struct ChunkCtx {
   int phase, cur, rp, bl;
   int done_mask, inner_mask;        // bit r: right-hand side r finished / runs an inner CG
   double bmean[kMaxRhs], scale[kMaxRhs], rmean[kMaxRhs], rnorm[kMaxRhs], xmean[kMaxRhs];
-  float alpha[kMaxRhs], beta[kMaxRhs], muw[kMaxRhs];
+  float alpha[kMaxRhs], beta[kMaxRhs], muw[kMaxRhs], muu[kMaxRhs];
 };
 
 // The slot's descriptor and per-pass scalars into shared memory (one warp:
@@ -212,6 +219,7 @@ __device__ __forceinline__ void load_slot(BSlotDesc& d, ChunkCtx& c, const BSlot
     c.alpha[lane] = __ldcg(&q->alpha);
     c.beta[lane] = __ldcg(&q->beta);
     c.muw[lane] = __ldcg(&q->muw);
+    c.muu[lane] = __ldcg(&q->muu);
   }
   const unsigned dm = __ballot_sync(0xffffffffu, lane < kMaxRhs && done);
   const unsigned im = __ballot_sync(0xffffffffu, lane < kMaxRhs && inner);
@@ -279,6 +287,7 @@ __device__ __forceinline__ void stream_chunk(const BSlotDesc& d, const ChunkCtx&
         fd[2 * L + base + r] = v;    // r0
         fd[4 * L + base + r] = 0.f;  // w0
         fd[6 * L + base + r] = 0.f;  // s0
+        if (d.precond) fd[8 * L + base + r] = 0.f;  // u
       }
     }
     ecbar();
@@ -385,10 +394,10 @@ __device__ __forceinline__ void e_lds(const unsigned char* p, float (&v)[VEC]) {
 // of the 4 TT gathered blocks into rn ([block][BL]).  Then (after the
 // caller's barrier) the two threads of each matrix row: w = A r_new, and the
 // row updates, each for half of the right-hand sides.
-template <int NPHI, typename T, int RP>
+template <int NPHI, typename T, int RP, bool PRE>
 __device__ __forceinline__ void cg_combine(const ChunkCtx& c, int nt, const unsigned char* st, float* rn) {
   using C = ETile<NPHI, T>;
-  using S = EStage<NPHI, T, RP>;
+  using S = EStage<NPHI, T, RP, PRE>;
   constexpr int BL = S::BL, NB = C::NB, Q = BL / 4;  // float4 per block
   const float4* gr = reinterpret_cast<const float4*>(st + S::GATHER);
   const float4* gw = gr + NB * Q;
@@ -432,11 +441,12 @@ struct RhsSplit {
   static constexpr int RT = RP >= 2 ? RP / 2 : 1;
 };
 
-template <int NPHI, typename T, int RP>
+template <int NPHI, typename T, int RP, bool PRE>
 __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, int tri0, int nt,
-                                        const unsigned char* st, const float* rn, float (&acc)[4][RhsSplit<RP>::RT]) {
+                                        const unsigned char* st, const float* rn,
+                                        float (&acc)[PRE ? 6 : 4][RhsSplit<RP>::RT]) {
   using C = ETile<NPHI, T>;
-  using S = EStage<NPHI, T, RP>;
+  using S = EStage<NPHI, T, RP, PRE>;
   constexpr int BL = S::BL, TT = C::TT, TR = C::TR, NG = C::NG, VEC = C::VEC, NC = C::NC, NB = C::NB;
   constexpr int RT = RhsSplit<RP>::RT;
   const int row = threadIdx.x & (kERows - 1), half = threadIdx.x / kERows;
@@ -463,10 +473,11 @@ __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, i
       }
     }
   }
-  const float coefK = (float)d.coefK;
+  // (PRE: the couplings of A P include coefK and the mass term)
+  const float coefK = PRE ? 1.f : (float)d.coefK;
 #pragma unroll
   for (int r = 0; r < RT; ++r) q[r] *= coefK;
-  if (d.coefM != 0.0) {
+  if (!PRE && d.coefM != 0.0) {
     float mv[RT];
 #pragma unroll
     for (int r = 0; r < RT; ++r) mv[r] = 0.f;
@@ -491,16 +502,52 @@ __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, i
   ld_rp<RT>(own, dd);
   ld_rp<RT>(own + TT * BL, pp);
   ld_rp<RT>(xs + k * RP, rr);
+  float u[RT];
+  if constexpr (PRE) {
+    // p = Pi u + beta p from the own u of the previous pass; u = P_i r_new
+    // from the streamed rows of P and the own block of the new residual
+    ld_rp<RT>(own + 2 * TT * BL, ro);
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      ro[r] -= c.muu[h0 + r];
+      u[r] = 0.f;
+    }
+    const unsigned char* pv = st + S::PBLK + (size_t)row * 16;
+#pragma unroll
+    for (int gg = 0; gg < S::NGP; ++gg) {
+      const float4 p4 = *reinterpret_cast<const float4*>(pv + (size_t)gg * TR * 16);
+      const float pl[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+      for (int l4 = 0; l4 < 4; ++l4) {
+        const int l = gg * 4 + l4;
+        if (l < NPHI) {
+          float x[RT];
+          ld_rp<RT>(xs + l * RP, x);
+#pragma unroll
+          for (int r = 0; r < RT; ++r) u[r] = fmaf(pl[l4], x[r], u[r]);
+        }
+      }
+    }
+  }
 #pragma unroll
   for (int r = 0; r < RT; ++r) {
     const float al = c.alpha[h0 + r], be = c.beta[h0 + r];
     pp[r] = fmaf(be, pp[r], ro[r]);
     so[r] = fmaf(be, so[r], wo[r] - c.muw[h0 + r]);
     dd[r] = fmaf(al, pp[r], dd[r]);
-    acc[0][r] = fmaf(rr[r], rr[r], acc[0][r]);
-    acc[1][r] = fmaf(q[r], rr[r], acc[1][r]);
-    acc[2][r] += q[r];
-    acc[3][r] += rr[r];
+    if constexpr (PRE) {
+      acc[0][r] = fmaf(rr[r], u[r], acc[0][r]);
+      acc[1][r] = fmaf(q[r], u[r], acc[1][r]);
+      acc[2][r] += q[r];
+      acc[3][r] += u[r];
+      acc[4][r] = fmaf(rr[r], rr[r], acc[4][r]);
+      acc[5][r] += rr[r];
+    } else {
+      acc[0][r] = fmaf(rr[r], rr[r], acc[0][r]);
+      acc[1][r] = fmaf(q[r], rr[r], acc[1][r]);
+      acc[2][r] += q[r];
+      acc[3][r] += rr[r];
+    }
   }
   const int64_t L = (int64_t)d.ne * BL;
   const int64_t idx = (int64_t)(tri0 + lt) * BL + (int64_t)k * RP + h0;
@@ -511,23 +558,25 @@ __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, i
   st_rp<RT>(fv + (2 + nx) * L + idx, rr);
   st_rp<RT>(fv + (4 + nx) * L + idx, q);
   st_rp<RT>(fv + (6 + nx) * L + idx, so);
+  if constexpr (PRE) st_rp<RT>(fv + 8 * L + idx, u);
 }
 
-// Runtime tile geometry of a slot (producers).
+// Runtime tile geometry of a slot (producers; the offsets of EStage).
 struct EGeom {
-  int nphi, tt, tr, ng, bl, gather, own, area;
+  int nphi, tt, tr, ng, ngp, bl, gather, own, area;
 };
 template <typename T>
-__device__ __forceinline__ EGeom e_geom(int p, int rp) {
+__device__ __forceinline__ EGeom e_geom(int p, int rp, int pre) {
   EGeom g;
   g.nphi = e_nphi(p);
   g.tt = e_tt(g.nphi);
   g.tr = g.tt * g.nphi;
   g.ng = (4 * g.nphi + Pack<T>::VEC - 1) / Pack<T>::VEC;
+  g.ngp = e_ngp(g.nphi, pre != 0);
   g.bl = e_block_len(g.nphi, rp);
-  g.gather = g.ng * g.tr * 16;
+  g.gather = (g.ng + g.ngp) * g.tr * 16;
   g.own = g.gather + 3 * 4 * g.tt * g.bl * 4;
-  g.area = g.own + 2 * g.tt * g.bl * 4;
+  g.area = g.own + (pre ? 3 : 2) * g.tt * g.bl * 4;
   return g;
 }
 
@@ -633,13 +682,19 @@ __device__ __noinline__ void slot_transition(const EngineParams& E, int sid, con
     case PH_CG0:
     case PH_CG: {
       if (mine && vq->inner) {
-        const float g = (float)t[4 * lane];
-        const double mu = mz ? t[4 * lane + 2] / n : 0.0;
-        const float dw = (float)(t[4 * lane + 1] - mu * t[4 * lane + 3]);
+        // sums per right-hand side: (r.r, w.r, sum w, sum r), preconditioned
+        // (r.u, w.u, sum w, sum u, r.r, sum r)
+        const int ns = d.precond ? 6 : 4;
+        const double* tr = t + ns * lane;
+        const double mu = mz ? tr[2] / n : 0.0;
+        const double mu_u = d.precond && mz ? tr[3] / n : 0.0;
+        const float g = (float)(d.precond ? tr[0] - mu_u * tr[5] : tr[0]);
+        const float dw = (float)(tr[1] - mu * tr[3]);
+        const double rr = d.precond ? tr[4] : tr[0];
         float an, bn;
         int iters = vq->iters;
         if (ph == PH_CG0) {
-          q->stop = vq->stop * t[4 * lane];
+          q->stop = vq->stop * rr;
           bn = 0.f;
           an = g / dw;
         } else {
@@ -648,15 +703,17 @@ __device__ __noinline__ void slot_transition(const EngineParams& E, int sid, con
           an = g / (dw - bn * g / vq->a_old);
         }
         q->iters = iters;
-        if (!(t[4 * lane] > vq->stop) || iters >= d.max_iters || !(an > 0.f) || !isfinite(an)) {
+        if (!(rr > vq->stop) || iters >= d.max_iters || !(an > 0.f) || !isfinite(an)) {
           q->inner = 0;  // frozen: alpha = beta = 0 leaves d and r as they are
           q->alpha = 0.f;
           q->beta = 0.f;
           q->muw = 0.f;
+          q->muu = 0.f;
         } else {
           q->alpha = an;
           q->beta = bn;
           q->muw = (float)mu;
+          q->muu = (float)mu_u;
           q->g_old = g;
           q->a_old = an;
         }
@@ -791,7 +848,7 @@ __device__ __noinline__ void engine_hook(const EngineParams& E) {
       const int sid = __ldcg(E.act_slot + k);
       const int ph = __ldcg(&E.state[sid].phase);
       if (ph == PH_CG0 || ph == PH_CG) {
-        const EGeom g = e_geom<T>(__ldcg(&E.slots[sid].p), __ldcg(&E.slots[sid].rp));
+        const EGeom g = e_geom<T>(__ldcg(&E.slots[sid].p), __ldcg(&E.slots[sid].rp), __ldcg(&E.slots[sid].precond));
         mx = max(mx, g.area + (g.tt * 8 + 15) / 16 * 16);
       }
     }
@@ -877,7 +934,8 @@ __device__ void coupling_pass(const EngineParams& E, int n_act, int cb, int ce, 
     const int p = __ldcg(&dp->p), ne = __ldcg(&dp->ne), ct = __ldcg(&dp->chunk_tris);
     const int64_t n = __ldcg(&dp->n);
     const T* vals = static_cast<const T*>(*((const void* const volatile*)&dp->Kin));
-    const EGeom g = e_geom<T>(p, 1);
+    const float* pin = *((const float* const volatile*)&dp->Pin);
+    const EGeom g = e_geom<T>(p, 1, __ldcg(&dp->precond));
     const int t0 = (cidx - w.chunk0) * ct, t1 = min(ne, t0 + ct);
     for (int tri0 = t0; tri0 < t1; tri0 += g.tt, ++gt) {
       const int s = (int)(gt % ring.S);
@@ -890,9 +948,12 @@ __device__ void coupling_pass(const EngineParams& E, int n_act, int cb, int ce, 
       const uint32_t bytes = (uint32_t)(nt * g.nphi * 16);
       unsigned char* dst = ring.base + (size_t)s * ring.SB;
       fence_proxy_async_smem();
-      mbar_expect_tx(&full[s], bytes * g.ng);
+      mbar_expect_tx(&full[s], bytes * (g.ng + g.ngp));
       for (int c = 0; c < g.ng; ++c)
         bulk_g2s_hint(dst + (size_t)c * g.tr * 16, vals + ((size_t)c * n + (size_t)tri0 * g.nphi) * Pack<T>::VEC, bytes,
+                      &full[s], pol);
+      for (int c = 0; c < g.ngp; ++c)  // rows of P (preconditioned slots)
+        bulk_g2s_hint(dst + (size_t)(g.ng + c) * g.tr * 16, pin + ((size_t)c * n + (size_t)tri0 * g.nphi) * 4, bytes,
                       &full[s], pol);
     }
   }
@@ -920,8 +981,9 @@ __device__ void gather_pass(const EngineParams& E, int n_act, int cb, int ce, in
     const int32_t* cols = *((const int32_t* const volatile*)&dp->cols);
     const double* area = *((const double* const volatile*)&dp->area);
     float* fvec = *((float* const volatile*)&dp->fvec);
-    const bool mass = __ldcg(&dp->coefM) != 0.0;
-    const EGeom g = e_geom<T>(p, rp);
+    const int pre = __ldcg(&dp->precond);
+    const bool mass = !pre && __ldcg(&dp->coefM) != 0.0;  // (A P holds the mass term)
+    const EGeom g = e_geom<T>(p, rp, pre);
     const int64_t L = (int64_t)ne * g.bl;
     const float* ro = fvec + (2 + cur) * L;
     const float* wo = fvec + (4 + cur) * L;
@@ -965,10 +1027,11 @@ __device__ void gather_pass(const EngineParams& E, int n_act, int cb, int ce, in
           ++b;
         }
       }
-      const int per = nt * cpb;  // chunks of one own vector
-      for (int q = lane; q < 2 * per; q += 32) {
-        const int v = q >= per ? 1 : 0, cx = q - v * per;
-        e_cp16(st + g.own + ((size_t)v * g.tt * g.bl + 4 * cx) * 4, fvec + v * L + (int64_t)tri0 * g.bl + 4 * cx);
+      const int per = nt * cpb;  // chunks of one own vector: d, p (and u, vector 8)
+      for (int q = lane; q < (pre ? 3 : 2) * per; q += 32) {
+        const int v = q >= 2 * per ? 2 : q >= per ? 1 : 0, cx = q - v * per;
+        e_cp16(st + g.own + ((size_t)v * g.tt * g.bl + 4 * cx) * 4,
+               fvec + (v == 2 ? 8 : v) * L + (int64_t)tri0 * g.bl + 4 * cx);
       }
       if (mass)
         for (int q = lane; q < (nt + 1) / 2; q += 32) e_cp16(st + g.area + q * 16, area + tri0 + 2 * q);
@@ -978,16 +1041,17 @@ __device__ void gather_pass(const EngineParams& E, int n_act, int cb, int ce, in
 }
 
 // Consumers: the CG tiles of one chunk (RP right-hand sides), partial sums of
-// the chunk into sums[4 r + j].
-template <int NPHI, typename T, int RP>
+// the chunk into sums[NA r + j] (NA = 4, or 6 preconditioned).
+template <int NPHI, typename T, int RP, bool PRE>
 __device__ __forceinline__ bool cg_chunk(const BSlotDesc& d, const ChunkCtx& c, int t0, int t1, const ERing& ring,
                                          uint64_t* full, uint64_t* gfull, uint64_t* empty, unsigned& gt,
                                          uint64_t timeout_ns, double* sums, double (*s_red)[kNV], float* s_rn) {
   constexpr int TT = ETile<NPHI, T>::TT;
   constexpr int RT = RhsSplit<RP>::RT;
-  float acc[4][RT];
+  constexpr int NA = PRE ? 6 : 4;
+  float acc[NA][RT];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < NA; ++j)
 #pragma unroll
     for (int r = 0; r < RT; ++r) acc[j][r] = 0.f;
   for (int tri0 = t0; tri0 < t1; tri0 += TT, ++gt) {
@@ -998,31 +1062,31 @@ __device__ __forceinline__ bool cg_chunk(const BSlotDesc& d, const ChunkCtx& c, 
     bool got = mbar_wait_bounded(&full[s], par, timeout_ns);
     got = got && mbar_wait_bounded(&gfull[s], par, timeout_ns);
     float* rn = s_rn + (gt & 1u) * kRnMax;
-    cg_combine<NPHI, T, RP>(c, nt, st, rn);
+    cg_combine<NPHI, T, RP, PRE>(c, nt, st, rn);
     if (!ecbar_and(got)) return false;  // also: the combined tile is complete
-    cg_rows<NPHI, T, RP>(d, c, tri0, nt, st, rn, acc);
+    cg_rows<NPHI, T, RP, PRE>(d, c, tri0, nt, st, rn, acc);
     __syncwarp();
     if ((threadIdx.x & 31) == 0) e_mbar_arrive(&empty[s]);  // this warp is done with the stage
   }
   // each right-hand side's sums come from one half of the consumer threads; the
   // other half adds exact zeros, so the reduction matches a one-RHS slot's
   const int half = threadIdx.x / kERows;
-  float v[4 * RP];
+  float v[NA * RP];
 #pragma unroll
   for (int r = 0; r < RP; ++r)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < NA; ++j) {
       float a = 0.f;
       if (r < RT) {
         if (half == 0) a = acc[j][r];
       } else {
         if (half == 1) a = acc[j][r - RT];
       }
-      v[4 * r + j] = a;
+      v[NA * r + j] = a;
     }
   if ((int)threadIdx.x < kNV) sums[threadIdx.x] = 0.0;
   ecbar();
-  e_reduce<4 * RP, float>(v, sums, s_red);
+  e_reduce<NA * RP, float>(v, sums, s_red);
   return true;
 }
 
@@ -1031,12 +1095,22 @@ __device__ __forceinline__ bool chunk_work(const BSlotDesc& d, const ChunkCtx& c
                                            uint64_t* full, uint64_t* gfull, uint64_t* empty, unsigned& gt,
                                            uint64_t timeout_ns, double* sums, double (*s_red)[kNV], float* s_rn) {
   if (is_cg(c.phase)) {
-    switch (c.rp) {
-      case 1: return cg_chunk<NPHI, T, 1>(d, c, t0, t1, ring, full, gfull, empty, gt, timeout_ns, sums, s_red, s_rn);
-      case 2: return cg_chunk<NPHI, T, 2>(d, c, t0, t1, ring, full, gfull, empty, gt, timeout_ns, sums, s_red, s_rn);
-      case 4: return cg_chunk<NPHI, T, 4>(d, c, t0, t1, ring, full, gfull, empty, gt, timeout_ns, sums, s_red, s_rn);
-      default: return cg_chunk<NPHI, T, 8>(d, c, t0, t1, ring, full, gfull, empty, gt, timeout_ns, sums, s_red, s_rn);
+#define DGSL_E_CG(RP, PRE) cg_chunk<NPHI, T, RP, PRE>(d, c, t0, t1, ring, full, gfull, empty, gt, timeout_ns, sums, s_red, s_rn)
+    if (d.precond) {
+      switch (c.rp) {
+        case 1: return DGSL_E_CG(1, true);
+        case 2: return DGSL_E_CG(2, true);
+        case 4: return DGSL_E_CG(4, true);
+        default: return DGSL_E_CG(8, true);
+      }
     }
+    switch (c.rp) {
+      case 1: return DGSL_E_CG(1, false);
+      case 2: return DGSL_E_CG(2, false);
+      case 4: return DGSL_E_CG(4, false);
+      default: return DGSL_E_CG(8, false);
+    }
+#undef DGSL_E_CG
   }
   stream_chunk<NPHI>(d, c, t0, t1, sums, s_red);
   return true;
@@ -1073,16 +1147,19 @@ __device__ bool consumer_pass(const EngineParams& E, int n_act, int cb, int ce, 
     ecbar();
     pend = 0;
     if (s_last) {
-      const int v = threadIdx.x & 31, grp = threadIdx.x >> 5;
-      double a = 0.0;
-      for (int ch = grp; ch < d.nchunk; ch += kECWarps) a += __ldcg(d.part + (size_t)ch * kNV + v);
-      s_red[grp][v] = a;
-      ecbar();
-      if (threadIdx.x < 32) {
-        double t = s_red[0][v];
-        for (int q = 1; q < kECWarps; ++q) t += s_red[q][v];
-        s_tot[v] = t;
+      const int grp = threadIdx.x >> 5;
+      for (int v = threadIdx.x & 31; v < kNV; v += 32) {
+        double a = 0.0;
+        for (int ch = grp; ch < d.nchunk; ch += kECWarps) a += __ldcg(d.part + (size_t)ch * kNV + v);
+        s_red[grp][v] = a;
       }
+      ecbar();
+      if (threadIdx.x < 32)
+        for (int v = threadIdx.x; v < kNV; v += 32) {
+          double t = s_red[0][v];
+          for (int q = 1; q < kECWarps; ++q) t += s_red[q][v];
+          s_tot[v] = t;
+        }
       ecbar();
       if (threadIdx.x < 32) slot_transition(E, cur_sid, d, s_tot);
       ecbar();
@@ -1224,13 +1301,14 @@ int engine_shared_admitted(const void* sh_host_copy) {
   return static_cast<const EngineShared*>(sh_host_copy)->admitted;
 }
 
-size_t engine_workspace_bytes(int p, int ne, int nrhs) {
+size_t engine_workspace_bytes(int p, int ne, int nrhs, int precond) {
   const int nphi = e_nphi(p);
   const int64_t n = (int64_t)ne * nphi;
   const int bl = e_block_len(nphi, e_rp(nrhs));
   const int nchunk = (ne + engine_chunk_tris(p, ne) - 1) / engine_chunk_tris(p, ne);
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  return a256(8 * (size_t)n * nrhs) + a256(4 * 8 * (size_t)ne * bl) + a256(8 * (size_t)kNV * nchunk);
+  return a256(8 * (size_t)n * nrhs) + a256(4 * (precond ? 9 : 8) * (size_t)ne * bl) +
+         a256(8 * (size_t)kNV * nchunk);
 }
 
 void engine_fill_workspace(BSlotDesc& s, char* ws) {
@@ -1243,7 +1321,7 @@ void engine_fill_workspace(BSlotDesc& s, char* ws) {
   s.r64 = reinterpret_cast<double*>(ws);
   ws += a256(8 * (size_t)s.n * s.nrhs);
   s.fvec = reinterpret_cast<float*>(ws);
-  ws += a256(4 * 8 * (size_t)s.ne * s.bl);
+  ws += a256(4 * (s.precond ? 9 : 8) * (size_t)s.ne * s.bl);
   s.part = reinterpret_cast<double*>(ws);
 }
 

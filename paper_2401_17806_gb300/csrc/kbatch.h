@@ -9,19 +9,23 @@ namespace dgsl {
 constexpr int kMaxSlots = 4096;       // slots per engine (admitted over its lifetime)
 constexpr int kMaxRhs = 8;            // right-hand sides per slot
 constexpr int kMaxCtas = 2048;        // CTAs of an engine launch (152 SMs x at most 8)
+constexpr int kEngineSums = 6 * kMaxRhs;  // partial sums per chunk (up to 6 per right-hand side)
 
 // One request (1..kMaxRhs right-hand sides of one operator), written by the
 // host and copied into device memory when the engine admits it.  All pointers
 // are device pointers (the inbox itself is mapped host memory).  b, x and r64
 // are [nrhs][n] doubles in the operator's order; fvec holds 8 FP32 vectors
 // d | p | r0 | r1 | w0 | w1 | s0 | s1 of ne blocks of bl floats (per triangle
-// N_phi x rp values, right-hand side innermost); part holds 32 doubles per chunk.
+// N_phi x rp values, right-hand side innermost), 9 with the block-Jacobi
+// preconditioner (u last); part holds kEngineSums doubles per chunk.
 struct BSlotDesc {
   int p, ne, ne_pad, mean_zero;
   long long n;
-  int nrhs, rp, bl, pad0;
+  int nrhs, rp, bl, precond;  // precond: block-Jacobi preconditioned inner CG
   const double* K64;        // FP64 couplings (refinement residual)
-  const void* Kin;          // inner couplings, float or bf16 bits (engine type)
+  const void* Kin;          // inner couplings, float or bf16 bits (engine type); with
+                            // precond those of A P (coefK and the mass term folded in)
+  const float* Pin;         // precond: P, FP32, layout of launch_build_precond
   const int32_t* cols;
   const double* area;
   const double* Mref;
@@ -83,8 +87,8 @@ struct EngineParams {
 int engine_chunk_tris(int p, int ne);
 // Device workspace of one request (r64 | fvec | partials) and the descriptor
 // fields that point into it (also sets rp, bl, chunk_tris, nchunk from p, ne,
-// n and nrhs).
-size_t engine_workspace_bytes(int p, int ne, int nrhs);
+// n, nrhs and precond).
+size_t engine_workspace_bytes(int p, int ne, int nrhs, int precond);
 void engine_fill_workspace(BSlotDesc& s, char* ws);
 // Device bytes of the engine-owned areas (slot copies, state, shared words,
 // lists) and their layout inside one allocation of that size.

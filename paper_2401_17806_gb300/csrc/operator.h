@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -66,8 +68,10 @@ struct dgsl_operator {
     CGResult* h_res = nullptr;  // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int max_parts = 0;
-    // block-Jacobi preconditioned operators (A P and P) of the last few
-    // systems (coefficients and coupling type), least recently used replaced first
+    // block-Jacobi preconditioned operators (A P and P) of recent systems
+    // (coefficients and coupling type): up to kKeep kept; an entry in use by a
+    // solve, a batch or an admitted server request (refs > 0) is never
+    // rebuilt; otherwise the least recently used is replaced first
     struct Precond {
       dgsl::PrecondOp op;
       void* ap = nullptr;
@@ -77,7 +81,10 @@ struct dgsl_operator {
       int type = 0;
       uint64_t used = 0;
       bool valid = false;
-    } pj[4];
+      std::atomic<int> refs{0};
+    };
+    static constexpr size_t kKeep = 4;
+    std::vector<std::unique_ptr<Precond>> pj;
     uint64_t pj_clock = 0;
     double* p64 = nullptr;  // FP64 P while building (FP32 / BF16 systems)
     int* pj_bad = nullptr;
@@ -131,17 +138,25 @@ struct dgsl_operator {
   }
   // Block-Jacobi preconditioned operator for A = coefM Mbar + coefK K with
   // couplings of type 0 (FP32), 1 (FP64) or 2 (BF16), built on stream s unless
-  // kept from an earlier solve; call after ensure_work.
-  const dgsl::PrecondOp* precond(double coefK, double coefM, int type, cudaStream_t s) {
+  // kept from an earlier solve, and held (refs + 1) until release_precond.
+  // The caller holds mu and has called ensure_work.
+  Work::Precond* acquire_precond(double coefK, double coefM, int type, cudaStream_t s) {
     ++w.pj_clock;
-    Work::Precond* slot = nullptr;
-    for (auto& c : w.pj)
-      if (c.valid && c.coefK == coefK && c.coefM == coefM && c.type == type) {
-        c.used = w.pj_clock;
-        return &c.op;
+    for (auto& e : w.pj)
+      if (e->valid && e->coefK == coefK && e->coefM == coefM && e->type == type) {
+        e->used = w.pj_clock;
+        e->refs.fetch_add(1);
+        return e.get();
       }
-    for (auto& c : w.pj)
-      if (!slot || (!c.valid && slot->valid) || (c.valid == slot->valid && c.used < slot->used)) slot = &c;
+    Work::Precond* slot = nullptr;
+    if (w.pj.size() >= Work::kKeep)
+      for (auto& e : w.pj)
+        if (e->refs.load() == 0 && (!slot || (!e->valid && slot->valid) || (e->valid == slot->valid && e->used < slot->used)))
+          slot = e.get();
+    if (!slot) {
+      w.pj.push_back(std::make_unique<Work::Precond>());
+      slot = w.pj.back().get();
+    }
     Work::Precond& c = *slot;
     c.valid = false;
     // (a buffer too small for a new type is replaced; the old one stays allocated until destroy)
@@ -172,7 +187,12 @@ struct dgsl_operator {
     c.type = type;
     c.used = w.pj_clock;
     c.valid = true;
-    return &c.op;
+    c.refs.fetch_add(1);
+    return &c;
+  }
+  // Ends a hold taken by acquire_precond (any thread; no lock needed).
+  static void release_precond(Work::Precond* c) {
+    if (c) c->refs.fetch_sub(1);
   }
 };
 

@@ -71,8 +71,20 @@ int request_nrhs(const dgsl_request& r) { return r.n_rhs < 1 ? 1 : r.n_rhs; }
 
 // Device workspace of one request (engine_workspace_bytes: FP64 residuals,
 // padded FP32 CG vectors, per-chunk partial sums).
-size_t request_workspace(const dgsl_operator* op, int nrhs) {
-  return align256(engine_workspace_bytes(op->d.p, op->d.ne, nrhs));
+size_t request_workspace(const dgsl_operator* op, int nrhs, int precond) {
+  return align256(engine_workspace_bytes(op->d.p, op->d.ne, nrhs, precond));
+}
+
+int precond_type(const dgsl_engine_opts& o) { return o.precision == DGSL_PREC_BF16_IR ? 2 : 0; }
+double request_coefK(const dgsl_request& r) { return r.kind == DGSL_SCHUR ? r.coef * r.coef : r.coef; }
+double request_coefM(const dgsl_request& r) { return r.kind == DGSL_SCHUR ? 0.0 : 1.0; }
+
+// Preconditioned operator of a request's system, held until released (builds
+// it on stream s if the operator does not keep it).
+dgsl_operator::Work::Precond* hold_precond(const dgsl_request& r, const dgsl_engine_opts& o, cudaStream_t s) {
+  dgsl_operator* op = const_cast<dgsl_operator*>(r.op);
+  std::lock_guard<std::mutex> lock(op->mu);
+  return op->acquire_precond(request_coefK(r), request_coefM(r), precond_type(o), s);
 }
 
 int check_request(const dgsl_request& r, const dgsl_engine_opts& o, std::string& why) {
@@ -89,7 +101,18 @@ int check_request(const dgsl_request& r, const dgsl_engine_opts& o, std::string&
   return DGSL_OK;
 }
 
-BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, uint64_t ticket) {
+int check_engine_opts(const dgsl_engine_opts& o, std::string& why) {
+  if (o.precision != DGSL_PREC_F32_IR && o.precision != DGSL_PREC_BF16_IR)
+    return why = "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR", DGSL_EINVAL;
+  if (!(o.inner_tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return why = "bad engine options", DGSL_EINVAL;
+  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
+    return why = "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI", DGSL_EINVAL;
+  return DGSL_OK;
+}
+
+// held: the request's preconditioned operator (precond), else nullptr.
+BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, uint64_t ticket,
+                    const dgsl_operator::Work::Precond* held) {
   const DevOp& d = r.op->d;
   BSlotDesc s{};
   s.p = d.p;
@@ -103,8 +126,13 @@ BSlotDesc fill_desc(const dgsl_request& r, const dgsl_engine_opts& o, char* ws, 
   s.cols = d.cols;
   s.area = d.area;
   s.Mref = d.Mref;
-  s.coefK = r.kind == DGSL_SCHUR ? r.coef * r.coef : r.coef;
-  s.coefM = r.kind == DGSL_SCHUR ? 0.0 : 1.0;
+  s.coefK = request_coefK(r);
+  s.coefM = request_coefM(r);
+  if (held) {
+    s.precond = 1;
+    s.Kin = held->op.ap;
+    s.Pin = static_cast<const float*>(held->op.pinv);
+  }
   s.b = r.b;
   s.x = r.x;
   s.tol = r.tol > 0.0 ? r.tol : 1e-10;
@@ -141,6 +169,8 @@ extern "C" void dgsl_default_engine_opts(dgsl_engine_opts* o) {
   o->device = 0;
   o->hbm_budget_bytes = 150000000000LL;
   o->idle_us = 500;
+  o->precond = DGSL_PRECOND_NONE;
+  o->pad = 0;
 }
 
 extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_engine_opts* opts,
@@ -151,10 +181,8 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
   if (opts) o = *opts;
   try {
     if (!reqs || n < 1 || n > kMaxSlots) throw Error(DGSL_EINVAL, "need 1..4096 requests");
-    if (o.precision != DGSL_PREC_F32_IR && o.precision != DGSL_PREC_BF16_IR)
-      throw Error(DGSL_EINVAL, "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR");
-    if (!(o.inner_tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) throw Error(DGSL_EINVAL, "bad engine options");
     std::string why;
+    if (int e = check_engine_opts(o, why)) throw Error(e, why);
     for (int i = 0; i < n; ++i)
       if (int e = check_request(reqs[i], o, why)) throw Error(e, "request " + std::to_string(i) + ": " + why);
     std::lock_guard<std::mutex> lock(g_batch_mu);
@@ -164,21 +192,31 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
       R = std::make_unique<EngineRes>();
       R->init(o.device);
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // preconditioned operators, held for the whole call
+    std::vector<dgsl_operator::Work::Precond*> held(n, nullptr);
+    struct Release {
+      std::vector<dgsl_operator::Work::Precond*>& h;
+      ~Release() {
+        for (auto* c : h) dgsl_operator::release_precond(c);
+      }
+    } release{held};
+    if (o.precond)
+      for (int i = 0; i < n; ++i) held[i] = hold_precond(reqs[i], o, s);
     std::vector<size_t> off(n);
     size_t total = 0;
     for (int i = 0; i < n; ++i) {
       off[i] = total;
-      total += request_workspace(reqs[i].op, request_nrhs(reqs[i]));
+      total += request_workspace(reqs[i].op, request_nrhs(reqs[i]), o.precond);
     }
     char* ws = nullptr;
     if (cudaMalloc(&ws, total) != cudaSuccess) throw Error(DGSL_ENOMEM, "batch workspace allocation failed");
     std::unique_ptr<char, void (*)(char*)> guard(ws, [](char* q) { cudaFree(q); });
-    for (int i = 0; i < n; ++i) R->inbox_h->slots[i] = fill_desc(reqs[i], o, ws + off[i], (uint64_t)i);
+    for (int i = 0; i < n; ++i) R->inbox_h->slots[i] = fill_desc(reqs[i], o, ws + off[i], (uint64_t)i, held[i]);
     std::memset(R->done_h, 0, sizeof(BCompletion) * kMaxSlots);
     R->inbox_h->stop = 1;
     std::atomic_thread_fence(std::memory_order_release);
     R->inbox_h->count = n;
-    cudaStream_t s = (cudaStream_t)stream;
     int grid = 0;
     DGSL_CUDA(R->launch(o.precision == DGSL_PREC_BF16_IR, 0, s, &grid));
     DGSL_CUDA(cudaStreamSynchronize(s));
@@ -263,7 +301,16 @@ struct Request {
   int state = RQ_QUEUED;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  dgsl_operator::Work::Precond* held = nullptr;  // preconditioned operator while admitted
   dgsl_solve_info info{};
+};
+
+// Operators of the requests in flight: how many, and the device bytes charged
+// to the budget for each (its size when first admitted, plus any growth from
+// preconditioned operators built for later requests).
+struct OpRef {
+  int count = 0;
+  int64_t charged = 0;
 };
 
 }  // namespace
@@ -272,6 +319,7 @@ struct dgsl_server {
   dgsl_engine_opts o{};
   EngineRes R;
   cudaStream_t stream = nullptr;
+  cudaStream_t build_stream = nullptr;  // preconditioned operators are built here
   cudaEvent_t exited = nullptr;
   Arena arena;
   std::mutex mu;
@@ -281,7 +329,7 @@ struct dgsl_server {
   uint64_t next_ticket = 1;
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> queue;
-  std::unordered_map<const dgsl_operator*, int> op_refs;  // operators of requests in flight
+  std::unordered_map<const dgsl_operator*, OpRef> op_refs;  // operators of requests in flight
   int64_t bytes_in_use = 0;
   bool running = false;
   int published = 0;                      // slots published to the current launch
@@ -289,15 +337,29 @@ struct dgsl_server {
   std::vector<char> collected;            // [kMaxSlots]
   int64_t submitted = 0, completed = 0, launches = 0;
 
-  int64_t op_cost(const dgsl_operator* op) const { return op_refs.count(op) ? 0 : op->device_bytes; }
+  // Device bytes of op not yet charged to the budget.
+  int64_t op_cost(const dgsl_operator* op) const {
+    auto it = op_refs.find(op);
+    return op->device_bytes - (it == op_refs.end() ? 0 : it->second.charged);
+  }
 
-  void finish(Request& q) {
+  // Gives back a request's workspace, its hold on the preconditioned operator
+  // and its reference to the operator.
+  void unadmit(Request& q) {
     arena.release(q.ws, q.ws_bytes);
     bytes_in_use -= (int64_t)q.ws_bytes;
-    if (--op_refs[q.r.op] == 0) {
-      bytes_in_use -= q.r.op->device_bytes;
+    dgsl_operator::release_precond(q.held);
+    q.held = nullptr;
+    q.ws = nullptr;
+    OpRef& ref = op_refs[q.r.op];
+    if (--ref.count == 0) {
+      bytes_in_use -= ref.charged;
       op_refs.erase(q.r.op);
     }
+  }
+
+  void finish(Request& q) {
+    unadmit(q);
     q.state = RQ_DONE;
     ++completed;
   }
@@ -314,13 +376,7 @@ struct dgsl_server {
       collect();
       for (int i = published - 1; i >= admitted; --i) {
         Request& q = reqs[slot_ticket[i]];
-        arena.release(q.ws, q.ws_bytes);
-        bytes_in_use -= (int64_t)q.ws_bytes;
-        if (--op_refs[q.r.op] == 0) {
-          bytes_in_use -= q.r.op->device_bytes;
-          op_refs.erase(q.r.op);
-        }
-        q.ws = nullptr;
+        unadmit(q);
         q.state = RQ_QUEUED;
         queue.push_front(q.ticket);
       }
@@ -336,15 +392,31 @@ struct dgsl_server {
     int added = 0;
     while (!queue.empty() && published < kMaxSlots) {
       Request& q = reqs[queue.front()];
-      const int64_t need = (int64_t)q.ws_bytes + op_cost(q.r.op);
-      if (bytes_in_use + need > o.hbm_budget_bytes) break;
+      if (o.precond && !q.held) {
+        // the operator grows by the preconditioned system the first time
+        try {
+          q.held = hold_precond(q.r, o, build_stream);
+        } catch (const Error& e) {
+          q.info = dgsl_solve_info{};
+          q.info.status = e.code;
+          q.state = RQ_DONE;
+          ++completed;
+          queue.pop_front();
+          continue;
+        }
+      }
+      const int64_t opc = op_cost(q.r.op);
+      const int64_t need = (int64_t)q.ws_bytes + opc;
+      if (bytes_in_use + need > o.hbm_budget_bytes) break;  // (keeps its hold until admitted)
       char* ws = arena.alloc(q.ws_bytes);
       if (!ws) break;
       q.ws = ws;
       bytes_in_use += need;
-      ++op_refs[q.r.op];
+      OpRef& ref = op_refs[q.r.op];
+      ++ref.count;
+      ref.charged += opc;
       q.state = RQ_ADMITTED;
-      R.inbox_h->slots[published] = fill_desc(q.r, o, ws, q.ticket);
+      R.inbox_h->slots[published] = fill_desc(q.r, o, ws, q.ticket, q.held);
       slot_ticket[published] = q.ticket;
       ++published;
       ++added;
@@ -396,11 +468,12 @@ extern "C" int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** ou
     dgsl_default_engine_opts(&s->o);
     if (opts) s->o = *opts;
     if (s->o.hbm_budget_bytes <= 0) s->o.hbm_budget_bytes = 150000000000LL;
-    if (s->o.precision != DGSL_PREC_F32_IR && s->o.precision != DGSL_PREC_BF16_IR)
-      throw Error(DGSL_EINVAL, "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR");
+    std::string why;
+    if (int e = check_engine_opts(s->o, why)) throw Error(e, why);
     if (s->o.idle_us < 0 || s->o.idle_us > 1000000) throw Error(DGSL_EINVAL, "idle_us must be in [0, 1e6]");
     s->R.init(s->o.device);
     DGSL_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    DGSL_CUDA(cudaStreamCreateWithFlags(&s->build_stream, cudaStreamNonBlocking));
     DGSL_CUDA(cudaEventCreateWithFlags(&s->exited, cudaEventDisableTiming));
     // workspace arena: the budget minus nothing (operators are owned by the
     // caller), capped by the memory free on the device
@@ -428,8 +501,13 @@ extern "C" int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* 
   if (int e = check_request(*req, srv->o, why)) return dgsl_set_last_error(why), e;
   Request q;
   q.r = *req;
-  q.ws_bytes = request_workspace(req->op, request_nrhs(*req));
-  if ((int64_t)q.ws_bytes + req->op->device_bytes > srv->o.hbm_budget_bytes ||
+  q.ws_bytes = request_workspace(req->op, request_nrhs(*req), srv->o.precond);
+  // with the preconditioner the operator may grow by A P, P and an FP64 P
+  const int64_t pre_bytes =
+      srv->o.precond ? (int64_t)(precond_ap_bytes(req->op->d, precond_type(srv->o)) +
+                                 precond_pinv_bytes(req->op->d, precond_type(srv->o)) + precond_pinv_bytes(req->op->d, 1))
+                     : 0;
+  if ((int64_t)q.ws_bytes + req->op->device_bytes + pre_bytes > srv->o.hbm_budget_bytes ||
       q.ws_bytes > srv->arena.bytes)
     return dgsl_set_last_error("request can never fit the memory budget"), DGSL_EBUDGET;
   {
@@ -484,6 +562,7 @@ extern "C" int dgsl_cancel(dgsl_server* srv, uint64_t ticket) {
   auto it = srv->reqs.find(ticket);
   if (it == srv->reqs.end()) return dgsl_set_last_error("unknown ticket"), DGSL_EINVAL;
   if (it->second.state != RQ_QUEUED) return DGSL_EPENDING;
+  dgsl_operator::release_precond(it->second.held);  // (a queued request may hold one)
   for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
     if (*q == ticket) {
       srv->queue.erase(q);
@@ -517,7 +596,9 @@ extern "C" void dgsl_server_destroy(dgsl_server* srv) {
   cudaSetDevice(srv->o.device);
   cudaStreamSynchronize(srv->stream);
   cudaFree(srv->arena.base);
+  for (auto& kv : srv->reqs) dgsl_operator::release_precond(kv.second.held);
   cudaEventDestroy(srv->exited);
   cudaStreamDestroy(srv->stream);
+  cudaStreamDestroy(srv->build_stream);
   delete srv;
 }

@@ -79,7 +79,7 @@ class dgsl_request(C.Structure):
 class dgsl_engine_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iters", C.c_int32), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("device", C.c_int32), ("hbm_budget_bytes", C.c_int64),
-                ("idle_us", C.c_int64)]
+                ("idle_us", C.c_int64), ("precond", C.c_int32), ("pad", C.c_int32)]
 
 
 class dgsl_server_stats(C.Structure):
