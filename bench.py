@@ -64,7 +64,7 @@ def parse_args(argv=None):
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
     ap.add_argument("--cg-iters", type=int, default=200)
     ap.add_argument("--precond", action="store_true",
-                    help="cg workload: block-Jacobi preconditioned CG")
+                    help="cg, batch and serve workloads: block-Jacobi preconditioned CG")
     ap.add_argument("--batch-solves", type=int, default=64)
     ap.add_argument("--batch-nmax", type=int, default=64)
     ap.add_argument("--rhs", type=int, default=8)
@@ -392,9 +392,16 @@ def batch_leg(args):
         n = op.n_dof
         split += [dgsl.request(op, dgsl.SCHUR, dt, b[j * n:(j + 1) * n], xs[j * n:(j + 1) * n]) for j in range(R)]
     prec = dgsl.PREC_BF16_IR if args.precision == "bf16" else dgsl.PREC_F32_IR
-    opts = dgsl.engine_opts(precision=prec)
+    pc = dgsl.PRECOND_BLOCK_JACOBI if args.precond else dgsl.PRECOND_NONE
+    opts = dgsl.engine_opts(precision=prec, precond=pc)
     dgsl.dgsl_cg_solve_batch(reqs[:min(2, len(reqs))], opts)   # warm-up
     torch.cuda.synchronize()
+    precond_build_s = 0.0
+    if args.precond:  # build every preconditioned system once (one CG iteration each), outside the timing
+        t = time.perf_counter()
+        dgsl.dgsl_cg_solve_batch(reqs, dgsl.engine_opts(precision=prec, precond=pc, max_iters=1, max_refine=1))
+        torch.cuda.synchronize()
+        precond_build_s = time.perf_counter() - t
 
     def timed(rs):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -435,6 +442,8 @@ def batch_leg(args):
         "ms_total": ms, "gpu_launches": launches, "dtype": {"bf16": "bf16+f32+f64"}.get(args.precision, "f32+f64"),
         "config": {"solves": nsol, "rhs_per_solve": R, "N_range": [8, args.batch_nmax], "p_range": [1, 4],
                    "tol": WORKLOAD["tol"], "dt": dt, "operator_build_s": build_s,
+                   "precond": "block-Jacobi" if args.precond else "none",
+                   "precond_build_s": precond_build_s,
                    "sample": f"{nsol} solves x {R} RHS (bounded sample of the 512-solve, N<=256 distribution)"},
         "converged": int(sum(ok)), "requests": len(reqs), "rhs": nrhs_total, "iters_p50": iters[len(iters) // 2],
         "iters_max": iters[-1], "max_relres": max(i.relres for i in infos),
@@ -478,6 +487,12 @@ def serve_leg(args):
         op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=o64, check=False)
         torch.cuda.synchronize()
         svc[key] = time.perf_counter() - t
+    pc = dgsl.PRECOND_BLOCK_JACOBI if args.precond else dgsl.PRECOND_NONE
+    if args.precond:  # every pool operator's preconditioned Schur system, built before the sweep
+        wx = [torch.zeros(op.n_dof, dtype=torch.float64, device="cuda") for op, _ in pool.values()]
+        warm = [dgsl.request(op, dgsl.SCHUR, dt, rhs[:op.n_dof], x) for (op, rhs), x in zip(pool.values(), wx)]
+        dgsl.dgsl_cg_solve_batch(warm, dgsl.engine_opts(precond=pc, max_iters=1, max_refine=1))
+        torch.cuda.synchronize()
     rng = np.random.default_rng(77)
     results = []
     for rate in [float(v) for v in args.serve_rates.split(",")]:
@@ -490,7 +505,7 @@ def serve_leg(args):
         xs = [torch.zeros(int(k) * pool[(int(N), int(p))][0].n_dof, dtype=torch.float64, device="cuda")
               for N, p, k in zip(Nr, pr, kr)]
         torch.cuda.synchronize()
-        srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=40_000_000_000, idle_us=2000))
+        srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=40_000_000_000, idle_us=2000, precond=pc))
         owner, tickets = {}, []
         start = time.perf_counter()
         done_t = np.full(len(arr), np.nan)
@@ -541,6 +556,7 @@ def serve_leg(args):
     print(json.dumps({
         "metric": "served Schur solves/s and p50/p99 latency", "workload": "serve", "data": "synthetic",
         "config": {"N_pool": sizes, "p_range": [1, 4], "rhs_per_request": [1, 8], "tol": WORKLOAD["tol"],
+                   "precond": "block-Jacobi" if args.precond else "none",
                    "seconds_per_rate": args.serve_seconds, "operator_pool_build_s": build_s,
                    "sample": f"N log-uniform in 16..{args.serve_nmax} (bounded sample of 16..1024)"},
         "sweep": results}))

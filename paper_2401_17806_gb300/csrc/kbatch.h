@@ -99,7 +99,9 @@ size_t engine_shared_bytes();
 int engine_shared_status(const void* sh_host_copy);
 int engine_shared_admitted(const void* sh_host_copy);
 // Launches the engine (cooperative) on `s`; `bf16` selects the inner coupling
-// type.  The caller zeroes EngineShared before the launch.
-cudaError_t launch_engine(const EngineParams& e, int bf16, cudaStream_t s, int* grid_used);
+// type, `precond` a kernel that also runs block-Jacobi preconditioned slots
+// (every slot with precond set needs it).  The caller zeroes EngineShared
+// before the launch.
+cudaError_t launch_engine(const EngineParams& e, int bf16, int precond, cudaStream_t s, int* grid_used);
 
 }  // namespace dgsl

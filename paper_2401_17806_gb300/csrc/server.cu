@@ -56,12 +56,12 @@ struct EngineRes {
     P.timeout_ns = 10ull * 1000 * 1000 * 1000;
     P.idle_ns = 0;
   }
-  cudaError_t launch(int bf16, uint64_t idle_ns, cudaStream_t s, int* grid) {
+  cudaError_t launch(int bf16, int precond, uint64_t idle_ns, cudaStream_t s, int* grid) {
     cudaError_t e = cudaMemsetAsync(P.sh, 0, engine_shared_bytes(), s);
     if (e != cudaSuccess) return e;
     EngineParams q = P;
     q.idle_ns = idle_ns;
-    return launch_engine(q, bf16, s, grid);
+    return launch_engine(q, bf16, precond, s, grid);
   }
 };
 
@@ -218,7 +218,7 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
     std::atomic_thread_fence(std::memory_order_release);
     R->inbox_h->count = n;
     int grid = 0;
-    DGSL_CUDA(R->launch(o.precision == DGSL_PREC_BF16_IR, 0, s, &grid));
+    DGSL_CUDA(R->launch(o.precision == DGSL_PREC_BF16_IR, o.precond, 0, s, &grid));
     DGSL_CUDA(cudaStreamSynchronize(s));
     std::vector<char> sh(engine_shared_bytes());
     DGSL_CUDA(cudaMemcpy(sh.data(), R->P.sh, sh.size(), cudaMemcpyDeviceToHost));
@@ -430,7 +430,8 @@ struct dgsl_server {
     // 3. launch when there is published work and no engine
     if (!running && published > 0) {
       int grid = 0;
-      if (R.launch(o.precision == DGSL_PREC_BF16_IR, (uint64_t)o.idle_us * 1000ull, stream, &grid) == cudaSuccess &&
+      if (R.launch(o.precision == DGSL_PREC_BF16_IR, o.precond, (uint64_t)o.idle_us * 1000ull, stream, &grid) ==
+              cudaSuccess &&
           cudaEventRecord(exited, stream) == cudaSuccess) {
         running = true;
         ++launches;
