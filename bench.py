@@ -58,7 +58,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-precond", action="store_true",
                     help="skip the block-Jacobi preconditioned run of the same stage")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg"], default="stage",
+    ap.add_argument("--sl-dt", type=float, default=0.01)
+    ap.add_argument("--sl-reps", type=int, default=100,
+                    help="sl workload: transport calls per timed step")
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl"], default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
@@ -360,6 +363,85 @@ def cg_leg(args):
     kind = "block-Jacobi preconditioned " if args.precond else ""
     print(json.dumps({"workload": f"one {kind}FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
                       "grid": info.grid, "us_per_iter": 1e3 * info.cg_kernel_ms / max(1, info.iters)}))
+
+
+def sl_flops(p, nf):
+    """Algorithmic FP64 operations of the semi-Lagrangian walk (FMA = 2): per
+    cell visited, the reference coordinates (8), the monomials (2p powers,
+    N_phi products), the velocity (4 N_phi), the barycentric rates (6 + 3),
+    the exit tests (9) and the move (8); per trajectory, the start point (8),
+    the final monomials and reference coordinates (2p + N_phi + 8), the fields
+    at the foot (2 N_phi nf) and its share of the projection (2 N_phi nf)."""
+    nphi = (p + 1) * (p + 2) // 2
+    per_visit = 8 + 2 * p + nphi + 4 * nphi + 9 + 9 + 8
+    per_traj = 8 + 2 * p + nphi + 8 + 4 * nphi * nf
+    return per_visit, per_traj
+
+
+def sl_leg(args):
+    """Semi-Lagrangian transport (Sec. 2.5, eq. intstage) on the N x N mesh:
+    the backward characteristic of every Gauss point over dt through the
+    Taylor-Green velocity (nodal interpolation on the main grid), both
+    velocity components transported.  Gauss-point trajectories per second,
+    device-timed, inputs resident; the walk's FP64 operation rate against the
+    GB300 FP64 peak."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    N, p, dt = args.N, args.p, args.sl_dt
+    xy, tri, per = synth.jittered_periodic_mesh(N, WORKLOAD["seed"])
+    op = dgsl.Operator(xy, tri, per, p, store=dgsl.STORE_F64)
+    X = op.node_coords(0)
+    tp = 2.0 * np.pi
+    u = np.sin(tp * X[:, 0]) * np.cos(tp * X[:, 1])
+    v = -np.cos(tp * X[:, 0]) * np.sin(tp * X[:, 1])
+    vbar = torch.tensor(np.concatenate([u, v]), device="cuda")
+    cstar = torch.empty_like(vbar)
+    ng = dgsl.sl_quadrature(p)[1].size
+    nt = op.n_tri * ng
+    steps = torch.zeros(nt, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            op.dgsl_sl_transport(dt, vbar, vbar, cstar, 2, steps=steps, stream=stream)
+    stream.synchronize()
+    visits = float(steps.sum().item()) + nt  # cells visited: crossings + the first
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = dgsl.dgsl_launch_count()
+    calls = args.steps * args.sl_reps
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(calls):
+            op.dgsl_sl_transport(dt, vbar, vbar, cstar, 2, stream=stream)
+        ev1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    launches = dgsl.dgsl_launch_count() - l0
+    ms = ev0.elapsed_time(ev1) / calls
+    pv, pt = sl_flops(p, 2)
+    flops = pv * visits + pt * nt
+    peak = 1250.0  # GFLOP/s: nominal GB300 FP64 (Blackwell Ultra)
+    line = {
+        "metric": "semi-Lagrangian Gauss-point trajectories/s", "workload": "sl", "data": "synthetic",
+        "value": nt / (ms * 1e-3), "unit": "trajectories/s", "ms_per_call": ms, "steps": args.steps,
+        "calls_per_step": args.sl_reps,
+        "warmup": args.warmup, "gpu_launches": launches, "dtype": "f64",
+        "cells_crossed_per_trajectory": visits / nt - 1.0, "cell_visits_per_s": visits / (ms * 1e-3),
+        "config": {"N": N, "p": p, "n_tri": op.n_tri, "gauss_points": ng, "trajectories": nt, "dt": dt,
+                   "velocity": "Taylor-Green, nodal interpolation", "fields": 2,
+                   "l2": "mesh records and fields (~%d MB) L2-resident; no flush (the walk re-reads them)"
+                         % int((op.n_tri * (144 + 2 * 8 * op.n_phi * 3)) / 1e6)},
+        "roofline": {"kernel": "k_sl_walk", "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e9,
+                     "peak": peak, "unit": "GFLOP/s (FP64)", "frac": flops / (ms * 1e-3) / 1e9 / peak,
+                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+                     "flops_per_cell_visit": pv, "flops_per_trajectory": pt},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
 
 
 def batch_leg(args):
@@ -676,6 +758,9 @@ def main():
         return
     if args.workload == "cg":
         cg_leg(args)
+        return
+    if args.workload == "sl":
+        sl_leg(args)
         return
     rank, world, local = dist_setup(args)
     import torch

@@ -212,6 +212,39 @@ int dgsl_apply_div(const dgsl_operator* op, const double* vhat, double* y, int n
 int dgsl_velocity_update(const dgsl_operator* op, double coef, const double* F, const double* p,
                          double* v, int n_rhs, void* stream);
 
+/* ------------------------------------------------------------ semi-Lagrangian transport */
+/* The quadrature rule of dgsl_sl_transport for degree p (1..4): the
+ * collapsed Gauss-Legendre rule on T_ref with n_g = (p+1)^2 points (exact to
+ * degree 2p+1); pts [n_g][2] (xi, eta) and w [n_g] (sum 1/2), host arrays,
+ * each optional.  Pure host call. */
+int dgsl_sl_quadrature(int p, double* pts, double* w, int32_t* n_g);
+
+/* Semi-Lagrangian transport on the main grid (Sec. 2.5, eq. lagrtrj; the
+ * Gauss-point projection of eq. intstage).  The characteristic of every
+ * quadrature point x_g of every triangle is followed backward over dt
+ * (forward if dt < 0) in straight Euler pieces, cell by cell: from x in
+ * triangle T with T's velocity polynomial v at x, the ray x - s v either
+ * ends in T after the time left (the foot) or leaves T through the edge whose
+ * opposite barycentric coordinate first reaches 0 (ties: the lowest local
+ * edge), and the walk continues in the neighbour across it (periodic
+ * neighbours by a frame translation), with no global search.  The fields are
+ * evaluated at the feet in the containing triangles and projected back:
+ *   cstar_i = Mbar_i^{-1} sum_g phi(xi_g) c(x_F(x_g)) w_g |J_i|.
+ *  - vbar: device double[2][n_dof], the main-grid velocity (two components,
+ *    each [n_tri][N_phi] nodal coefficients in internal order).
+ *  - c, cstar: device double[n_fields][n_dof] (n_fields 0..8; cstar must not
+ *    alias c or vbar).
+ *  - foot: device double[n_tri * n_g][2], the foot of trajectory
+ *    (triangle i, point g) at index i n_g + g, in the frame of the triangle
+ *    that contains it (its vertices unwrapped around its first vertex); cell:
+ *    device int32[n_tri * n_g], that triangle (internal index); steps: device
+ *    int32[n_tri * n_g], the cells crossed.  Each may be NULL.
+ * Synchronous (reads a status word).  Returns DGSL_ENOTCONV if a trajectory
+ * crossed more than 65536 cells (its walk stops there). */
+int dgsl_sl_transport(const dgsl_operator* op, double dt, const double* vbar, const double* c,
+                      double* cstar, int n_fields, double* foot, int32_t* cell, int32_t* steps,
+                      void* stream);
+
 /* ------------------------------------------------------------ solves */
 enum { DGSL_SCHUR = 0, DGSL_HELMHOLTZ = 1 };
 enum {

@@ -62,6 +62,9 @@ double cvt_d(double v) { return v; }
 float cvt_f(double v) { return (float)v; }
 uint16_t cvt_b(double v) { return f32_to_bf16_bits((float)v); }
 
+// Cells one semi-Lagrangian trajectory may cross before the walk gives up.
+constexpr int kSLMaxSteps = 1 << 16;
+
 const dgsl_operator* check_dev(const dgsl_operator* op) {
   if (!op) throw Error(DGSL_EINVAL, "operator is NULL");
   if (op->host_only) throw Error(DGSL_ENODEVICE, "operator was built host-only");
@@ -334,6 +337,41 @@ int dgsl_velocity_update(const dgsl_operator* op, double coef, const double* F, 
     for (int k = 0; k < n_rhs; ++k)
       DGSL_CUDA(launch_velocity_update(op->d, coef, F + k * nv, p + (size_t)k * op->d.n, v + k * nv,
                                        (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+int dgsl_sl_quadrature(int p, double* pts, double* w, int32_t* n_g) {
+  if (p < 1 || p > 4) return fail(DGSL_EINVAL, "p must be 1..4");
+  std::vector<double> q, qw;
+  dgsl::sl_rule(p, q, qw);
+  if (n_g) *n_g = (int32_t)qw.size();
+  if (pts) std::copy(q.begin(), q.end(), pts);
+  if (w) std::copy(qw.begin(), qw.end(), w);
+  return DGSL_OK;
+}
+
+int dgsl_sl_transport(const dgsl_operator* cop, double dt, const double* vbar, const double* c, double* cstar,
+                      int n_fields, double* foot, int32_t* cell, int32_t* steps, void* stream) {
+  NvtxRange nvtx("dgsl_sl_transport");
+  DGSL_TRY({
+    check_dev(cop);
+    if (!vbar) return fail(DGSL_EINVAL, "vbar must be non-NULL");
+    if (!std::isfinite(dt)) return fail(DGSL_EINVAL, "dt must be finite");
+    if (n_fields < 0 || n_fields > dgsl::kSLMaxFields) return fail(DGSL_EINVAL, "n_fields must be 0..8");
+    if (n_fields > 0 && (!c || !cstar)) return fail(DGSL_EINVAL, "c and cstar must be non-NULL");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_sl(n_fields);
+    cudaStream_t s = (cudaStream_t)stream;
+    DGSL_CUDA(cudaMemsetAsync(op->sl.err, 0, sizeof(int), s));
+    DGSL_CUDA(dgsl::launch_sl_transport(op->sl.g, op->d.n, dt, vbar, c, n_fields, cstar, foot, cell, steps,
+                                        kSLMaxSteps, op->sl.vmono, op->sl.cmono, op->sl.err, s));
+    DGSL_CUDA(cudaMemcpyAsync(op->sl.h_err, op->sl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*op->sl.h_err)
+      return fail(DGSL_ENOTCONV, "a trajectory crossed more than " + std::to_string(kSLMaxSteps) + " cells");
     return DGSL_OK;
   });
 }

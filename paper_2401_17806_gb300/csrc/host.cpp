@@ -596,6 +596,75 @@ HostBlocks build_blocks(const HostMesh& hm, const RefOps& ro) {
   return hb;
 }
 
+void sl_rule(int p, std::vector<double>& pts, std::vector<double>& w) {
+  std::vector<double> qx, qy;
+  triangle_rule(p + 1, qx, qy, w);
+  pts.resize(2 * qx.size());
+  for (size_t g = 0; g < qx.size(); ++g) {
+    pts[2 * g] = qx[g];
+    pts[2 * g + 1] = qy[g];
+  }
+}
+
+SLHost build_sl_host(const HostMesh& hm, const RefOps& ro) {
+  SLHost s;
+  s.p = ro.p;
+  s.nphi = ro.nphi;
+  const int ne = hm.ne, n = ro.nphi;
+  const double Px = hm.period[0], Py = hm.period[1];
+  s.tri.assign((size_t)ne * 16, 0.0);
+  s.nbr.assign((size_t)ne * 4, 0);
+  for (int ti = 0; ti < ne; ++ti) {
+    const int t = hm.perm[ti];
+    const double* P = &hm.txy[(size_t)t * 6];
+    double* o = &s.tri[(size_t)ti * 16];
+    const double e1x = P[2] - P[0], e1y = P[3] - P[1], e2x = P[4] - P[0], e2y = P[5] - P[1];
+    const double det = e1x * e2y - e1y * e2x;
+    o[0] = P[0];
+    o[1] = P[1];
+    o[2] = e1x;
+    o[3] = e1y;
+    o[4] = e2x;
+    o[5] = e2y;
+    o[6] = e2y / det;   // xi  = j00 dx + j01 dy
+    o[7] = -e2x / det;
+    o[8] = -e1y / det;  // eta = j10 dx + j11 dy
+    o[9] = e1x / det;
+    for (int k = 0; k < 3; ++k) {
+      const int j = hm.tri_edge[(size_t)t * 3 + k];
+      const int l = hm.lr[2 * j], r = hm.lr[2 * j + 1];
+      // shift: periods to add to r's frame to reach l's
+      const double sx = hm.shift[2 * (size_t)j] * Px, sy = hm.shift[2 * (size_t)j + 1] * Py;
+      const bool is_l = l == t;
+      o[10 + 2 * k] = is_l ? -sx : sx;
+      o[11 + 2 * k] = is_l ? -sy : sy;
+      s.nbr[(size_t)ti * 4 + k] = hm.rank[is_l ? r : l];
+    }
+  }
+  Basis b(ro.p);
+  s.mono_c = b.C;
+  std::vector<double> qx, qy, qw;
+  triangle_rule(ro.p + 1, qx, qy, qw);
+  s.ng = (int)qw.size();
+  s.pts.resize((size_t)s.ng * 2);
+  s.w = qw;
+  std::vector<double> Minv;
+  invert(n, ro.Mref, Minv);
+  s.q.assign((size_t)n * s.ng, 0.0);
+  std::vector<double> phi(n);
+  for (int g = 0; g < s.ng; ++g) {
+    s.pts[2 * g] = qx[g];
+    s.pts[2 * g + 1] = qy[g];
+    b.eval(qx[g], qy[g], phi.data());
+    for (int k = 0; k < n; ++k) {
+      double a = 0.0;
+      for (int l = 0; l < n; ++l) a += Minv[(size_t)k * n + l] * phi[l];
+      s.q[(size_t)k * s.ng + g] = a * qw[g];
+    }
+  }
+  return s;
+}
+
 void node_coords(const HostMesh& hm, const RefOps& ro, int grid, double* out) {
   const int p = ro.p, n = ro.nphi;
   auto ab = node_ab(p);

@@ -67,4 +67,21 @@ HostBlocks build_blocks(const HostMesh& hm, const RefOps& ro);
 
 void node_coords(const HostMesh& hm, const RefOps& ro, int grid, double* out);
 
+// Semi-Lagrangian walk (Sec. 2.5): per-triangle records in internal order
+// (see SLTri in kernels.h) and the reference data of degree p:
+//   mono_c[m][k]  coefficient of monomial m = x^i y^j ((i, j) with i = 0..p
+//                 outer, j = 0..p-i inner) in phi_k;
+//   pts[g][2], w[g]  the collapsed Gauss-Legendre rule, (p+1)^2 points;
+//   q[k][g] = sum_l (Mref^-1)[k][l] phi_l(pts_g) w_g  (the projection of
+//                 eq. intstage; |J_i| cancels against Mbar_i = A_i Mref).
+struct SLHost {
+  int p = 0, nphi = 0, ng = 0;
+  std::vector<double> tri;  // [ne][16] doubles: v0 (2), e1 (2), e2 (2), J^-1 (4), translations (3 x 2)
+  std::vector<int32_t> nbr; // [ne][4]: neighbours across local edges 0..2 (internal), 0
+  std::vector<double> mono_c, pts, w, q;
+};
+SLHost build_sl_host(const HostMesh& hm, const RefOps& ro);
+// The quadrature rule of SLHost alone (no mesh needed).
+void sl_rule(int p, std::vector<double>& pts, std::vector<double>& w);
+
 }  // namespace dgsl

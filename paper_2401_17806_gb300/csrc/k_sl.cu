@@ -1,0 +1,199 @@
+// Semi-Lagrangian trajectories and transport of dgsl (Sec. 2.5, eq. lagrtrj,
+// and the Gauss-point projection of eq. intstage) on the main grid.
+//
+// Every quadrature point x_g of every main triangle follows its characteristic
+// backward over dt in straight (Euler) pieces, one cell at a time: from x in
+// triangle T, with T's DG velocity v at x, the backward ray x - s v either
+// stays in T for the time left (the foot) or leaves T through the edge whose
+// opposite barycentric coordinate first reaches 0; the walk moves to that
+// exit point, into the neighbour's frame (a whole number of periods), and
+// continues with the neighbour's velocity polynomial.  No global search.  At
+// the foot the transported fields are evaluated with the polynomials of the
+// triangle that contains it, and each triangle's values are projected back:
+//   c*_i = Mref^-1 sum_g phi(xi_g) w_g c(x_F(x_g))      (Mbar_i = A_i Mref, |J_i| = A_i).
+//
+// One thread per trajectory (FP64: the walk's decisions are geometric), the
+// NG = (p+1)^2 trajectories of a triangle in consecutive threads of one block,
+// so the projection reads them from shared memory.  Velocity and fields are
+// first converted to monomial coefficients per cell, so each step evaluates
+// v as 2 N_phi FMAs.  Candidate exits are compared by cross-multiplication;
+// one division per crossed edge.
+#include "kernels.h"
+
+namespace dgsl {
+
+template <int P>
+struct SLDeg {
+  static constexpr int NPHI = (P + 1) * (P + 2) / 2;
+  static constexpr int NG = (P + 1) * (P + 1);
+  static constexpr int TPB = 128 / NG;  // triangles per block of 128 threads
+};
+
+// Monomials x^i y^j of degree <= P, i = 0..P outer, j = 0..P-i inner.
+template <int P>
+__device__ __forceinline__ void sl_monomials(double x, double y, double (&m)[SLDeg<P>::NPHI]) {
+  double xp[P + 1], yp[P + 1];
+  xp[0] = 1.0;
+  yp[0] = 1.0;
+#pragma unroll
+  for (int i = 1; i <= P; ++i) {
+    xp[i] = xp[i - 1] * x;
+    yp[i] = yp[i - 1] * y;
+  }
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i <= P; ++i)
+#pragma unroll
+    for (int j = 0; j <= P - i; ++j) m[c++] = xp[i] * yp[j];
+}
+
+// Nodal to monomial coefficients, a[m] = sum_k C[m][k] u[k], for nf fields of
+// n values ([nf][ne][NPHI] in), written [cell][nf][NPHI] (vel: the
+// components of a cell together) or [nf][ne][NPHI].
+template <int NPHI>
+__global__ void k_sl_mono(const double* __restrict__ in, int64_t n, int ne, int nf, const double* __restrict__ C,
+                          double* __restrict__ out, int vel) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nf * ne * NPHI) return;
+  const int m = (int)(t % NPHI);
+  const int64_t fc = t / NPHI;
+  const int f = (int)(fc / ne), cell = (int)(fc - (int64_t)f * ne);
+  const double* u = in + (int64_t)f * n + (int64_t)cell * NPHI;
+  double a = 0.0;
+#pragma unroll
+  for (int k = 0; k < NPHI; ++k) a = fma(__ldg(C + m * NPHI + k), __ldg(u + k), a);
+  out[vel ? ((int64_t)cell * nf + f) * NPHI + m : ((int64_t)f * ne + cell) * NPHI + m] = a;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, const double* __restrict__ vmono,
+                                                 const double* __restrict__ cmono, int nf, double* __restrict__ cstar,
+                                                 double* __restrict__ foot, int32_t* __restrict__ cellout,
+                                                 int32_t* __restrict__ stepsout, int max_steps, int* err) {
+  using D = SLDeg<P>;
+  constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
+  __shared__ double s_val[kSLMaxFields][TPB * NG];
+  const int lt = threadIdx.x / NG, gq = threadIdx.x - lt * NG;
+  const int ti = blockIdx.x * TPB + lt;
+  if (lt < TPB && ti < g.ne) {
+    const double* T = g.tri + (int64_t)ti * 16;
+    const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
+    double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
+    double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
+    int cell = ti, steps = 0;
+    double tau = dt;
+    double mono[NPHI];
+    for (;;) {
+      const double* C = g.tri + (int64_t)cell * 16;
+      const double j00 = __ldg(C + 6), j01 = __ldg(C + 7), j10 = __ldg(C + 8), j11 = __ldg(C + 9);
+      const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
+      const double xi = fma(j00, dx, j01 * dy), eta = fma(j10, dx, j11 * dy);
+      sl_monomials<P>(xi, eta, mono);
+      const double* a = vmono + (int64_t)cell * 2 * NPHI;
+      double vx = 0.0, vy = 0.0;
+#pragma unroll
+      for (int m = 0; m < NPHI; ++m) {
+        vx = fma(__ldg(a + m), mono[m], vx);
+        vy = fma(__ldg(a + NPHI + m), mono[m], vy);
+      }
+      if (vx == 0.0 && vy == 0.0) break;  // no motion: the foot is here
+      const double dxi = fma(j00, vx, j01 * vy), deta = fma(j10, vx, j11 * vy);
+      // barycentrics of vertices 0, 1, 2 and their rates along x - s v
+      const double lam[3] = {1.0 - xi - eta, xi, eta};
+      const double rate[3] = {dxi + deta, -dxi, -deta};
+      int kx = -1;
+      double bn = 0.0, bd = 1.0;  // exit parameter bn / bd
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int o = k == 0 ? 2 : k - 1;  // vertex opposite local edge k: (k + 2) mod 3
+        if (rate[o] < 0.0) {
+          const double nn = fmax(lam[o], 0.0), dd = -rate[o];
+          if (kx < 0 || nn * bd < bn * dd) {
+            kx = k;
+            bn = nn;
+            bd = dd;
+          }
+        }
+      }
+      if (kx < 0 || bn >= tau * bd) {  // the foot is in this cell
+        x = fma(-tau, vx, x);
+        y = fma(-tau, vy, y);
+        break;
+      }
+      const double s = bn / bd;
+      x = fma(-s, vx, x) + __ldg(C + 10 + 2 * kx);
+      y = fma(-s, vy, y) + __ldg(C + 11 + 2 * kx);
+      tau -= s;
+      cell = __ldg(g.nbr + (int64_t)cell * 4 + kx);
+      if (++steps > max_steps) {  // bounded walk: reported, never a hang
+        atomicExch(err, 1);
+        break;
+      }
+    }
+    const double* C = g.tri + (int64_t)cell * 16;
+    const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
+    sl_monomials<P>(fma(__ldg(C + 6), dx, __ldg(C + 7) * dy), fma(__ldg(C + 8), dx, __ldg(C + 9) * dy), mono);
+    const int64_t tr = (int64_t)ti * NG + gq;
+    if (foot) {
+      foot[2 * tr] = x;
+      foot[2 * tr + 1] = y;
+    }
+    if (cellout) cellout[tr] = cell;
+    if (stepsout) stepsout[tr] = steps;
+    for (int f = 0; f < nf; ++f) {
+      const double* cf = cmono + ((int64_t)f * g.ne + cell) * NPHI;
+      double v = 0.0;
+#pragma unroll
+      for (int m = 0; m < NPHI; ++m) v = fma(__ldg(cf + m), mono[m], v);
+      s_val[f][threadIdx.x] = v;
+    }
+  }
+  __syncthreads();
+  // eq. intstage: thread (triangle, k) of the block
+  if ((int)threadIdx.x < TPB * NPHI) {
+    const int l2 = threadIdx.x / NPHI, k = threadIdx.x - l2 * NPHI;
+    const int t2 = blockIdx.x * TPB + l2;
+    if (t2 < g.ne)
+      for (int f = 0; f < nf; ++f) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q) acc = fma(__ldg(g.q + k * NG + q), s_val[f][l2 * NG + q], acc);
+        cstar[(int64_t)f * n + (int64_t)t2 * NPHI + k] = acc;
+      }
+  }
+}
+
+template <int P>
+static cudaError_t run_sl(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,
+                          double* cstar, double* foot, int32_t* cell, int32_t* steps, int max_steps, double* vmono,
+                          double* cmono, int* err, cudaStream_t s) {
+  using D = SLDeg<P>;
+  const int64_t tv = (int64_t)2 * g.ne * D::NPHI;
+  k_sl_mono<D::NPHI><<<(int)((tv + 255) / 256), 256, 0, s>>>(vbar, n, g.ne, 2, g.mono_c, vmono, 1);
+  int launches = 2;
+  if (nf > 0) {
+    const int64_t tc = (int64_t)nf * g.ne * D::NPHI;
+    k_sl_mono<D::NPHI><<<(int)((tc + 255) / 256), 256, 0, s>>>(c, n, g.ne, nf, g.mono_c, cmono, 0);
+    ++launches;
+  }
+  k_sl_walk<P><<<(g.ne + D::TPB - 1) / D::TPB, 128, 0, s>>>(g, n, dt, vmono, cmono, nf, cstar, foot, cell, steps,
+                                                            max_steps, err);
+  count_launch(launches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,
+                                double* cstar, double* foot, int32_t* cell, int32_t* steps, int max_steps,
+                                double* vmono, double* cmono, int* err, cudaStream_t s) {
+  if (nf < 0 || nf > kSLMaxFields || g.ne < 1 || !vbar || (nf > 0 && (!c || !cstar || !cmono)))
+    return cudaErrorInvalidValue;
+  switch (g.p) {
+    case 1: return run_sl<1>(g, n, dt, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 2: return run_sl<2>(g, n, dt, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 3: return run_sl<3>(g, n, dt, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 4: return run_sl<4>(g, n, dt, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dgsl

@@ -123,6 +123,29 @@ size_t cg_vec_bytes(const DevOp& op, int precond);
 // Bounded-wait self-test (see k_cg.cu): records kStatusTimeout in bar->status.
 cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s);
 
+// ---- semi-Lagrangian trajectories and transport (Sec. 2.5, eq. intstage; k_sl.cu)
+// Device copy of SLHost (host.h): per-triangle records [ne][16] doubles
+// (v0, e1, e2, J^-1, frame translations across local edges 0..2), neighbours
+// [ne][4], and the reference data of degree p.
+struct SLDev {
+  int p = 0, nphi = 0, ng = 0, ne = 0;
+  const double* tri = nullptr;
+  const int32_t* nbr = nullptr;
+  const double* mono_c = nullptr;  // [nphi][nphi]
+  const double* pts = nullptr;     // [ng][2]
+  const double* q = nullptr;       // [nphi][ng]
+};
+constexpr int kSLMaxFields = 8;
+// Feet of the ne * ng trajectories (foot [ne * ng][2] in the containing
+// triangle's frame, cell and steps [ne * ng], each optional) and the
+// transported fields cstar = projection of c at the feet (nf <= 8 fields of n
+// values).  vbar: [2][n] main-grid velocity.  Workspace: vmono [ne][2][nphi],
+// cmono [nf][ne][nphi].  *err (zeroed by the caller) becomes 1 if a
+// trajectory crossed more than max_steps cells (its walk stops there).
+cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,
+                                double* cstar, double* foot, int32_t* cell, int32_t* steps, int max_steps,
+                                double* vmono, double* cmono, int* err, cudaStream_t s);
+
 void count_launch(int n = 1);
 uint64_t launch_count();
 

@@ -49,6 +49,16 @@ struct dgsl_operator {
   bool have_blocks = false;
   int host_only = 0;
   DevOp d;
+  // semi-Lagrangian walk data (built on first use) and its workspace
+  struct SL {
+    dgsl::SLDev g;
+    bool built = false;
+    double* vmono = nullptr;
+    double* cmono = nullptr;
+    size_t cmono_cap = 0;
+    int* err = nullptr;
+    int* h_err = nullptr;  // pinned
+  } sl;
   std::vector<void*> allocs;
   int64_t device_bytes = 0;
   std::mutex mu;
@@ -114,6 +124,7 @@ struct dgsl_operator {
       if (w.h_part) cudaFreeHost(w.h_part);
       if (w.h_res) cudaFreeHost(w.h_res);
       if (w.h_pj_bad) cudaFreeHost(w.h_pj_bad);
+      if (sl.h_err) cudaFreeHost(sl.h_err);
       if (w.ev0) cudaEventDestroy(w.ev0);
       if (w.ev1) cudaEventDestroy(w.ev1);
     }
@@ -135,6 +146,30 @@ struct dgsl_operator {
     DGSL_CUDA(cudaMallocHost(&w.h_res, sizeof(CGResult)));
     DGSL_CUDA(cudaEventCreate(&w.ev0));
     DGSL_CUDA(cudaEventCreate(&w.ev1));
+  }
+  // Semi-Lagrangian walk data and workspace for nf fields (caller holds mu).
+  void ensure_sl(int nf) {
+    if (!sl.built) {
+      dgsl::SLHost h = dgsl::build_sl_host(hm, ro);
+      sl.g.p = h.p;
+      sl.g.nphi = h.nphi;
+      sl.g.ng = h.ng;
+      sl.g.ne = d.ne;
+      sl.g.tri = upload(h.tri);
+      sl.g.nbr = upload(h.nbr);
+      sl.g.mono_c = upload(h.mono_c);
+      sl.g.pts = upload(h.pts);
+      sl.g.q = upload(h.q);
+      sl.vmono = dalloc<double>((size_t)d.ne * 2 * d.nphi);
+      sl.err = dalloc<int>(1);
+      DGSL_CUDA(cudaMallocHost(&sl.h_err, sizeof(int)));
+      sl.built = true;
+    }
+    const size_t need = (size_t)nf * d.ne * d.nphi;
+    if (need > sl.cmono_cap) {
+      sl.cmono = dalloc<double>(need);  // (a smaller one stays allocated until destroy)
+      sl.cmono_cap = need;
+    }
   }
   // Block-Jacobi preconditioned operator for A = coefM Mbar + coefK K with
   // couplings of type 0 (FP32), 1 (FP64) or 2 (BF16), built on stream s unless

@@ -111,6 +111,9 @@ _SIGS = {
     "dgsl_apply_div": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dgsl_velocity_update": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                        C.c_void_p]),
+    "dgsl_sl_quadrature": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "dgsl_sl_transport": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
@@ -294,6 +297,19 @@ class Operator:
                                            _dptr(v, "float64", 2 * self.n_dual * n_rhs), int(n_rhs),
                                            _stream(stream)))
 
+    def dgsl_sl_transport(self, dt, vbar, c=None, cstar=None, n_fields=0, foot=None, cell=None, steps=None,
+                          stream=None):
+        """Semi-Lagrangian transport (Sec. 2.5, eq. intstage): vbar [2 * n_dof]
+        float64; c, cstar [n_fields * n_dof] float64; optional foot
+        [n_tri * n_g * 2] float64, cell and steps [n_tri * n_g] int32."""
+        ng = sl_quadrature(self.p)[1].size
+        nt = self.n_tri * ng
+        opt = lambda t, dt_, m: _dptr(t, dt_, m) if t is not None else None  # noqa: E731
+        _check(load().dgsl_sl_transport(
+            self.h, float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
+            opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
+            opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
+
     def dgsl_cg_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, check=True):
         """Returns a list of dgsl_solve_info (one per right-hand side)."""
         if opts is None:
@@ -333,6 +349,16 @@ def _set_fields(o, kw):
             raise TypeError(f"{type(o).__name__} has no field {k!r}")
         setattr(o, k, v)
     return o
+
+
+def sl_quadrature(p):
+    """(pts f64[n_g, 2], w f64[n_g]) of dgsl_sl_transport for degree p."""
+    ng = C.c_int32()
+    _check(load().dgsl_sl_quadrature(int(p), None, None, C.byref(ng)))
+    pts = np.zeros((ng.value, 2))
+    w = np.zeros(ng.value)
+    _check(load().dgsl_sl_quadrature(int(p), C.c_void_p(pts.ctypes.data), C.c_void_p(w.ctypes.data), C.byref(ng)))
+    return pts, w
 
 
 def solve_opts(**kw):

@@ -93,3 +93,18 @@ def test_bad_inputs_rejected(dgsl_lib):
         dgsl.load().dgsl_apply_schur(op.h, 0, 1.0, x.data_ptr() or 8, x.data_ptr() or 8, 1, None)
         dgsl._check(dgsl.load().dgsl_apply_schur(op.h, 0, 1.0, 8, 8, 1, None))
     assert e.value.code == dgsl.ENODEVICE
+
+
+def test_sl_quadrature_matches_the_oracle_rule(dgsl_lib):
+    """dgsl_sl_quadrature (host call): the collapsed Gauss-Legendre rule of
+    the semi-Lagrangian projection, point for point the oracle's."""
+    from oracle import sl as SL
+    from paper_2401_17806_gb300 import dgsl
+    for p in (1, 2, 3, 4):
+        pts, w = dgsl.sl_quadrature(p)
+        po, wo = SL.quadrature(p)
+        assert pts.shape == ((p + 1) ** 2, 2)
+        np.testing.assert_allclose(pts, po, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(w, wo, rtol=0, atol=1e-15)
+    with pytest.raises(dgsl.DgslError):
+        dgsl.sl_quadrature(5)
