@@ -18,6 +18,8 @@ Reading of Sec. 2.5 (the paper describes the method in words):
    the edges whose opposite barycentric decreases along the ray, the exit is
    the one with the smallest s (a slightly negative barycentric counts as 0);
    equal s goes to the lowest k.  A zero velocity ends the walk in place.
+ - dt < 0 (forward characteristics): the same walk along x + s v, i.e. with
+   -v over the time |dt|.
  - Each triangle has its own frame: its vertices unwrapped around v_0
    (Connectivity.tri_xy).  Crossing local edge k adds the whole number of
    periods that maps T's frame to the neighbour's; the foot is reported in
@@ -98,12 +100,13 @@ def walk(tri_xy, nbr, trans, velocity, x, cell, dt, max_steps=4096):
     """Backward trajectory from x (in triangle `cell`'s frame) over dt.
     velocity(cell, xi, eta) -> v[2].  Returns (foot, cell, pieces crossed)."""
     x = np.array(x, dtype=np.float64)
-    tau = float(dt)
+    sign = -1.0 if dt < 0 else 1.0
+    tau = abs(float(dt))
     steps = 0
     while True:
         P = tri_xy[cell]
         lam, xi, eta = barycentric(P, x)
-        v = np.asarray(velocity(cell, xi, eta), dtype=np.float64)
+        v = sign * np.asarray(velocity(cell, xi, eta), dtype=np.float64)
         if v[0] == 0.0 and v[1] == 0.0:
             return x, cell, steps
         rate = barycentric_rates(P, v)

@@ -60,6 +60,26 @@ def test_uniform_velocity_foot_and_cell(p):
             assert cell[i, g] in [h[0] for h in hits]
 
 
+def test_forward_time_walks_the_other_way():
+    """dt < 0: forward characteristics, the foot at x - dt v in a cell that
+    contains it, crossing cells on the way."""
+    conn, per = _conn(6)
+    p = 1
+    V = np.array([0.37, -0.21])
+    vbar = np.zeros((2, conn.n_tri, B.n_phi(p)))
+    vbar[0], vbar[1] = V[0], V[1]
+    dt = -0.5
+    foot, cell, steps, _ = SL.transport(conn, per, p, vbar, np.zeros((0, conn.n_tri, B.n_phi(p))), dt)
+    pts, _ = SL.quadrature(p)
+    X = B.triangle_points(conn.tri_xy, pts)
+    assert steps.min() >= 1
+    for i in range(conn.n_tri):
+        for g in range(len(pts)):
+            d = foot[i, g] - (X[i, g] - dt * V)
+            assert np.abs(d - per * np.round(d / per)).max() < 1e-13
+            assert cell[i, g] in [h[0] for h in SL.locate(conn.tri_xy, per, foot[i, g])]
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_zero_velocity_gives_back_the_fields(p):
     conn, per = _conn(4)
