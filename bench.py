@@ -366,15 +366,17 @@ def cg_leg(args):
 
 
 def sl_flops(p, nf):
-    """Algorithmic FP64 operations of the semi-Lagrangian walk (FMA = 2): per
-    cell visited, the reference coordinates (8), the monomials (2p powers,
-    N_phi products), the velocity (4 N_phi), the barycentric rates (6 + 3),
-    the exit tests (9) and the move (8); per trajectory, the start point (8),
-    the final monomials and reference coordinates (2p + N_phi + 8), the fields
-    at the foot (2 N_phi nf) and its share of the projection (2 N_phi nf)."""
+    """Algorithmic FP64 operations of the semi-Lagrangian walk (FMA = 2), with
+    a polynomial of degree p evaluated by nested Horner (h = p(p+1)/2 + p
+    FMAs): per cell visited, the reference coordinates (8), the two velocity
+    components (4 h), the barycentric rates (6 + 3), the exit tests (9) and the
+    move (8); per trajectory, the start point (8), the final reference
+    coordinates (8), the fields at the foot (2 h nf) and its share of the
+    projection (2 N_phi nf)."""
     nphi = (p + 1) * (p + 2) // 2
-    per_visit = 8 + 2 * p + nphi + 4 * nphi + 9 + 9 + 8
-    per_traj = 8 + 2 * p + nphi + 8 + 4 * nphi * nf
+    h = p * (p + 1) // 2 + p
+    per_visit = 8 + 4 * h + 9 + 9 + 8
+    per_traj = 8 + 8 + 2 * h * nf + 2 * nphi * nf
     return per_visit, per_traj
 
 

@@ -16,8 +16,8 @@
 // NG = (p+1)^2 trajectories of a triangle in consecutive threads of one block,
 // so the projection reads them from shared memory.  Velocity and fields are
 // first converted to monomial coefficients per cell, so each step evaluates
-// v as 2 N_phi FMAs.  Candidate exits are compared by cross-multiplication;
-// one division per crossed edge.
+// v by nested Horner (P(P+1)/2 + P FMAs per component).  Candidate exits are
+// compared by cross-multiplication; one division per crossed edge.
 #include "kernels.h"
 
 namespace dgsl {
@@ -29,22 +29,21 @@ struct SLDeg {
   static constexpr int TPB = 128 / NG;  // triangles per block of 128 threads
 };
 
-// Monomials x^i y^j of degree <= P, i = 0..P outer, j = 0..P-i inner.
+// Value at (x, y) of sum_{i+j<=P} a_ij x^i y^j, coefficients in the order
+// i = 0..P outer, j = 0..P-i inner, by nested Horner (y inside, then x):
+// P(P+1)/2 + P FMAs.
 template <int P>
-__device__ __forceinline__ void sl_monomials(double x, double y, double (&m)[SLDeg<P>::NPHI]) {
-  double xp[P + 1], yp[P + 1];
-  xp[0] = 1.0;
-  yp[0] = 1.0;
+__device__ __forceinline__ double sl_poly(const double* __restrict__ a, double x, double y) {
+  double v = 0.0;
 #pragma unroll
-  for (int i = 1; i <= P; ++i) {
-    xp[i] = xp[i - 1] * x;
-    yp[i] = yp[i - 1] * y;
+  for (int i = P; i >= 0; --i) {
+    const int o = i * (P + 1) - i * (i - 1) / 2;  // offset of (i, 0)
+    double r = __ldg(a + o + (P - i));
+#pragma unroll
+    for (int j = P - i - 1; j >= 0; --j) r = fma(r, y, __ldg(a + o + j));
+    v = i == P ? r : fma(v, x, r);
   }
-  int c = 0;
-#pragma unroll
-  for (int i = 0; i <= P; ++i)
-#pragma unroll
-    for (int j = 0; j <= P - i; ++j) m[c++] = xp[i] * yp[j];
+  return v;
 }
 
 // Nodal to monomial coefficients, a[m] = sum_k C[m][k] u[k], for nf fields of
@@ -81,21 +80,15 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
     double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
     double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
     int cell = ti, steps = 0;
-    double tau = dt;
-    double mono[NPHI];
+    const double sgn = dt < 0.0 ? -1.0 : 1.0;  // dt < 0: forward, the same walk with -v over |dt|
+    double tau = fabs(dt);
     for (;;) {
       const double* C = g.tri + (int64_t)cell * 16;
       const double j00 = __ldg(C + 6), j01 = __ldg(C + 7), j10 = __ldg(C + 8), j11 = __ldg(C + 9);
       const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
       const double xi = fma(j00, dx, j01 * dy), eta = fma(j10, dx, j11 * dy);
-      sl_monomials<P>(xi, eta, mono);
       const double* a = vmono + (int64_t)cell * 2 * NPHI;
-      double vx = 0.0, vy = 0.0;
-#pragma unroll
-      for (int m = 0; m < NPHI; ++m) {
-        vx = fma(__ldg(a + m), mono[m], vx);
-        vy = fma(__ldg(a + NPHI + m), mono[m], vy);
-      }
+      const double vx = sgn * sl_poly<P>(a, xi, eta), vy = sgn * sl_poly<P>(a + NPHI, xi, eta);
       if (vx == 0.0 && vy == 0.0) break;  // no motion: the foot is here
       const double dxi = fma(j00, vx, j01 * vy), deta = fma(j10, vx, j11 * vy);
       // barycentrics of vertices 0, 1, 2 and their rates along x - s v
@@ -132,7 +125,7 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
     }
     const double* C = g.tri + (int64_t)cell * 16;
     const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
-    sl_monomials<P>(fma(__ldg(C + 6), dx, __ldg(C + 7) * dy), fma(__ldg(C + 8), dx, __ldg(C + 9) * dy), mono);
+    const double xf = fma(__ldg(C + 6), dx, __ldg(C + 7) * dy), yf = fma(__ldg(C + 8), dx, __ldg(C + 9) * dy);
     const int64_t tr = (int64_t)ti * NG + gq;
     if (foot) {
       foot[2 * tr] = x;
@@ -140,13 +133,7 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
     }
     if (cellout) cellout[tr] = cell;
     if (stepsout) stepsout[tr] = steps;
-    for (int f = 0; f < nf; ++f) {
-      const double* cf = cmono + ((int64_t)f * g.ne + cell) * NPHI;
-      double v = 0.0;
-#pragma unroll
-      for (int m = 0; m < NPHI; ++m) v = fma(__ldg(cf + m), mono[m], v);
-      s_val[f][threadIdx.x] = v;
-    }
+    for (int f = 0; f < nf; ++f) s_val[f][threadIdx.x] = sl_poly<P>(cmono + ((int64_t)f * g.ne + cell) * NPHI, xf, yf);
   }
   __syncthreads();
   // eq. intstage: thread (triangle, k) of the block

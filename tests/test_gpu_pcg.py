@@ -160,3 +160,24 @@ def test_pcg_full_size_solve_sampled_residual(dgsl_lib):
     Sx = OP.sampled_rows(conn, p, x, ids, dt * dt)
     r = b64.reshape(-1, op.n_phi)[ids] - Sx
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b64)
+
+
+def test_pcg_bf16_couplings(dgsl_lib):
+    """Block-Jacobi with A P rounded to BF16 (P in FP32) under FP64
+    refinement: the Helmholtz system converges to 1e-10 (oracle residual);
+    the Schur system converges or reports DGSL_ENOTCONV with a relative
+    residual the oracle confirms."""
+    from paper_2401_17806_gb300 import dgsl
+    op, orc, m = _setup(12, 3, 26, store=dgsl.STORE_F64 | dgsl.STORE_BF16)
+    b = synth.standard_normal(op.n_dof, 72)
+    x, info, _ = _solve(op, m, dgsl.HELMHOLTZ, 1e-3, b, tol=1e-10, precision=dgsl.PREC_BF16_IR, precond=BJ)
+    assert info.status == dgsl.OK
+    H = orc.helmholtz_matrix(1e-3)
+    assert np.linalg.norm(b - H @ x) / np.linalg.norm(b) <= 2e-10
+    x, info, _ = _solve(op, m, dgsl.SCHUR, 1e-2, b, tol=1e-10, precision=dgsl.PREC_BF16_IR, precond=BJ,
+                        max_refine=60)
+    assert info.status in (dgsl.OK, dgsl.ENOTCONV)
+    S = orc.schur_matrix(1e-2)
+    pb = OP.project_mean(b)
+    r = np.linalg.norm(pb - S @ x) / np.linalg.norm(pb)
+    assert r <= max(2e-10, 1.01 * info.relres + 1e-12)

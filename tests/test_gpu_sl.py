@@ -156,3 +156,34 @@ def test_sl_full_size_sampled(dgsl_lib):
         rhs = np.einsum("gl,g,ag->al", phi_g, w, vals[f]) * np.abs(area2)[:, None]
         ref = np.linalg.solve(Mbar, rhs[..., None])[..., 0]
         np.testing.assert_allclose(cstar[f][tris], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_non_unit_period_forward_time_and_determinism(dgsl_lib):
+    """A 2 x 0.5 periodic domain, dt < 0 (forward characteristics): the feet
+    of a uniform velocity are x - dt v modulo the periods, in cells that
+    contain them; repeated calls give the same bits."""
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, _ = synth.jittered_periodic_mesh(9, 41)
+    per = np.array([2.0, 0.5])
+    xy = xy * per
+    op = dgsl.Operator(xy, tri, per, 2)
+    conn = OM.connectivity(xy, tri, per)
+    V = np.array([-0.8, 0.33])
+    dt = -0.9  # forward: about 3 cells in x, 5 in y
+    foot, cell, steps, _ = _run(op, dt, [np.full(op.n_dof, V[0]), np.full(op.n_dof, V[1])], [])
+    pts, _ = dgsl.sl_quadrature(2)
+    X = B.triangle_points(conn.tri_xy, pts)
+    d = foot - (X - dt * V)
+    assert np.abs(d - per * np.round(d / per)).max() < 1e-12
+    assert steps.max() >= 5
+    rng = np.random.default_rng(2)
+    for _ in range(40):
+        i, g = int(rng.integers(op.n_tri)), int(rng.integers(pts.shape[0]))
+        assert cell[i, g] in [h[0] for h in SL.locate(conn.tri_xy, per, foot[i, g])]
+    Xn = B.triangle_points(conn.tri_xy, B.nodes(2))
+    vb = np.stack(_tg(Xn[..., 0] / per[0], Xn[..., 1] / per[1])).reshape(2, -1)
+    f = [synth.standard_normal(op.n_dof, 3)]
+    a = _run(op, 0.05, vb, f)
+    b = _run(op, 0.05, vb, f)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
