@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-precond", action="store_true",
                     help="skip the block-Jacobi preconditioned run of the same stage")
+    ap.add_argument("--no-sl", action="store_true",
+                    help="skip the semi-Lagrangian transport of the stage's velocity")
     ap.add_argument("--sl-dt", type=float, default=0.01)
     ap.add_argument("--sl-reps", type=int, default=100,
                     help="sl workload: transport calls per timed step")
@@ -324,6 +326,25 @@ def gpu_leg(args, rank, world, local):
                          iters_total=sum(i.iters for i in b_infos),
                          kern_ms=sum(i.cg_kernel_ms for i in b_infos),
                          relres_max=max(i.relres for i in b_infos))
+    # ---- semi-Lagrangian transport of the stage's main-grid velocity (two
+    # components) by itself over dt, on the same mesh (Sec. 2.5, eq. intstage)
+    if not args.no_sl:
+        vb = st.vbar.clone()  # [2][n_dof]: the viscous solve's velocity
+        cs = torch.empty_like(vb)
+        ng = dgsl.sl_quadrature(op.p)[1].size
+        stp = torch.zeros(op.n_tri * ng, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(stream):
+            op.dgsl_sl_transport(WORKLOAD["dt"], vb, vb, cs, 2, steps=stp, stream=stream)
+        stream.synchronize()
+        reps = 20
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(reps):
+                op.dgsl_sl_transport(WORKLOAD["dt"], vb, vb, cs, 2, stream=stream)
+            ev1.record(stream)
+        stream.synchronize()
+        res["sl"] = dict(ms=ev0.elapsed_time(ev1) / reps, trajectories=op.n_tri * ng,
+                         crossed=float(stp.sum().item()) / (op.n_tri * ng))
     return res
 
 
@@ -853,6 +874,13 @@ def main():
             "max_relres": bj["relres_max"],
             "kernel_achieved_gbs": ach, "kernel_frac": ach / peak if peak else None,
             "bytes_per_row_iter": per_row_bj,
+        }
+    if "sl" in res:
+        sl = res["sl"]
+        line["sl_transport"] = {
+            "what": "semi-Lagrangian transport of the stage's main-grid velocity by itself over dt (Sec. 2.5)",
+            "ms_per_call": sl["ms"], "trajectories_per_s": sl["trajectories"] / (sl["ms"] * 1e-3),
+            "gauss_point_trajectories": sl["trajectories"], "cells_crossed_per_trajectory": sl["crossed"],
         }
     print(json.dumps(line))
     if world > 1:
