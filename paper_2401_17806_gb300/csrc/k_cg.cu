@@ -695,7 +695,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
       const double gg = PRE ? tot[0] - mu_u * tot[NW - 1] : tot[0];  // gamma: r.r (PRE: r . Pi u)
       const V gv = (V)gg;
       const V dv = (V)(tot[1] - mu * tot[3]);  // (w - mu 1) . r  (PRE: . Pi u)
-      rr = PRE ? tot[4 % NW] : gg;             // r.r
+      if constexpr (PRE) rr = tot[4];  // r.r
+      else rr = gg;
       V an, bn;
       if (pass == 0) {
         rr0 = rr;
