@@ -20,6 +20,16 @@ Reading of Sec. 2.5 (the paper describes the method in words):
    equal s goes to the lowest k.  A zero velocity ends the walk in place.
  - dt < 0 (forward characteristics): the same walk along x + s v, i.e. with
    -v over the time |dt|.
+ - Held trajectories (the paper is silent here): the DG velocity jumps
+   across edges, and where the backward rays of two neighbours both point at
+   their shared edge (the forward flow leaves the edge on both sides) the walk
+   would cross back and forth with pieces of zero length and never end.  A
+   walk that leaves a cell through the edge it entered by (a bounce: the
+   velocity at the arrival point sends the ray straight back) is normal once,
+   since the cell it returns to may carry it on along its own velocity; when
+   the cell it bounced back into sends it across that same edge again, the
+   trajectory is held: the foot is the current point (on that edge) in the
+   current cell, and the time left is dropped.
  - Each triangle has its own frame: its vertices unwrapped around v_0
    (Connectivity.tri_xy).  Crossing local edge k adds the whole number of
    periods that maps T's frame to the neighbour's; the foot is reported in
@@ -52,19 +62,22 @@ def quadrature(p):
 
 
 def frames(conn: Connectivity, period):
-    """Neighbour across each local edge, i32[Ne, 3], and the translation
+    """Neighbour across each local edge, i32[Ne, 3]; the translation
     f64[Ne, 3, 2] that maps a point of a triangle's frame into that
-    neighbour's frame (conn.shift: periods to add to r's frame to reach l's)."""
+    neighbour's frame (conn.shift: periods to add to r's frame to reach l's);
+    and back i32[Ne, 3], the local index of the same edge in the neighbour."""
     period = np.asarray(period, dtype=np.float64)
     nbr = neighbours(conn)
     trans = np.zeros((conn.n_tri, 3, 2))
+    back = np.zeros((conn.n_tri, 3), dtype=np.int32)
     for t in range(conn.n_tri):
         for k in range(3):
             j = conn.tri_edge[t, k]
             l, r = conn.lr[j]
             s = conn.shift[j].astype(np.float64) * period
             trans[t, k] = -s if t == l else s
-    return nbr, trans
+            back[t, k] = conn.loc[j, 1] if t == l else conn.loc[j, 0]
+    return nbr, trans, back
 
 
 def barycentric(P, x):
@@ -96,13 +109,15 @@ def dg_value(p, coeffs, xi, eta):
     return float(phi @ coeffs)
 
 
-def walk(tri_xy, nbr, trans, velocity, x, cell, dt, max_steps=4096):
+def walk(tri_xy, nbr, trans, back, velocity, x, cell, dt, max_steps=4096):
     """Backward trajectory from x (in triangle `cell`'s frame) over dt.
     velocity(cell, xi, eta) -> v[2].  Returns (foot, cell, pieces crossed)."""
     x = np.array(x, dtype=np.float64)
     sign = -1.0 if dt < 0 else 1.0
     tau = abs(float(dt))
     steps = 0
+    k_in = -1  # local edge of `cell` through which the walk entered it
+    bounced = False  # the walk entered `cell` by leaving the last cell through its entry edge
     while True:
         P = tri_xy[cell]
         lam, xi, eta = barycentric(P, x)
@@ -119,8 +134,12 @@ def walk(tri_xy, nbr, trans, velocity, x, cell, dt, max_steps=4096):
                     s_exit, k_exit = s, k
         if k_exit < 0 or s_exit >= tau:
             return x - tau * v, cell, steps
+        if k_exit == k_in and bounced:  # a second bounce on the same edge: held
+            return x, cell, steps
         x = x - s_exit * v + trans[cell, k_exit]
         tau -= s_exit
+        bounced = k_exit == k_in
+        k_in = int(back[cell, k_exit])
         cell = int(nbr[cell, k_exit])
         steps += 1
         if steps > max_steps:
@@ -140,7 +159,7 @@ def transport(conn: Connectivity, period, p, vbar, c, dt, max_steps=4096):
     pts, w = quadrature(p)
     ng = len(w)
     nphi = B.n_phi(p)
-    nbr, trans = frames(conn, period)
+    nbr, trans, back = frames(conn, period)
     X = B.triangle_points(conn.tri_xy, pts)  # [Ne, Ng, 2]
 
     def velocity(cell, xi, eta):
@@ -153,7 +172,7 @@ def transport(conn: Connectivity, period, p, vbar, c, dt, max_steps=4096):
     vals = np.zeros((c.shape[0], ne, ng))
     for i in range(ne):
         for g in range(ng):
-            xf, cf, st = walk(conn.tri_xy, nbr, trans, velocity, X[i, g], i, dt, max_steps)
+            xf, cf, st = walk(conn.tri_xy, nbr, trans, back, velocity, X[i, g], i, dt, max_steps)
             foot[i, g], cell[i, g], steps[i, g] = xf, cf, st
             _, xi, eta = barycentric(conn.tri_xy[cf], xf)
             phi = B.eval_phi(p, np.array([[xi, eta]]))[0]

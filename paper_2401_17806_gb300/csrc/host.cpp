@@ -596,6 +596,12 @@ HostBlocks build_blocks(const HostMesh& hm, const RefOps& ro) {
   return hb;
 }
 
+std::vector<double> mref_inverse(const RefOps& ro) {
+  std::vector<double> inv;
+  invert(ro.nphi, ro.Mref, inv);
+  return inv;
+}
+
 void sl_rule(int p, std::vector<double>& pts, std::vector<double>& w) {
   std::vector<double> qx, qy;
   triangle_rule(p + 1, qx, qy, w);
@@ -639,6 +645,8 @@ SLHost build_sl_host(const HostMesh& hm, const RefOps& ro) {
       o[10 + 2 * k] = is_l ? -sx : sx;
       o[11 + 2 * k] = is_l ? -sy : sy;
       s.nbr[(size_t)ti * 4 + k] = hm.rank[is_l ? r : l];
+      // local index of the same edge in that neighbour, 2 bits per edge
+      s.nbr[(size_t)ti * 4 + 3] |= (int32_t)hm.loc[2 * (size_t)j + (is_l ? 1 : 0)] << (2 * k);
     }
   }
   Basis b(ro.p);

@@ -7,7 +7,12 @@
 // stays in T for the time left (the foot) or leaves T through the edge whose
 // opposite barycentric coordinate first reaches 0; the walk moves to that
 // exit point, into the neighbour's frame (a whole number of periods), and
-// continues with the neighbour's velocity polynomial.  No global search.  At
+// continues with the neighbour's velocity polynomial.  No global search.
+// Where the backward rays on both sides of an edge point at it (the DG
+// velocity jumps there), the walk would bounce across it forever with pieces
+// of zero length: leaving a cell through the edge it entered by is allowed
+// once, and a second bounce on the same edge holds the trajectory there (the
+// foot is the current point, the time left is dropped).  At
 // the foot the transported fields are evaluated with the polynomials of the
 // triangle that contains it, and each triangle's values are projected back:
 //   c*_i = Mref^-1 sum_g phi(xi_g) w_g c(x_F(x_g))      (Mbar_i = A_i Mref, |J_i| = A_i).
@@ -79,7 +84,8 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
     const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
     double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
     double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
-    int cell = ti, steps = 0;
+    int cell = ti, steps = 0, kin = -1;  // kin: local edge of `cell` the walk entered by
+    bool bounced = false;                // it entered by leaving the last cell through its entry edge
     const double sgn = dt < 0.0 ? -1.0 : 1.0;  // dt < 0: forward, the same walk with -v over |dt|
     double tau = fabs(dt);
     for (;;) {
@@ -113,10 +119,13 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
         y = fma(-tau, vy, y);
         break;
       }
+      if (kx == kin && bounced) break;  // a second bounce on the same edge: held here
       const double s = bn / bd;
       x = fma(-s, vx, x) + __ldg(C + 10 + 2 * kx);
       y = fma(-s, vy, y) + __ldg(C + 11 + 2 * kx);
       tau -= s;
+      bounced = kx == kin;
+      kin = (__ldg(g.nbr + (int64_t)cell * 4 + 3) >> (2 * kx)) & 3;
       cell = __ldg(g.nbr + (int64_t)cell * 4 + kx);
       if (++steps > max_steps) {  // bounded walk: reported, never a hang
         atomicExch(err, 1);

@@ -127,7 +127,7 @@ def test_sl_full_size_sampled(dgsl_lib):
     X = B.triangle_points(conn.tri_xy, B.nodes(p))
     vbar = np.stack(_tg(X[..., 0], X[..., 1])).reshape(2, -1)
     foot, cell, steps, cstar = _run(op, dt, vbar, [vbar[0], vbar[1]])
-    nbr, trans = SL.frames(conn, per)
+    nbr, trans, back = SL.frames(conn, per)
     vb = vbar.reshape(2, conn.n_tri, -1)
 
     def velocity(c, xi, eta):
@@ -140,7 +140,7 @@ def test_sl_full_size_sampled(dgsl_lib):
     vals = np.zeros((2, len(tris), len(w)))
     for a, i in enumerate(tris):
         for g in range(len(w)):
-            xf, cf, st = SL.walk(conn.tri_xy, nbr, trans, velocity, P[i, g], i, dt)
+            xf, cf, st = SL.walk(conn.tri_xy, nbr, trans, back, velocity, P[i, g], i, dt)
             assert cf == cell[i, g] and st == steps[i, g]
             assert np.abs(xf - foot[i, g]).max() < 1e-11
             _, xi, eta = SL.barycentric(conn.tri_xy[cf], xf)
@@ -187,3 +187,22 @@ def test_non_unit_period_forward_time_and_determinism(dgsl_lib):
     b = _run(op, 0.05, vb, f)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_held_trajectories_on_a_source_line(dgsl_lib, p):
+    """Velocity pointing away from one edge on both sides: the kernel holds
+    the trajectories that meet the edge where they meet it (after one
+    crossing and one bounce back), like the oracle, at the perpendicular
+    feet."""
+    from test_oracle_sl import source_line
+    op, conn, per, perm = _setup(6, p, 3)
+    for j in (0, 7, conn.n_edge - 1):
+        vbar, want = source_line(conn, per, p, j)
+        foot, cell, steps, _ = _run(op, 5.0, vbar.reshape(2, -1), [])
+        fo, co, so, _ = SL.transport(conn, per, p, vbar, np.zeros((0, conn.n_tri, B.n_phi(p))), 5.0)
+        assert np.array_equal(cell, co) and np.array_equal(steps, so)
+        np.testing.assert_allclose(foot, fo, rtol=0, atol=1e-13)
+        for (t, g), q in want.items():
+            assert cell[t, g] == t and steps[t, g] == 2
+            np.testing.assert_allclose(foot[t, g], q, rtol=0, atol=1e-13)
