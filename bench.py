@@ -63,7 +63,7 @@ def parse_args(argv=None):
     ap.add_argument("--sl-dt", type=float, default=0.01)
     ap.add_argument("--sl-reps", type=int, default=100,
                     help="sl workload: transport calls per timed step")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl"], default="stage",
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns"], default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
@@ -467,6 +467,75 @@ def sl_leg(args):
     print(json.dumps(line))
 
 
+def ns_leg(args):
+    """First-order semi-Lagrangian Navier-Stokes steps (dgsl_ns_step) of the
+    Taylor-Green vortex on the N x N mesh (dt = 1e-3, nu = 1e-3, FP32 inner CG
+    under FP64 refinement to 1e-10, block-Jacobi preconditioned, the pressure
+    solve warm-started from the last step's pressure): steps per second,
+    device-timed.  Then the temporal order on a 64 x 64, p = 2 mesh:
+    the error against the exact decay exp(-8 pi^2 nu t) at t = 0.1 for dt =
+    0.05, 0.025, 0.0125 (nu = 0.01)."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    tp = 2.0 * np.pi
+
+    def tg_dual(op):
+        X = op.node_coords(1)
+        return torch.tensor(np.concatenate([np.sin(tp * X[:, 0]) * np.cos(tp * X[:, 1]),
+                                            -np.cos(tp * X[:, 0]) * np.sin(tp * X[:, 1])]), device="cuda")
+
+    N, p = args.N, args.p
+    op = dgsl.Operator(*synth.jittered_periodic_mesh(N, WORKLOAD["seed"]), p, factored=True)
+    # the pressure solve starts from the last step's pressure
+    opts = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F32_IR, precond=dgsl.PRECOND_BLOCK_JACOBI,
+                           use_x0=1)
+    v = tg_dual(op)
+    pr = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        op.dgsl_ns_step(WORKLOAD["dt"], WORKLOAD["nu"], v, v, pr, opts=opts)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = dgsl.dgsl_launch_count()
+    infos = []
+    ev0.record()
+    for _ in range(args.steps):
+        infos += op.dgsl_ns_step(WORKLOAD["dt"], WORKLOAD["nu"], v, v, pr, opts=opts)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = dgsl.dgsl_launch_count() - l0
+    # temporal order (the exact Taylor-Green decay)
+    opo = dgsl.Operator(*synth.jittered_periodic_mesh(64, 3), 2, factored=True)
+    o2 = dgsl.solve_opts(tol=1e-12, precision=dgsl.PREC_F32_IR, precond=dgsl.PRECOND_BLOCK_JACOBI)
+    v0 = tg_dual(opo)
+    nu, T = 0.01, 0.1
+    ref = v0 * np.exp(-8.0 * np.pi ** 2 * nu * T)
+    errs = []
+    for n in (2, 4, 8):
+        w = v0.clone()
+        for _ in range(n):
+            opo.dgsl_ns_step(T / n, nu, w, w, opts=o2)
+        errs.append(float(torch.linalg.norm(w - ref) / torch.linalg.norm(ref)))
+    print(json.dumps({
+        "metric": "first-order semi-Lagrangian Navier-Stokes steps/s", "workload": "ns", "data": "synthetic",
+        "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+        "gpu_launches": launches, "dtype": "f32+f64",
+        "schur_iters_per_step": sum(i.iters for k, i in enumerate(infos) if k % 3 == 2) / args.steps,
+        "helmholtz_iters_per_step": sum(i.iters for k, i in enumerate(infos) if k % 3 != 2) / args.steps,
+        "config": {"N": N, "p": p, "n_dof": op.n_dof, "dt": WORKLOAD["dt"], "nu": WORKLOAD["nu"],
+                   "tol": WORKLOAD["tol"], "initial": "Taylor-Green vortex (nodal on the dual grid)",
+                   "solves": "FP32 inner CG, FP64 refinement, block-Jacobi; pressure warm-started"},
+        "temporal_order": {"mesh": "64x64, p=2", "nu": nu, "t": T, "dt": [T / 2, T / 4, T / 8], "rel_error": errs,
+                           "observed_order": [float(np.log2(errs[0] / errs[1])), float(np.log2(errs[1] / errs[2]))]},
+        "clocks": clk,
+    }))
+
+
 def batch_leg(args):
     """Independent Schur solves of random meshes (N uniform in 8..nmax, p uniform
     in 1..4, per-solve seeds), each with `rhs` Fourier right-hand sides, all in
@@ -784,6 +853,9 @@ def main():
         return
     if args.workload == "sl":
         sl_leg(args)
+        return
+    if args.workload == "ns":
+        ns_leg(args)
         return
     rank, world, local = dist_setup(args)
     import torch

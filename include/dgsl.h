@@ -337,6 +337,30 @@ int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const 
                           double* x, int n_rhs, const dgsl_solve_opts* opts,
                           dgsl_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------ Navier-Stokes step */
+/* One first-order semi-Lagrangian semi-implicit step of the incompressible
+ * Navier-Stokes equations on the staggered grids: the one-stage (R = 0, Euler)
+ * tableau of App. A applied to the splitting of Sec. 3, without temperature
+ * or gravity.
+ *  1. vbar = L_dm(vhat_in) (eq. d2m), the main-grid velocity;
+ *  2. c = vbar transported by itself over dt (dgsl_sl_transport, Sec. 2.5);
+ *  3. (Mbar + nu dt K) vbar* = Mbar c per component (eq. ad5, lambda = nu);
+ *  4. vhat* = L_md(vbar*) (eq. m2d);
+ *  5. S p = G^T vhat* with S = dt^2 G^T Mhat^-1 G (eq. pressure_final);
+ *  6. vhat_out = vhat* - dt^2 Mhat^-1 G p (eq. nc.2), so that G^T vhat_out = 0.
+ * vhat_in, vhat_out: device double[2][n_dual] (may alias); p_out: device
+ * double[n_dof] in internal order, or NULL: receives p of step 5.  opts
+ * govern the three solves (tolerance, precision, preconditioner); the
+ * Helmholtz solves start from c, and the pressure solve starts from the
+ * contents of p_out when opts->use_x0 is set and p_out is given (the last
+ * step's pressure), else from 0.  info: host array of 3 or NULL (Helmholtz x,
+ * Helmholtz y, Schur).  Needs an operator built with opts.factored.
+ * Synchronous.  Returns the first non-OK solve status, or DGSL_ENOTCONV if a
+ * trajectory crossed more than 65536 cells. */
+int dgsl_ns_step(const dgsl_operator* op, double dt, double nu, const double* vhat_in,
+                 double* vhat_out, double* p_out, const dgsl_solve_opts* opts,
+                 dgsl_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------ batched engine and serving */
 /* One solve request: op's Schur (coef = dt) or Helmholtz (coef = nu*dt)
  * system with n_rhs right-hand sides (0 or 1: one; at most 8): b and x device

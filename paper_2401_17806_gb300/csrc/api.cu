@@ -135,6 +135,7 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
         d.area = op->upload(a);
       }
       d.Mref = op->upload(op->ro.Mref);
+      d.Mrefinv = op->upload(dgsl::mref_inverse(op->ro));
       if (o.store & DGSL_STORE_F64) d.K64 = op->upload(to_ell<double>(hb, d.n, cvt_d));
       if (o.store & DGSL_STORE_F32) d.K32 = op->upload(to_ell<float>(hb, d.n, cvt_f));
       if (o.store & DGSL_STORE_BF16) d.K16 = op->upload(to_ell<uint16_t>(hb, d.n, cvt_b));
@@ -542,6 +543,79 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
       if (st != DGSL_OK && worst == DGSL_OK) worst = st;
     }
     if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";
+    return worst;
+  });
+}
+
+// ------------------------------------------------------------ Navier-Stokes step
+extern "C" int dgsl_ns_step(const dgsl_operator* cop, double dt, double nu, const double* vhat_in, double* vhat_out,
+                            double* p_out, const dgsl_solve_opts* opts, dgsl_solve_info* info, void* stream) {
+  NvtxRange nvtx("dgsl_ns_step");
+  DGSL_TRY({
+    check_dev(cop);
+    if (!vhat_in || !vhat_out) return fail(DGSL_EINVAL, "vhat_in and vhat_out must be non-NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(nu >= 0.0) || !std::isfinite(nu))
+      return fail(DGSL_EINVAL, "dt must be finite and > 0, nu finite and >= 0");
+    if (!cop->d.G || !cop->d.Minv || !cop->d.Uloc) return fail(DGSL_EINVAL, "the step needs opts.factored");
+    dgsl_solve_opts o;
+    dgsl_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
+    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
+      return fail(DGSL_EINVAL, "bad precond");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
+    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_work();
+    op->ensure_sl(2);
+    const DevOp& d = op->d;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = d.n;
+    const size_t nv = (size_t)d.nd * d.npsi;
+    double* w = op->ensure_ns();
+    double* vbar = w;               // [2][n] main-grid velocity (eq. d2m)
+    double* c = vbar + 2 * n;       // [2][n] transported (Sec. 2.5)
+    double* mc = c + 2 * n;         // [2][n] Mbar c
+    double* vst = mc + 2 * n;       // [2][n] after the viscous solve (eq. ad5)
+    double* vhs = vst + 2 * n;      // [2][nd][npsi] on the dual grid (eq. m2d)
+    double* b = vhs + 2 * nv;       // [n] divergence
+    // (the d2m right-hand side goes to c first: the inverse mass is not applied in place)
+    for (int k = 0; k < 2; ++k) DGSL_CUDA(launch_d2m_rhs(d, vhat_in + k * nv, c + k * n, s));
+    DGSL_CUDA(launch_mass_inv(d, c, vbar, 2, s));
+    DGSL_CUDA(cudaMemsetAsync(op->sl.err, 0, sizeof(int), s));
+    DGSL_CUDA(dgsl::launch_sl_transport(op->sl.g, n, dt, vbar, vbar, 2, c, nullptr, nullptr, nullptr, kSLMaxSteps,
+                                        op->sl.vmono, op->sl.cmono, op->sl.err, s));
+    DGSL_CUDA(cudaMemcpyAsync(op->sl.h_err, op->sl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    for (int k = 0; k < 2; ++k) DGSL_CUDA(launch_apply_assembled_f64(d, 0.0, 1.0, c + k * n, mc + k * n, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*op->sl.h_err)
+      return fail(DGSL_ENOTCONV, "a trajectory crossed more than " + std::to_string(kSLMaxSteps) + " cells");
+    int worst = DGSL_OK;
+    dgsl_solve_info inf[3];
+    // the viscous solves start from the transported velocity (H = Mbar + nu dt K)
+    DGSL_CUDA(cudaMemcpyAsync(vst, c, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    dgsl_solve_opts oh = o;
+    oh.use_x0 = 1;
+    for (int k = 0; k < 2; ++k) {
+      const int st = solve_one(op, DGSL_HELMHOLTZ, nu * dt, mc + k * n, vst + k * n, oh, &inf[k], s);
+      if (st != DGSL_OK && worst == DGSL_OK) worst = st;
+    }
+    for (int k = 0; k < 2; ++k) DGSL_CUDA(launch_m2d(d, vst + k * n, vhs + k * nv, s));
+    DGSL_CUDA(launch_div(d, vhs, b, s));
+    double* pr = p_out ? p_out : vbar;  // (vbar is free again)
+    dgsl_solve_opts osch = o;
+    osch.use_x0 = o.use_x0 && p_out ? 1 : 0;  // warm start from the caller's last pressure
+    const int st = solve_one(op, DGSL_SCHUR, dt, b, pr, osch, &inf[2], s);
+    if (st != DGSL_OK && worst == DGSL_OK) worst = st;
+    DGSL_CUDA(launch_velocity_update(d, dt * dt, vhs, pr, vhat_out, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (info)
+      for (int k = 0; k < 3; ++k) info[k] = inf[k];
+    if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "a solve did not converge" : "device wait timed out";
     return worst;
   });
 }

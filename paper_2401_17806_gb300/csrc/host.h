@@ -77,10 +77,13 @@ void node_coords(const HostMesh& hm, const RefOps& ro, int grid, double* out);
 struct SLHost {
   int p = 0, nphi = 0, ng = 0;
   std::vector<double> tri;  // [ne][16] doubles: v0 (2), e1 (2), e2 (2), J^-1 (4), translations (3 x 2)
-  std::vector<int32_t> nbr; // [ne][4]: neighbours across local edges 0..2 (internal), 0
+  std::vector<int32_t> nbr; // [ne][4]: neighbours across local edges 0..2 (internal); word 3 holds,
+                            // in bits 2k..2k+1, the local index of edge k in the neighbour across it
   std::vector<double> mono_c, pts, w, q;
 };
 SLHost build_sl_host(const HostMesh& hm, const RefOps& ro);
+// Mref^-1 (row-major), for the inverse main-grid mass matrix Mbar_i^-1 = Mref^-1 / A_i.
+std::vector<double> mref_inverse(const RefOps& ro);
 // The quadrature rule of SLHost alone (no mesh needed).
 void sl_rule(int p, std::vector<double>& pts, std::vector<double>& w);
 

@@ -525,6 +525,37 @@ cudaError_t launch_axpy_f64(double a, const double* d, double* x, int64_t n, cud
   return cudaGetLastError();
 }
 
+// ---- inverse main-grid mass matrix: y_i = Mref^-1 x_i / A_i (eq. MassMatrixM), thread per row
+template <int NPHI>
+__global__ void __launch_bounds__(256) k_mass_inv(const double* __restrict__ area, const double* __restrict__ Minv,
+                                                  int64_t n, int ncomp, const double* __restrict__ x,
+                                                  double* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * ncomp) return;
+  const int64_t c = t / n, row = t - c * n;
+  const int64_t i = row / NPHI;
+  const int k = (int)(row - i * NPHI);
+  const double* xi = x + c * n + i * NPHI;
+  double acc = 0.0;
+#pragma unroll
+  for (int l = 0; l < NPHI; ++l) acc = fma(__ldg(Minv + k * NPHI + l), __ldg(xi + l), acc);
+  y[t] = acc / __ldg(area + i);
+}
+
+cudaError_t launch_mass_inv(const DevOp& op, const double* x, double* y, int ncomp, cudaStream_t s) {
+  if (!op.Mrefinv || ncomp < 1) return cudaErrorInvalidValue;
+  const int g = (int)((op.n * ncomp + 255) / 256);
+  switch (op.p) {
+    case 1: k_mass_inv<3><<<g, 256, 0, s>>>(op.area, op.Mrefinv, op.n, ncomp, x, y); break;
+    case 2: k_mass_inv<6><<<g, 256, 0, s>>>(op.area, op.Mrefinv, op.n, ncomp, x, y); break;
+    case 3: k_mass_inv<10><<<g, 256, 0, s>>>(op.area, op.Mrefinv, op.n, ncomp, x, y); break;
+    case 4: k_mass_inv<15><<<g, 256, 0, s>>>(op.area, op.Mrefinv, op.n, ncomp, x, y); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 // ---- block-Jacobi preconditioner (an extension): P_i = D_i^-1 for the diagonal blocks
 // D_i = coefK K_0(i) + coefM A_i Mref of A (symmetrised), one triangle per
 // thread in FP64: Cholesky D = L L^T, W = L^-1 by forward substitution, then

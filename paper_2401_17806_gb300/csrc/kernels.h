@@ -27,6 +27,7 @@ struct DevOp {
   uint16_t* K16 = nullptr;         // assembled, BF16 bits
   double* area = nullptr;          // [ne]  A_i = 2|T_i|
   double* Mref = nullptr;          // [nphi][nphi]
+  double* Mrefinv = nullptr;       // [nphi][nphi]
   // factored per-edge blocks (optional)
   double* G = nullptr;             // [nd][2][2][nphi][nphi]
   double* Minv = nullptr;          // [nd][npsi][npsi]
@@ -53,6 +54,9 @@ cudaError_t launch_m2d(const DevOp& op, const double* vbar, double* vhat, cudaSt
 cudaError_t launch_div(const DevOp& op, const double* vhat, double* y, cudaStream_t s);
 cudaError_t launch_velocity_update(const DevOp& op, double coef, const double* F, const double* pr, double* v,
                                    cudaStream_t s);
+// y = Mbar^-1 x (per triangle Mref^-1 x_i / A_i) for ncomp main fields of n values
+// (y must not alias x).
+cudaError_t launch_mass_inv(const DevOp& op, const double* x, double* y, int ncomp, cudaStream_t s);
 
 // ---- vector helpers for the refinement loop
 // r = b - A x (FP64 assembled form, A = coefM Mbar + coefK K), optional mean
@@ -130,7 +134,7 @@ cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_n
 struct SLDev {
   int p = 0, nphi = 0, ng = 0, ne = 0;
   const double* tri = nullptr;
-  const int32_t* nbr = nullptr;
+  const int32_t* nbr = nullptr;   // [ne][4]: 3 neighbours, then their local edge indices (2 bits each)
   const double* mono_c = nullptr;  // [nphi][nphi]
   const double* pts = nullptr;     // [ng][2]
   const double* q = nullptr;       // [nphi][ng]

@@ -59,6 +59,8 @@ struct dgsl_operator {
     int* err = nullptr;
     int* h_err = nullptr;  // pinned
   } sl;
+  // workspace of dgsl_ns_step: vbar | c | Mbar c | vbar* (2 n each) | vhat* (2 nd npsi) | b (n)
+  double* ns = nullptr;
   std::vector<void*> allocs;
   int64_t device_bytes = 0;
   std::mutex mu;
@@ -146,6 +148,11 @@ struct dgsl_operator {
     DGSL_CUDA(cudaMallocHost(&w.h_res, sizeof(CGResult)));
     DGSL_CUDA(cudaEventCreate(&w.ev0));
     DGSL_CUDA(cudaEventCreate(&w.ev1));
+  }
+  // Workspace of dgsl_ns_step (caller holds mu).
+  double* ensure_ns() {
+    if (!ns) ns = dalloc<double>((size_t)9 * d.n + (size_t)2 * d.nd * d.npsi);
+    return ns;
   }
   // Semi-Lagrangian walk data and workspace for nf fields (caller holds mu).
   void ensure_sl(int nf) {

@@ -112,6 +112,8 @@ _SIGS = {
     "dgsl_velocity_update": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                        C.c_void_p]),
     "dgsl_sl_quadrature": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
+    "dgsl_ns_step": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_sl_transport": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
@@ -309,6 +311,22 @@ class Operator:
             self.h, float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
             opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
             opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
+
+    def dgsl_ns_step(self, dt, nu, vhat_in, vhat_out, p_out=None, opts=None, stream=None, check=True):
+        """One first-order semi-Lagrangian Navier-Stokes step; vhat [2 * n_dual]
+        float64 (may alias), p_out [n_dof] or None (with opts.use_x0 its
+        contents start the pressure solve).  Returns the three
+        dgsl_solve_info (Helmholtz x, Helmholtz y, Schur)."""
+        if opts is None:
+            opts = dgsl_default_solve_opts()
+        infos = (dgsl_solve_info * 3)()
+        code = load().dgsl_ns_step(self.h, float(dt), float(nu), _dptr(vhat_in, "float64", 2 * self.n_dual),
+                                   _dptr(vhat_out, "float64", 2 * self.n_dual),
+                                   _dptr(p_out, "float64", self.n_dof) if p_out is not None else None,
+                                   C.byref(opts), infos, _stream(stream))
+        if check:
+            _check(code)
+        return list(infos)
 
     def dgsl_cg_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, check=True):
         """Returns a list of dgsl_solve_info (one per right-hand side)."""
