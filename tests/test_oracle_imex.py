@@ -1,0 +1,161 @@
+"""Pins of the oracle's IMEX tableaux (App. A) and stage trajectories.
+
+The tableaux satisfy the order conditions of their formal orders (1, 2, 3)
+to the six printed digits, the explicit row sums give the printed c~, and
+the implicit ones are stiffly accurate.  The stage-trajectory scheme
+integrates the exact Taylor-Green characteristics (SciPy to 1e-12) at
+orders 1, 2, 3.  With the DG velocity: a uniform velocity gives the exact
+feet (to the weights' printed sum) in the cells a brute-force point location
+finds, R = 0 is one straight Euler segment from the Gauss point, a zero
+velocity gives the fields back, and the sampled feet still converge at
+orders 2 and 3."""
+import numpy as np
+import pytest
+
+from oracle import basis as B
+from oracle import fields as OF
+from oracle import imex as IM
+from oracle import mesh as OM
+from oracle import sl as SL
+from paper_2401_17806_gb300 import synth
+
+TP = 2.0 * np.pi
+
+
+def _tg(x, y):
+    return np.sin(TP * x) * np.cos(TP * y), -np.cos(TP * x) * np.sin(TP * y)
+
+
+def test_tableau_order_conditions():
+    for R, order in ((0, 1), (1, 2), (2, 3)):
+        At, bt, ct, A, b, c = IM.tableau(R)
+        tol = 2e-6 if R == 2 else 1e-14
+        assert np.allclose(np.triu(At), 0.0)
+        for W, C, M in ((bt, ct, At), (b, c, A)):
+            assert abs(W.sum() - 1.0) <= tol
+            if order >= 2:
+                assert abs(W @ C - 0.5) <= tol
+            if order >= 3:
+                assert abs(W @ C ** 2 - 1.0 / 3.0) <= tol
+                assert abs(W @ (M @ C) - 1.0 / 6.0) <= tol
+        np.testing.assert_array_equal(bt, b)  # the semi-implicit class: one set of weights
+        if R >= 1:
+            np.testing.assert_array_equal(A[-1], b)  # stiffly accurate
+    # the printed c~ and c columns
+    g1 = 1.0 - 1.0 / np.sqrt(2.0)
+    np.testing.assert_allclose(IM.tableau(1)[2], [0.0, 1.0 / (2.0 * g1)], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(IM.tableau(1)[5], [g1, 1.0], rtol=0, atol=1e-15)
+    # (each printed entry is rounded to 5e-7: a row of three is within 1.5e-6)
+    np.testing.assert_allclose(IM.tableau(2)[2], [0.0, 0.435866, 0.717933, 1.0], rtol=0, atol=1.5e-6)
+    np.testing.assert_allclose(IM.tableau(2)[5], [0.435866, 0.435866, 0.717933, 1.0], rtol=0, atol=1.5e-6)
+
+
+def _exact_foot(x, dt):
+    solve_ivp = pytest.importorskip("scipy.integrate").solve_ivp
+    r = solve_ivp(lambda t, z: -np.array(_tg(z[0], z[1])), (0.0, dt), x, rtol=1e-12, atol=1e-14)
+    return r.y[:, -1]
+
+
+@pytest.mark.parametrize("R", [0, 1, 2])
+def test_stage_trajectories_reach_their_order(R):
+    rng = np.random.default_rng(4)
+    pts = rng.random((12, 2))
+    errs = []
+    dts = (0.08, 0.04, 0.02)
+    for dt in dts:
+        e = [np.abs(IM.rk_foot(lambda y: np.array(_tg(*y)), x, dt, R) - _exact_foot(x, dt)).max() for x in pts]
+        errs.append(max(e))
+    # one step: local error O(dt^(R+2))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > R + 2 - 0.35) and np.all(orders < R + 2 + 0.6), orders
+
+
+def _conn(N, seed=3):
+    xy, tri, per = synth.jittered_periodic_mesh(N, seed)
+    return OM.connectivity(xy, tri, per), per
+
+
+@pytest.mark.parametrize("R", [0, 1, 2])
+def test_uniform_velocity_feet_and_cells(R):
+    conn, per = _conn(6)
+    p = 1
+    V = np.array([0.37, -0.21])
+    vbar = np.zeros((2, conn.n_tri, B.n_phi(p)))
+    vbar[0], vbar[1] = V[0], V[1]
+    dt = 0.5
+    foot, cell, steps, _ = IM.rk_transport(conn, per, p, vbar, np.zeros((0, conn.n_tri, B.n_phi(p))), dt, R)
+    sb = IM.tableau(R)[1].sum()
+    X = B.triangle_points(conn.tri_xy, SL.quadrature(p)[0])
+    assert steps.max() >= 3
+    for i in range(conn.n_tri):
+        for g in range(X.shape[1]):
+            d = foot[i, g] - (X[i, g] - dt * sb * V)
+            assert np.abs(d - per * np.round(d / per)).max() < 1e-13
+            assert cell[i, g] in [h[0] for h in SL.locate(conn.tri_xy, per, foot[i, g])]
+
+
+def test_euler_tableau_is_one_straight_segment():
+    conn, per = _conn(7)
+    p = 2
+    Xn = OF.main_nodes(conn, p)
+    vbar = np.stack(_tg(Xn[..., 0], Xn[..., 1]))
+    dt = 0.15
+    foot, cell, _, _ = IM.rk_transport(conn, per, p, vbar, np.zeros((0, conn.n_tri, B.n_phi(p))), dt, 0)
+    X = B.triangle_points(conn.tri_xy, SL.quadrature(p)[0])
+    phi = B.eval_phi(p, SL.quadrature(p)[0])  # [Ng, Nphi]
+    for i in range(conn.n_tri):
+        v0 = vbar[:, i, :] @ phi.T  # [2, Ng] the velocity at the Gauss points of i
+        for g in range(X.shape[1]):
+            d = foot[i, g] - (X[i, g] - dt * v0[:, g])
+            assert np.abs(d - per * np.round(d / per)).max() < 1e-13
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_zero_velocity_and_constant_field(R):
+    conn, per = _conn(4)
+    p = 3
+    nphi = B.n_phi(p)
+    c = synth.standard_normal((2, conn.n_tri, nphi), 5)
+    _, _, steps, cs = IM.rk_transport(conn, per, p, np.zeros((2, conn.n_tri, nphi)), c, 0.3, R)
+    assert steps.max() == 0
+    np.testing.assert_allclose(cs, c, rtol=0, atol=1e-12)
+    Xn = OF.main_nodes(conn, p)
+    vbar = np.stack(_tg(Xn[..., 0], Xn[..., 1]))
+    _, _, steps, cs = IM.rk_transport(conn, per, p, vbar, np.full((1, conn.n_tri, nphi), 2.5), 0.2, R)
+    assert steps.max() >= 2
+    np.testing.assert_allclose(cs, 2.5, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_dg_velocity_feet_converge_at_order(R):
+    """Sampled Gauss points of a 32 x 32 mesh, p = 4: the DG velocity's own
+    error (h^5) stays below the time error at these dt."""
+    conn, per = _conn(32)
+    p = 4
+    Xn = OF.main_nodes(conn, p)
+    vbar = np.stack(_tg(Xn[..., 0], Xn[..., 1]))
+    nbr, trans, back = SL.frames(conn, per)
+    X = B.triangle_points(conn.tri_xy, SL.quadrature(p)[0])
+    At, bt = IM.tableau(R)[:2]
+
+    def vel(cell, y):
+        _, xi, eta = SL.barycentric(conn.tri_xy[cell], y)
+        return vbar[:, cell, :] @ B.eval_phi(p, np.array([[xi, eta]]))[0]
+
+    rng = np.random.default_rng(1)
+    sample = [(int(rng.integers(conn.n_tri)), int(rng.integers(X.shape[1]))) for _ in range(10)]
+    errs = []
+    for dt in (0.16, 0.08, 0.04):
+        e = []
+        for i, g in sample:
+            V = []
+            for s in range(len(bt)):
+                d = -dt * sum(At[s, j] * V[j] for j in range(s)) if s else np.zeros(2)
+                y, cy, _ = IM.locate_from(conn.tri_xy, nbr, trans, back, X[i, g], i, d)
+                V.append(vel(cy, y))
+            xf = X[i, g] - dt * sum(bt[j] * V[j] for j in range(len(bt)))
+            dd = xf - _exact_foot(X[i, g], dt)
+            e.append(np.abs(dd - per * np.round(dd / per)).max())
+        errs.append(max(e))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > R + 2 - 0.5), (errs, orders)
