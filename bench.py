@@ -463,8 +463,73 @@ def sl_leg(args):
                      "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
                      "flops_per_cell_visit": pv, "flops_per_trajectory": pt},
         "clocks": clk,
+        "stages": sl_stage_timings(op, vbar, cstar, dt, calls, stream, nt),
     }
     print(json.dumps(line))
+
+
+def _tg_exact_feet(x0, dt, sub=400):
+    """Backward characteristics of the Taylor-Green velocity over dt from the
+    points x0 [m, 2], by classical RK4 with `sub` substeps (error ~1e-16)."""
+    import numpy as np
+    tp = 2.0 * np.pi
+
+    def f(z):
+        return -np.stack([np.sin(tp * z[:, 0]) * np.cos(tp * z[:, 1]),
+                          -np.cos(tp * z[:, 0]) * np.sin(tp * z[:, 1])], axis=1)
+
+    z, h = np.array(x0, dtype=np.float64), dt / sub
+    for _ in range(sub):
+        k1 = f(z)
+        k2 = f(z + 0.5 * h * k1)
+        k3 = f(z + 0.5 * h * k2)
+        k4 = f(z + h * k3)
+        z = z + h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return z
+
+
+def sl_stage_timings(op, vbar, cstar, dt, calls, stream, nt):
+    """The stage-trajectory transport (dgsl_sl_transport_imex, R = 0, 1, 2) on
+    the same mesh and fields: time per call at dt, and the feet's one-step
+    error against the exact characteristics on 256 sampled Gauss points at
+    dt = 0.16, 0.08, 0.04 (observed order = log2 of the ratios)."""
+    import numpy as np
+    import torch
+    out = {}
+    foot = torch.zeros(2 * nt, dtype=torch.float64, device="cuda")
+    steps = torch.zeros(nt, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        op.dgsl_sl_transport_imex(0, 0.0, vbar, foot=foot, stream=stream)  # dt = 0: the Gauss points
+    stream.synchronize()
+    rng = np.random.default_rng(11)
+    idx = rng.choice(nt, 256, replace=False)
+    x0 = foot.view(nt, 2).cpu().numpy()[idx]
+    for R in (0, 1, 2):
+        with torch.cuda.stream(stream):
+            op.dgsl_sl_transport_imex(R, dt, vbar, vbar, cstar, 2, steps=steps, stream=stream)
+        stream.synchronize()
+        crossed = float(steps.sum().item()) / nt
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(calls):
+                op.dgsl_sl_transport_imex(R, dt, vbar, vbar, cstar, 2, stream=stream)
+            ev1.record(stream)
+        stream.synchronize()
+        ms = ev0.elapsed_time(ev1) / calls
+        errs = []
+        for h in (0.16, 0.08, 0.04):
+            with torch.cuda.stream(stream):
+                op.dgsl_sl_transport_imex(R, h, vbar, foot=foot, stream=stream)
+            stream.synchronize()
+            d = foot.view(nt, 2).cpu().numpy()[idx] - _tg_exact_feet(x0, h)
+            errs.append(float(np.abs(d - np.round(d)).max()))
+        out["R%d" % R] = {"ms_per_call": ms, "trajectories_per_s": nt / (ms * 1e-3),
+                          "cells_crossed_per_trajectory": crossed,
+                          "one_step_foot_error": {"dt": [0.16, 0.08, 0.04], "max_abs": errs,
+                                                  "observed_order": [float(np.log2(errs[0] / errs[1])),
+                                                                     float(np.log2(errs[1] / errs[2]))]}}
+    return out
 
 
 def ns_leg(args):

@@ -227,7 +227,10 @@ int dgsl_sl_quadrature(int p, double* pts, double* w, int32_t* n_g);
  * ends in T after the time left (the foot) or leaves T through the edge whose
  * opposite barycentric coordinate first reaches 0 (ties: the lowest local
  * edge), and the walk continues in the neighbour across it (periodic
- * neighbours by a frame translation), with no global search.  The fields are
+ * neighbours by a frame translation), with no global search.  A walk sent
+ * back through the edge it entered a cell by may do so once; sent across
+ * that edge again at once, it is held there (the foot is that point, the
+ * time left dropped: the velocity on both sides points at the edge).  The fields are
  * evaluated at the feet in the containing triangles and projected back:
  *   cstar_i = Mbar_i^{-1} sum_g phi(xi_g) c(x_F(x_g)) w_g |J_i|.
  *  - vbar: device double[2][n_dof], the main-grid velocity (two components,
@@ -244,6 +247,23 @@ int dgsl_sl_quadrature(int p, double* pts, double* w, int32_t* n_g);
 int dgsl_sl_transport(const dgsl_operator* op, double dt, const double* vbar, const double* c,
                       double* cstar, int n_fields, double* foot, int32_t* cell, int32_t* steps,
                       void* stream);
+
+/* Semi-Lagrangian transport with the stage trajectories of the IMEX scheme
+ * of degree R (Sec. 3, the explicit tableau (A~, b) of App. A: R = 0 Euler,
+ * R = 1 two stages, R = 2 four stages with the printed six digits), for a
+ * field carried by a steady main-grid velocity vbar without diffusion.
+ * Every Gauss point x follows
+ *   x^E_s = x - dt sum_{j<s} a~_{s,j} V_j,  V_j = vbar(x^E_j),
+ *   x_F   = x - dt sum_j b_j V_j,
+ * each stage point and the foot reached from x along the straight segment,
+ * cell by cell, as in dgsl_sl_transport (so vbar is evaluated with the
+ * polynomial of the cell reached).  The feet converge at order R + 1 in dt.
+ * The fields are evaluated at x_F and projected as in dgsl_sl_transport.
+ * Arguments, outputs and errors as dgsl_sl_transport (steps: the cells
+ * crossed by all segments of a trajectory); DGSL_EINVAL for R outside 0..2. */
+int dgsl_sl_transport_imex(const dgsl_operator* op, int R, double dt, const double* vbar,
+                           const double* c, double* cstar, int n_fields, double* foot,
+                           int32_t* cell, int32_t* steps, void* stream);
 
 /* ------------------------------------------------------------ solves */
 enum { DGSL_SCHUR = 0, DGSL_HELMHOLTZ = 1 };

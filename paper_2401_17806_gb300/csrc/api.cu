@@ -377,6 +377,33 @@ int dgsl_sl_transport(const dgsl_operator* cop, double dt, const double* vbar, c
   });
 }
 
+int dgsl_sl_transport_imex(const dgsl_operator* cop, int R, double dt, const double* vbar, const double* c,
+                           double* cstar, int n_fields, double* foot, int32_t* cell, int32_t* steps, void* stream) {
+  NvtxRange nvtx("dgsl_sl_transport_imex");
+  DGSL_TRY({
+    check_dev(cop);
+    dgsl::SLTableau tab;
+    if (!dgsl::sl_tableau(R, tab)) return fail(DGSL_EINVAL, "R must be 0, 1 or 2");
+    if (!vbar) return fail(DGSL_EINVAL, "vbar must be non-NULL");
+    if (!std::isfinite(dt)) return fail(DGSL_EINVAL, "dt must be finite");
+    if (n_fields < 0 || n_fields > dgsl::kSLMaxFields) return fail(DGSL_EINVAL, "n_fields must be 0..8");
+    if (n_fields > 0 && (!c || !cstar)) return fail(DGSL_EINVAL, "c and cstar must be non-NULL");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_sl(n_fields);
+    cudaStream_t s = (cudaStream_t)stream;
+    DGSL_CUDA(cudaMemsetAsync(op->sl.err, 0, sizeof(int), s));
+    DGSL_CUDA(dgsl::launch_sl_stages(op->sl.g, op->d.n, dt, tab, vbar, c, n_fields, cstar, foot, cell, steps,
+                                     kSLMaxSteps, op->sl.vmono, op->sl.cmono, op->sl.err, s));
+    DGSL_CUDA(cudaMemcpyAsync(op->sl.h_err, op->sl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*op->sl.h_err)
+      return fail(DGSL_ENOTCONV, "a segment crossed more than " + std::to_string(kSLMaxSteps) + " cells");
+    return DGSL_OK;
+  });
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ solve driver

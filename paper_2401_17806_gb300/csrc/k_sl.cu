@@ -23,6 +23,8 @@
 // first converted to monomial coefficients per cell, so each step evaluates
 // v by nested Horner (P(P+1)/2 + P FMAs per component).  Candidate exits are
 // compared by cross-multiplication; one division per crossed edge.
+#include <cmath>
+
 #include "kernels.h"
 
 namespace dgsl {
@@ -69,83 +71,116 @@ __global__ void k_sl_mono(const double* __restrict__ in, int64_t n, int ne, int 
   out[vel ? ((int64_t)cell * nf + f) * NPHI + m : ((int64_t)f * ne + cell) * NPHI + m] = a;
 }
 
+// Velocity of the walk: the cell's DG polynomial (times sgn) at (xi, eta).
 template <int P>
-__global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, const double* __restrict__ vmono,
-                                                 const double* __restrict__ cmono, int nf, double* __restrict__ cstar,
-                                                 double* __restrict__ foot, int32_t* __restrict__ cellout,
-                                                 int32_t* __restrict__ stepsout, int max_steps, int* err) {
-  using D = SLDeg<P>;
-  constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
-  __shared__ double s_val[kSLMaxFields][TPB * NG];
-  const int lt = threadIdx.x / NG, gq = threadIdx.x - lt * NG;
-  const int ti = blockIdx.x * TPB + lt;
-  if (lt < TPB && ti < g.ne) {
-    const double* T = g.tri + (int64_t)ti * 16;
-    const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
-    double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
-    double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
-    int cell = ti, steps = 0, kin = -1;  // kin: local edge of `cell` the walk entered by
-    bool bounced = false;                // it entered by leaving the last cell through its entry edge
-    const double sgn = dt < 0.0 ? -1.0 : 1.0;  // dt < 0: forward, the same walk with -v over |dt|
-    double tau = fabs(dt);
-    for (;;) {
-      const double* C = g.tri + (int64_t)cell * 16;
-      const double j00 = __ldg(C + 6), j01 = __ldg(C + 7), j10 = __ldg(C + 8), j11 = __ldg(C + 9);
-      const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
-      const double xi = fma(j00, dx, j01 * dy), eta = fma(j10, dx, j11 * dy);
-      const double* a = vmono + (int64_t)cell * 2 * NPHI;
-      const double vx = sgn * sl_poly<P>(a, xi, eta), vy = sgn * sl_poly<P>(a + NPHI, xi, eta);
-      if (vx == 0.0 && vy == 0.0) break;  // no motion: the foot is here
-      const double dxi = fma(j00, vx, j01 * vy), deta = fma(j10, vx, j11 * vy);
-      // barycentrics of vertices 0, 1, 2 and their rates along x - s v
-      const double lam[3] = {1.0 - xi - eta, xi, eta};
-      const double rate[3] = {dxi + deta, -dxi, -deta};
-      int kx = -1;
-      double bn = 0.0, bd = 1.0;  // exit parameter bn / bd
+struct SLPolyVel {
+  const double* vmono;
+  double sgn;
+  __device__ __forceinline__ void operator()(int cell, double xi, double eta, double& vx, double& vy) const {
+    constexpr int NPHI = SLDeg<P>::NPHI;
+    const double* a = vmono + (int64_t)cell * 2 * NPHI;
+    vx = sgn * sl_poly<P>(a, xi, eta);
+    vy = sgn * sl_poly<P>(a + NPHI, xi, eta);
+  }
+};
+
+// A constant velocity: the straight segment to a given point.
+struct SLConstVel {
+  double vx, vy;
+  __device__ __forceinline__ void operator()(int, double, double, double& ox, double& oy) const {
+    ox = vx;
+    oy = vy;
+  }
+};
+
+// The walk from (x, y) in `cell` along x - s v over the time tau (see the file
+// header); on return (x, y) is the foot in the frame of `cell`.  Returns the
+// cells crossed; sets *err and stops after max_steps.
+template <class Vel>
+__device__ __forceinline__ int sl_walk_path(const SLDev& g, double& x, double& y, int& cell, double tau, const Vel& vel,
+                                            int max_steps, int* err) {
+  int steps = 0, kin = -1;  // kin: local edge of `cell` the walk entered by
+  bool bounced = false;     // it entered by leaving the last cell through its entry edge
+  for (;;) {
+    const double* C = g.tri + (int64_t)cell * 16;
+    const double j00 = __ldg(C + 6), j01 = __ldg(C + 7), j10 = __ldg(C + 8), j11 = __ldg(C + 9);
+    const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
+    const double xi = fma(j00, dx, j01 * dy), eta = fma(j10, dx, j11 * dy);
+    double vx, vy;
+    vel(cell, xi, eta, vx, vy);
+    if (vx == 0.0 && vy == 0.0) break;  // no motion: the foot is here
+    const double dxi = fma(j00, vx, j01 * vy), deta = fma(j10, vx, j11 * vy);
+    // barycentrics of vertices 0, 1, 2 and their rates along x - s v
+    const double lam[3] = {1.0 - xi - eta, xi, eta};
+    const double rate[3] = {dxi + deta, -dxi, -deta};
+    int kx = -1;
+    double bn = 0.0, bd = 1.0;  // exit parameter bn / bd
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int o = k == 0 ? 2 : k - 1;  // vertex opposite local edge k: (k + 2) mod 3
-        if (rate[o] < 0.0) {
-          const double nn = fmax(lam[o], 0.0), dd = -rate[o];
-          if (kx < 0 || nn * bd < bn * dd) {
-            kx = k;
-            bn = nn;
-            bd = dd;
-          }
+    for (int k = 0; k < 3; ++k) {
+      const int o = k == 0 ? 2 : k - 1;  // vertex opposite local edge k: (k + 2) mod 3
+      if (rate[o] < 0.0) {
+        const double nn = fmax(lam[o], 0.0), dd = -rate[o];
+        if (kx < 0 || nn * bd < bn * dd) {
+          kx = k;
+          bn = nn;
+          bd = dd;
         }
       }
-      if (kx < 0 || bn >= tau * bd) {  // the foot is in this cell
-        x = fma(-tau, vx, x);
-        y = fma(-tau, vy, y);
-        break;
-      }
-      if (kx == kin && bounced) break;  // a second bounce on the same edge: held here
-      const double s = bn / bd;
-      x = fma(-s, vx, x) + __ldg(C + 10 + 2 * kx);
-      y = fma(-s, vy, y) + __ldg(C + 11 + 2 * kx);
-      tau -= s;
-      bounced = kx == kin;
-      kin = (__ldg(g.nbr + (int64_t)cell * 4 + 3) >> (2 * kx)) & 3;
-      cell = __ldg(g.nbr + (int64_t)cell * 4 + kx);
-      if (++steps > max_steps) {  // bounded walk: reported, never a hang
-        atomicExch(err, 1);
-        break;
-      }
     }
-    const double* C = g.tri + (int64_t)cell * 16;
-    const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
-    const double xf = fma(__ldg(C + 6), dx, __ldg(C + 7) * dy), yf = fma(__ldg(C + 8), dx, __ldg(C + 9) * dy);
-    const int64_t tr = (int64_t)ti * NG + gq;
-    if (foot) {
-      foot[2 * tr] = x;
-      foot[2 * tr + 1] = y;
+    if (kx < 0 || bn >= tau * bd) {  // the foot is in this cell
+      x = fma(-tau, vx, x);
+      y = fma(-tau, vy, y);
+      break;
     }
-    if (cellout) cellout[tr] = cell;
-    if (stepsout) stepsout[tr] = steps;
-    for (int f = 0; f < nf; ++f) s_val[f][threadIdx.x] = sl_poly<P>(cmono + ((int64_t)f * g.ne + cell) * NPHI, xf, yf);
+    if (kx == kin && bounced) break;  // a second bounce on the same edge: held here
+    const double s = bn / bd;
+    x = fma(-s, vx, x) + __ldg(C + 10 + 2 * kx);
+    y = fma(-s, vy, y) + __ldg(C + 11 + 2 * kx);
+    tau -= s;
+    bounced = kx == kin;
+    kin = (__ldg(g.nbr + (int64_t)cell * 4 + 3) >> (2 * kx)) & 3;
+    cell = __ldg(g.nbr + (int64_t)cell * 4 + kx);
+    if (++steps > max_steps) {  // bounded walk: reported, never a hang
+      atomicExch(err, 1);
+      break;
+    }
   }
-  __syncthreads();
-  // eq. intstage: thread (triangle, k) of the block
+  return steps;
+}
+
+// Reference coordinates of (x, y) (in the frame of `cell`).
+__device__ __forceinline__ void sl_ref(const SLDev& g, int cell, double x, double y, double& xi, double& eta) {
+  const double* C = g.tri + (int64_t)cell * 16;
+  const double dx = x - __ldg(C + 0), dy = y - __ldg(C + 1);
+  xi = fma(__ldg(C + 6), dx, __ldg(C + 7) * dy);
+  eta = fma(__ldg(C + 8), dx, __ldg(C + 9) * dy);
+}
+
+// Outputs of one trajectory: foot, cell, steps (each optional) and the fields
+// at the foot into the block's shared values.
+template <int P>
+__device__ __forceinline__ void sl_record(const SLDev& g, int64_t tr, double x, double y, int cell, int steps,
+                                          const double* __restrict__ cmono, int nf, double (*s_val)[128],
+                                          double* __restrict__ foot, int32_t* __restrict__ cellout,
+                                          int32_t* __restrict__ stepsout) {
+  constexpr int NPHI = SLDeg<P>::NPHI;
+  double xf, yf;
+  sl_ref(g, cell, x, y, xf, yf);
+  if (foot) {
+    foot[2 * tr] = x;
+    foot[2 * tr + 1] = y;
+  }
+  if (cellout) cellout[tr] = cell;
+  if (stepsout) stepsout[tr] = steps;
+  for (int f = 0; f < nf; ++f) s_val[f][threadIdx.x] = sl_poly<P>(cmono + ((int64_t)f * g.ne + cell) * NPHI, xf, yf);
+}
+
+// eq. intstage for the block's triangles: thread (triangle, k) of the block.
+template <int P>
+__device__ __forceinline__ void sl_project(const SLDev& g, int64_t n, int nf, const double (*s_val)[128],
+                                           double* __restrict__ cstar) {
+  using D = SLDeg<P>;
+  constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
   if ((int)threadIdx.x < TPB * NPHI) {
     const int l2 = threadIdx.x / NPHI, k = threadIdx.x - l2 * NPHI;
     const int t2 = blockIdx.x * TPB + l2;
@@ -157,6 +192,88 @@ __global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, 
         cstar[(int64_t)f * n + (int64_t)t2 * NPHI + k] = acc;
       }
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_sl_walk(SLDev g, int64_t n, double dt, const double* __restrict__ vmono,
+                                                 const double* __restrict__ cmono, int nf, double* __restrict__ cstar,
+                                                 double* __restrict__ foot, int32_t* __restrict__ cellout,
+                                                 int32_t* __restrict__ stepsout, int max_steps, int* err) {
+  using D = SLDeg<P>;
+  constexpr int NG = D::NG, TPB = D::TPB;
+  __shared__ double s_val[kSLMaxFields][128];
+  const int lt = threadIdx.x / NG, gq = threadIdx.x - lt * NG;
+  const int ti = blockIdx.x * TPB + lt;
+  if (lt < TPB && ti < g.ne) {
+    const double* T = g.tri + (int64_t)ti * 16;
+    const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
+    double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
+    double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
+    int cell = ti;
+    // dt < 0: forward, the same walk with -v over |dt|
+    const SLPolyVel<P> vel{vmono, dt < 0.0 ? -1.0 : 1.0};
+    const int steps = sl_walk_path(g, x, y, cell, fabs(dt), vel, max_steps, err);
+    sl_record<P>(g, (int64_t)ti * NG + gq, x, y, cell, steps, cmono, nf, s_val, foot, cellout, stepsout);
+  }
+  __syncthreads();
+  sl_project<P>(g, n, nf, s_val, cstar);
+}
+
+// Stage trajectories of the explicit IMEX tableau (At, b) with NS stages:
+// x^E_s = x - dt sum_{j<s} At[s][j] V_j with V_j = vbar(x^E_j), and the foot
+// x_F = x - dt sum_j b_j V_j; every point is reached from x along the straight
+// segment, cell by cell.
+template <int P, int NS>
+__global__ void __launch_bounds__(128) k_sl_stages(SLDev g, int64_t n, double dt, SLTableau tab,
+                                                   const double* __restrict__ vmono, const double* __restrict__ cmono,
+                                                   int nf, double* __restrict__ cstar, double* __restrict__ foot,
+                                                   int32_t* __restrict__ cellout, int32_t* __restrict__ stepsout,
+                                                   int max_steps, int* err) {
+  using D = SLDeg<P>;
+  constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
+  __shared__ double s_val[kSLMaxFields][128];
+  const int lt = threadIdx.x / NG, gq = threadIdx.x - lt * NG;
+  const int ti = blockIdx.x * TPB + lt;
+  if (lt < TPB && ti < g.ne) {
+    const double* T = g.tri + (int64_t)ti * 16;
+    const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
+    const double x0 = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
+    const double y0 = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
+    double Vx[NS], Vy[NS];
+    int steps = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = x0, y = y0;
+      int cell = ti;
+      if (s > 0) {
+        double dx = 0.0, dy = 0.0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+          dx = fma(tab.at[s][j], Vx[j], dx);
+          dy = fma(tab.at[s][j], Vy[j], dy);
+        }
+        // the segment x -> x - dt (dx, dy): the walk with the constant velocity dt (dx, dy) over time 1
+        steps += sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * dx, dt * dy}, max_steps, err);
+      }
+      double xi, eta;
+      sl_ref(g, cell, x, y, xi, eta);
+      const double* a = vmono + (int64_t)cell * 2 * NPHI;
+      Vx[s] = sl_poly<P>(a, xi, eta);
+      Vy[s] = sl_poly<P>(a + NPHI, xi, eta);
+    }
+    double dx = 0.0, dy = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      dx = fma(tab.b[j], Vx[j], dx);
+      dy = fma(tab.b[j], Vy[j], dy);
+    }
+    double x = x0, y = y0;
+    int cell = ti;
+    steps += sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * dx, dt * dy}, max_steps, err);
+    sl_record<P>(g, (int64_t)ti * NG + gq, x, y, cell, steps, cmono, nf, s_val, foot, cellout, stepsout);
+  }
+  __syncthreads();
+  sl_project<P>(g, n, nf, s_val, cstar);
 }
 
 template <int P>
@@ -176,6 +293,86 @@ static cudaError_t run_sl(const SLDev& g, int64_t n, double dt, const double* vb
                                                             max_steps, err);
   count_launch(launches);
   return cudaGetLastError();
+}
+
+template <int P, int NS>
+static cudaError_t run_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                                 const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
+                                 int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s) {
+  using D = SLDeg<P>;
+  const int64_t tv = (int64_t)2 * g.ne * D::NPHI;
+  k_sl_mono<D::NPHI><<<(int)((tv + 255) / 256), 256, 0, s>>>(vbar, n, g.ne, 2, g.mono_c, vmono, 1);
+  int launches = 2;
+  if (nf > 0) {
+    const int64_t tc = (int64_t)nf * g.ne * D::NPHI;
+    k_sl_mono<D::NPHI><<<(int)((tc + 255) / 256), 256, 0, s>>>(c, n, g.ne, nf, g.mono_c, cmono, 0);
+    ++launches;
+  }
+  k_sl_stages<P, NS><<<(g.ne + D::TPB - 1) / D::TPB, 128, 0, s>>>(g, n, dt, tab, vmono, cmono, nf, cstar, foot, cell,
+                                                                  steps, max_steps, err);
+  count_launch(launches);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t run_sl_stages_p(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                                   const double* c, int nf, double* cstar, double* foot, int32_t* cell,
+                                   int32_t* steps, int max_steps, double* vmono, double* cmono, int* err,
+                                   cudaStream_t s) {
+  switch (tab.ns) {
+    case 1: return run_sl_stages<P, 1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 2: return run_sl_stages<P, 2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 4: return run_sl_stages<P, 4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The explicit tableaux of App. A (eq. IMEX1-IMEX3): R = 0 Euler, R = 1 the
+// two-stage scheme with gamma = 1 - 1/sqrt(2) and beta = 1/(2 gamma), R = 2
+// the four-stage scheme with its six printed digits.
+bool sl_tableau(int R, SLTableau& t) {
+  t = SLTableau{};
+  if (R == 0) {
+    t.ns = 1;
+    t.b[0] = 1.0;
+  } else if (R == 1) {
+    const double gm = 1.0 - 1.0 / std::sqrt(2.0);
+    t.ns = 2;
+    t.at[1][0] = 1.0 / (2.0 * gm);
+    t.b[0] = 1.0 - gm;
+    t.b[1] = gm;
+  } else if (R == 2) {
+    const double gm = 0.435866;
+    t.ns = 4;
+    t.at[1][0] = gm;
+    t.at[2][0] = 1.437745;
+    t.at[2][1] = -0.719812;
+    t.at[3][0] = 0.916993;
+    t.at[3][1] = 0.5;
+    t.at[3][2] = -0.416993;
+    t.b[0] = 0.0;
+    t.b[1] = 1.208496;
+    t.b[2] = -0.644363;
+    t.b[3] = gm;
+  } else {
+    return false;
+  }
+  return true;
+}
+
+cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                             const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
+                             int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s) {
+  if (nf < 0 || nf > kSLMaxFields || g.ne < 1 || !vbar || (nf > 0 && (!c || !cstar || !cmono)) ||
+      (tab.ns != 1 && tab.ns != 2 && tab.ns != 4))
+    return cudaErrorInvalidValue;
+  switch (g.p) {
+    case 1: return run_sl_stages_p<1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 2: return run_sl_stages_p<2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 3: return run_sl_stages_p<3>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 4: return run_sl_stages_p<4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,

@@ -149,6 +149,22 @@ constexpr int kSLMaxFields = 8;
 cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,
                                 double* cstar, double* foot, int32_t* cell, int32_t* steps, int max_steps,
                                 double* vmono, double* cmono, int* err, cudaStream_t s);
+// An explicit Runge-Kutta tableau (strictly lower At, weights b) of ns <= 4 stages.
+struct SLTableau {
+  int ns = 0;
+  double at[4][4] = {};
+  double b[4] = {};
+};
+// The explicit tableau of App. A for R = 0, 1, 2 (false for another R).
+bool sl_tableau(int R, SLTableau& t);
+// As launch_sl_transport, but the feet come from the stage trajectories of the
+// tableau (each stage point and the foot reached from the Gauss point along a
+// straight segment): x^E_s = x - dt sum_{j<s} at[s][j] vbar(x^E_j),
+// x_F = x - dt sum_j b_j vbar(x^E_j).  steps: the cells crossed by all the
+// segments of a trajectory.
+cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                             const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
+                             int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s);
 
 void count_launch(int n = 1);
 uint64_t launch_count();

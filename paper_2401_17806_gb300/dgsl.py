@@ -116,6 +116,8 @@ _SIGS = {
                                C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_sl_transport": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dgsl_sl_transport_imex": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
@@ -309,6 +311,18 @@ class Operator:
         opt = lambda t, dt_, m: _dptr(t, dt_, m) if t is not None else None  # noqa: E731
         _check(load().dgsl_sl_transport(
             self.h, float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
+            opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
+            opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
+
+    def dgsl_sl_transport_imex(self, R, dt, vbar, c=None, cstar=None, n_fields=0, foot=None, cell=None,
+                               steps=None, stream=None):
+        """Transport with the stage trajectories of the IMEX scheme of degree R
+        (0, 1, 2); arguments as dgsl_sl_transport."""
+        ng = sl_quadrature(self.p)[1].size
+        nt = self.n_tri * ng
+        opt = lambda t, dt_, m: _dptr(t, dt_, m) if t is not None else None  # noqa: E731
+        _check(load().dgsl_sl_transport_imex(
+            self.h, int(R), float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
             opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
             opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
 
