@@ -255,9 +255,10 @@ int dgsl_sl_transport(const dgsl_operator* op, double dt, const double* vbar, co
  * Every Gauss point x follows
  *   x^E_s = x - dt sum_{j<s} a~_{s,j} V_j,  V_j = vbar(x^E_j),
  *   x_F   = x - dt sum_j b_j V_j,
- * each stage point and the foot reached from x along the straight segment,
- * cell by cell, as in dgsl_sl_transport (so vbar is evaluated with the
- * polynomial of the cell reached).  The feet converge at order R + 1 in dt.
+ * each stage point located by walking the straight segment from the
+ * previous one (the first from x, the foot from the last), cell by cell, as
+ * in dgsl_sl_transport (so vbar is evaluated with the polynomial of the cell
+ * reached).  The feet converge at order R + 1 in dt.
  * The fields are evaluated at x_F and projected as in dgsl_sl_transport.
  * Arguments, outputs and errors as dgsl_sl_transport (steps: the cells
  * crossed by all segments of a trajectory); DGSL_EINVAL for R outside 0..2. */

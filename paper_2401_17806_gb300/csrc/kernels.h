@@ -158,8 +158,8 @@ struct SLTableau {
 // The explicit tableau of App. A for R = 0, 1, 2 (false for another R).
 bool sl_tableau(int R, SLTableau& t);
 // As launch_sl_transport, but the feet come from the stage trajectories of the
-// tableau (each stage point and the foot reached from the Gauss point along a
-// straight segment): x^E_s = x - dt sum_{j<s} at[s][j] vbar(x^E_j),
+// tableau (each stage point and the foot reached from the previous point along
+// a straight segment): x^E_s = x - dt sum_{j<s} at[s][j] vbar(x^E_j),
 // x_F = x - dt sum_j b_j vbar(x^E_j).  steps: the cells crossed by all the
 // segments of a trajectory.
 cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
