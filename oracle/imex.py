@@ -1,8 +1,9 @@
 """Oracle: the semi-implicit IMEX Runge-Kutta tableaux of App. A (eq. IMEX1,
-IMEX2, IMEX3) and the semi-Lagrangian stage trajectories of Sec. 3 (after
-eq. butcher) that use the explicit tableau, for a passive field carried by
-a steady main-grid velocity without diffusion (the setting of the paper's
-non-linear transport test, Table ct1).
+IMEX2, IMEX3), the semi-Lagrangian stage trajectories of Sec. 3 (after
+eq. butcher) that use the explicit tableau, and the SL-IMEX step of the
+advection-diffusion model (Sec. 3, its advection-diffusion subsection): a
+main-grid scalar C carried by a steady main-grid velocity and diffused
+implicitly.
 
 Readings (the paper gives the scheme as an overview):
  - Tableaux: the numbers of App. A as printed (six digits for R = 2, whose
@@ -21,6 +22,29 @@ Readings (the paper gives the scheme as an overview):
  - Without diffusion the stage fluxes H^P vanish, the shifted fluxes and the
    stage solves drop out, and the new field is the old one at the final foot,
    projected as eq. intstage.
+
+Readings of the advection-diffusion step (the paper gives the stage
+formulas as an overview; stages s = 1..Ns, implicit tableau (A, b, c)):
+ - V_j(x) = vbar(x^E_j(x)) are the stage velocities of the trajectory from
+   the Gauss point x (above); the implicit trajectory of stage s is
+   x^I_s = x - dt sum_{j<=s} a_{s,j} V_j.
+ - The stage-j flux enters stage s at the point where the characteristic
+   through x at stage s was at stage j: x - (c_s - c_j) dt V_j.  The printed
+   shift weight w_j = sum_{r<=j} a_{j,r} - sum_{r<=j} a_{s,r} is read with
+   the second sum over the whole row s (c_j - c_s) and with the backward
+   sign of the trajectories.  As printed, the sum leaves out a_{s,s} (and
+   any entries between j and s), so even a constant velocity misplaces the
+   fluxes by O(dt) and the scheme falls to first order.
+ - The stage value is C^I_s = proj[C^n(x^I_s) + sum_{j<s} dt a_{s,j}
+   H_j(x - (c_s - c_j) dt V_j)], projected by eq. intstage from the Gauss
+   points (the printed "U^n(x)" is read as C^n at the implicit foot, where
+   the text says the solution is interpolated).
+ - The diffusion sub-system (Mbar + a_{s,s} dt alpha K) C*_s = Mbar C^I_s,
+   the discrete form of eq. ad5 with lambda = alpha, gives the stage flux
+   H_s = (C*_s - C^I_s) / (a_{s,s} dt) = -alpha Mbar^-1 K C*_s.
+ - The tableaux of App. A are stiffly accurate (a_{Ns,j} = b_j), so the final
+   update C^n(x_F) + sum_j dt b_j H_j(x - (1 - c_j) dt V_j) equals the last
+   stage: C^{n+1} = C*_{Ns}.
 
 Test infrastructure only (see the package docstring).
 """
@@ -141,3 +165,65 @@ def rk_transport(conn: Connectivity, period, p, vbar, c, dt, R, max_steps=4096):
         rhs = np.einsum("gl,g,ig->il", phi_g, w, vals[f]) * absJ[:, None]
         cstar[f] = np.linalg.solve(Mbar, rhs[..., None])[..., 0]
     return foot, cell, steps, cstar
+
+
+def advdiff_step(ops, conn: Connectivity, period, p, vbar, C, dt, alpha, R, max_steps=4096):
+    """One SL-IMEX step of the advection-diffusion model: vbar f64[2, Ne,
+    Nphi] steady main-grid velocity, C f64[Ne * Nphi] (natural order), ops an
+    oracle.operators.Operators of the same mesh and degree.  Returns C^{n+1}."""
+    from . import operators as OPS
+    vbar = np.asarray(vbar, dtype=np.float64)
+    Cn = np.asarray(C, dtype=np.float64).reshape(conn.n_tri, -1)
+    At, bt, _, A, b, c = tableau(R)
+    ns = len(b)
+    ne = conn.n_tri
+    pts, w = SL.quadrature(p)
+    ng = len(w)
+    nphi = B.n_phi(p)
+    nbr, trans, back = SL.frames(conn, period)
+    X = B.triangle_points(conn.tri_xy, pts)
+
+    def value(field, cell, y):
+        _, xi, eta = SL.barycentric(conn.tri_xy[cell], y)
+        return field[..., cell, :] @ B.eval_phi(p, np.array([[xi, eta]]))[0]
+
+    def at(field, i, x, d):
+        y, cy, _ = locate_from(conn.tri_xy, nbr, trans, back, x, i, d, max_steps)
+        return value(field, cy, y)
+
+    # stage velocities of every Gauss-point trajectory: V[j, i, g]
+    V = np.zeros((ns, ne, ng, 2))
+    for i in range(ne):
+        for g in range(ng):
+            for s in range(ns):
+                d = -dt * sum(At[s, j] * V[j, i, g] for j in range(s)) if s else np.zeros(2)
+                V[s, i, g] = at(vbar, i, X[i, g], d)
+    # projection of Gauss-point values (eq. intstage)
+    phi_g = B.eval_phi(p, pts)
+    Mbar, _ = main_mass(conn, p)
+    e1 = conn.tri_xy[:, 1] - conn.tri_xy[:, 0]
+    e2 = conn.tri_xy[:, 2] - conn.tri_xy[:, 0]
+    absJ = np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+
+    def project(vals):
+        rhs = np.einsum("gl,g,ig->il", phi_g, w, vals) * absJ[:, None]
+        return np.linalg.solve(Mbar, rhs[..., None])[..., 0]
+
+    H = []
+    Cs = None
+    for s in range(ns):
+        vals = np.zeros((ne, ng))
+        for i in range(ne):
+            for g in range(ng):
+                x = X[i, g]
+                d = -dt * sum(A[s, j] * V[j, i, g] for j in range(s + 1))
+                v = at(Cn, i, x, d)
+                for j in range(s):
+                    if A[s, j] != 0.0:
+                        v += dt * A[s, j] * at(H[j], i, x, -(c[s] - c[j]) * dt * V[j, i, g])
+                vals[i, g] = v
+        CI = project(vals).ravel()
+        Hm = ops.helmholtz_matrix(A[s, s] * dt * alpha)
+        Cs = OPS.direct_solve(Hm, ops.apply_Mbar(CI))
+        H.append(((Cs - CI) / (A[s, s] * dt)).reshape(ne, nphi))
+    return Cs
