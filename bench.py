@@ -63,7 +63,7 @@ def parse_args(argv=None):
     ap.add_argument("--sl-dt", type=float, default=0.01)
     ap.add_argument("--sl-reps", type=int, default=100,
                     help="sl workload: transport calls per timed step")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns"], default="stage",
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns", "advdiff"], default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
@@ -601,6 +601,83 @@ def ns_leg(args):
     }))
 
 
+def advdiff_leg(args):
+    """SL-IMEX steps of the advection-diffusion model (dgsl_advdiff_step) on the
+    N x N mesh: a scalar carried by the steady Taylor-Green velocity and
+    diffused (alpha = 1e-3, dt = 0.01, block-Jacobi FP32 inner CG under FP64
+    refinement to 1e-10), steps per second for R = 0, 1, 2, device-timed.  Then the global
+    order in time on 48 x 48, p = 4: the exact solution exp(-alpha |k|^2 t)
+    sin(k.(x - V t)) for a constant V (alpha = 0.2, k = (2 pi, 0)) at t = 0.2
+    with dt = 0.05, 0.025, 0.0125."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    N, p = args.N, args.p
+    op = dgsl.Operator(*synth.jittered_periodic_mesh(N, WORKLOAD["seed"]), p)
+    X = op.node_coords(0)
+    tp = 2.0 * np.pi
+    vb = torch.tensor(np.concatenate([np.sin(tp * X[:, 0]) * np.cos(tp * X[:, 1]),
+                                      -np.cos(tp * X[:, 0]) * np.sin(tp * X[:, 1])]), device="cuda")
+    c0 = torch.tensor(np.exp(-20.0 * ((X[:, 0] - 0.5) ** 2 + (X[:, 1] - 0.5) ** 2)), device="cuda")
+    opts = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F32_IR, precond=dgsl.PRECOND_BLOCK_JACOBI)
+    dt, alpha = 0.01, 1e-3
+    clocks = ClockSampler(0)
+    clocks.start()
+    legs = {}
+    for R in (0, 1, 2):
+        c = c0.clone()
+        for _ in range(args.warmup):
+            op.dgsl_advdiff_step(R, dt, alpha, vb, c, c, opts=opts)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = dgsl.dgsl_launch_count()
+        iters = 0
+        ev0.record()
+        for _ in range(args.steps):
+            iters += sum(i.iters for i in op.dgsl_advdiff_step(R, dt, alpha, vb, c, c, opts=opts))
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        legs["R%d" % R] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "cg_iters_per_step": iters / args.steps,
+                           "gpu_launches_per_step": (dgsl.dgsl_launch_count() - l0) / args.steps}
+    clk = clocks.stop()
+    # global order in time
+    opo = dgsl.Operator(*synth.jittered_periodic_mesh(48, 3), 4)
+    Xo = opo.node_coords(0)
+    V = np.array([0.8, 0.5])
+    k = np.array([tp, 0.0])
+    a2 = 0.2
+    lam = a2 * (k @ k)
+    vo = torch.tensor(np.concatenate([np.full(opo.n_dof, V[0]), np.full(opo.n_dof, V[1])]), device="cuda")
+    # (FP64 bottoms out near 1e-12 on these Helmholtz systems; 1e-11 is far below the errors measured)
+    o2 = dgsl.solve_opts(tol=1e-11, precision=dgsl.PREC_F64, precond=dgsl.PRECOND_BLOCK_JACOBI)
+    T = 0.2
+    order = {}
+    for R in (0, 1, 2):
+        errs = []
+        for nstep in (4, 8, 16):
+            c = torch.tensor(np.sin(Xo @ k), device="cuda")
+            for _ in range(nstep):
+                opo.dgsl_advdiff_step(R, T / nstep, a2, vo, c, c, opts=o2)
+            ex = np.exp(-lam * T) * np.sin(Xo @ k - (k @ V) * T)
+            errs.append(float(np.abs(c.cpu().numpy() - ex).max()))
+        order["R%d" % R] = {"max_abs_error": errs,
+                            "observed_order": [float(np.log2(errs[0] / errs[1])), float(np.log2(errs[1] / errs[2]))]}
+    r2 = legs["R2"]
+    print(json.dumps({
+        "metric": "SL-IMEX advection-diffusion steps/s (R = 2)", "workload": "advdiff", "data": "synthetic",
+        "value": r2["steps_per_s"], "unit": "steps/s", "ms_per_step": r2["ms_per_step"], "steps": args.steps,
+        "warmup": args.warmup, "dtype": "f32+f64", "by_R": legs,
+        "config": {"N": N, "p": p, "n_dof": op.n_dof, "dt": dt, "alpha": alpha, "tol": WORKLOAD["tol"],
+                   "velocity": "Taylor-Green, steady", "initial": "Gaussian bump",
+                   "solves": "Helmholtz per stage: FP32 inner CG, FP64 refinement, block-Jacobi, started from the stage value"},
+        "temporal_order": {"mesh": "48x48, p=4", "alpha": a2, "V": V.tolist(), "k": k.tolist(), "t": T,
+                           "dt": [T / 4, T / 8, T / 16], **order},
+        "clocks": clk,
+    }))
+
+
 def batch_leg(args):
     """Independent Schur solves of random meshes (N uniform in 8..nmax, p uniform
     in 1..4, per-solve seeds), each with `rhs` Fourier right-hand sides, all in
@@ -921,6 +998,9 @@ def main():
         return
     if args.workload == "ns":
         ns_leg(args)
+        return
+    if args.workload == "advdiff":
+        advdiff_leg(args)
         return
     rank, world, local = dist_setup(args)
     import torch

@@ -382,6 +382,33 @@ int dgsl_ns_step(const dgsl_operator* op, double dt, double nu, const double* vh
                  double* vhat_out, double* p_out, const dgsl_solve_opts* opts,
                  dgsl_solve_info* info, void* stream);
 
+/* ------------------------------------------------------------ advection-diffusion step */
+/* One semi-Lagrangian IMEX step of the advection-diffusion model (Sec. 3 and
+ * its advection-diffusion subsection; tableaux of App. A, R = 0, 1, 2):
+ * dC/dt + vbar . grad C = alpha Laplacian C for a main-grid scalar C carried
+ * by the steady main-grid velocity vbar.  With V_j the stage velocities of
+ * the Gauss-point trajectories (as dgsl_sl_transport_imex) and the implicit
+ * tableau (A, c), each stage s
+ *  1. forms C^I_s = proj[C^n(x - dt sum_{j<=s} a_{s,j} V_j)
+ *                        + sum_{j<s} dt a_{s,j} H_j(x - (c_s - c_j) dt V_j)]
+ *     at every Gauss point x (the earlier stage fluxes taken where the
+ *     characteristic was at their stage; eq. intstage projection);
+ *  2. solves (Mbar + a_{s,s} dt alpha K) C*_s = Mbar C^I_s (eq. ad5, the
+ *     Helmholtz system of dgsl_cg_solve, started from C^I_s);
+ *  3. keeps H_s = (C*_s - C^I_s) / (a_{s,s} dt).
+ * The tableaux are stiffly accurate: c_out = C*_{Ns}.  Every point is
+ * reached from x along a straight segment, cell by cell.
+ *  - vbar: device double[2][n_dof]; c_in, c_out: device double[n_dof]
+ *    (internal order; may alias).
+ *  - opts govern the Ns diffusion solves; info: host array of Ns (1, 2, 4)
+ *    or NULL.
+ * Synchronous.  Returns the first non-OK solve status, DGSL_ENOTCONV if a
+ * segment crossed more than 65536 cells, DGSL_EINVAL for R outside 0..2,
+ * dt <= 0 or alpha < 0. */
+int dgsl_advdiff_step(const dgsl_operator* op, int R, double dt, double alpha, const double* vbar,
+                      const double* c_in, double* c_out, const dgsl_solve_opts* opts,
+                      dgsl_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------ batched engine and serving */
 /* One solve request: op's Schur (coef = dt) or Helmholtz (coef = nu*dt)
  * system with n_rhs right-hand sides (0 or 1: one; at most 8): b and x device

@@ -647,6 +647,81 @@ extern "C" int dgsl_ns_step(const dgsl_operator* cop, double dt, double nu, cons
   });
 }
 
+extern "C" int dgsl_advdiff_step(const dgsl_operator* cop, int R, double dt, double alpha, const double* vbar,
+                      const double* c_in, double* c_out, const dgsl_solve_opts* opts, dgsl_solve_info* info,
+                      void* stream) {
+  NvtxRange nvtx("dgsl_advdiff_step");
+  DGSL_TRY({
+    check_dev(cop);
+    dgsl::SLTableau tab;
+    if (!dgsl::sl_tableau(R, tab)) return fail(DGSL_EINVAL, "R must be 0, 1 or 2");
+    if (!vbar || !c_in || !c_out) return fail(DGSL_EINVAL, "vbar, c_in and c_out must be non-NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(alpha >= 0.0) || !std::isfinite(alpha))
+      return fail(DGSL_EINVAL, "dt must be finite and > 0, alpha finite and >= 0");
+    dgsl_solve_opts o;
+    dgsl_default_solve_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
+    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
+      return fail(DGSL_EINVAL, "bad precond");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
+    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_work();
+    op->ensure_sl(1 + tab.ns);
+    const DevOp& d = op->d;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = d.n;
+    const int64_t nt = (int64_t)d.ne * op->sl.g.ng;
+    double* V = op->ensure_advdiff();         // [ns][nt][2] stage velocities
+    double* F = V + 8 * nt;                   // [1 + ns][n]: C^n, H_0, ..., H_{ns-1}
+    double* ci = F + 5 * n;                   // stage value C^I_s
+    double* rhs = ci + n;                     // Mbar C^I_s
+    double* cst = rhs + n;                    // C*_s
+    DGSL_CUDA(cudaMemcpyAsync(F, c_in, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DGSL_CUDA(cudaMemsetAsync(op->sl.err, 0, sizeof(int), s));
+    DGSL_CUDA(dgsl::launch_sl_stage_velocities(op->sl.g, n, dt, tab, vbar, V, op->sl.vmono, kSLMaxSteps, op->sl.err,
+                                               s));
+    dgsl_solve_opts oh = o;
+    oh.use_x0 = 1;  // each diffusion solve starts from its stage value
+    int worst = DGSL_OK;
+    dgsl_solve_info inf[4];
+    // implicit c_s = sum_j a_{s,j}
+    double c[4] = {};
+    for (int i = 0; i < tab.ns; ++i)
+      for (int j = 0; j <= i; ++j) c[i] += tab.ai[i][j];
+    for (int st = 0; st < tab.ns; ++st) {
+      dgsl::SLStage sg;
+      sg.s = st;
+      for (int j = 0; j <= st; ++j) {
+        sg.a[j] = tab.ai[st][j];
+        sg.shift[j] = c[st] - c[j];
+      }
+      DGSL_CUDA(dgsl::launch_sl_advdiff_stage(op->sl.g, n, dt, sg, V, F, op->sl.cmono, ci, kSLMaxSteps, op->sl.err,
+                                              s));
+      DGSL_CUDA(launch_apply_assembled_f64(d, 0.0, 1.0, ci, rhs, s));
+      DGSL_CUDA(cudaMemcpyAsync(cst, ci, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      const double add = tab.ai[st][st] * dt;
+      const int r = solve_one(op, DGSL_HELMHOLTZ, add * alpha, rhs, cst, oh, &inf[st], s);
+      if (r != DGSL_OK && worst == DGSL_OK) worst = r;
+      if (st + 1 < tab.ns) DGSL_CUDA(dgsl::launch_sl_flux(cst, ci, 1.0 / add, F + (int64_t)(1 + st) * n, n, s));
+    }
+    DGSL_CUDA(cudaMemcpyAsync(c_out, cst, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DGSL_CUDA(cudaMemcpyAsync(op->sl.h_err, op->sl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*op->sl.h_err)
+      return fail(DGSL_ENOTCONV, "a segment crossed more than " + std::to_string(kSLMaxSteps) + " cells");
+    if (info)
+      for (int k = 0; k < tab.ns; ++k) info[k] = inf[k];
+    if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "a solve did not converge" : "device wait timed out";
+    return worst;
+  });
+}
+
 // ------------------------------------------------------------ solve without allocation
 //
 // dgsl_cg_solve_noalloc: the same refinement + persistent-CG solve as

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(128) k_sl_stages(SLDev g, int64_t n, double dt
                                                    const double* __restrict__ vmono, const double* __restrict__ cmono,
                                                    int nf, double* __restrict__ cstar, double* __restrict__ foot,
                                                    int32_t* __restrict__ cellout, int32_t* __restrict__ stepsout,
-                                                   int max_steps, int* err) {
+                                                   int max_steps, int* err, double* __restrict__ vout) {
   using D = SLDeg<P>;
   constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
   __shared__ double s_val[kSLMaxFields][128];
@@ -265,6 +265,11 @@ __global__ void __launch_bounds__(128) k_sl_stages(SLDev g, int64_t n, double dt
       const double* a = vmono + (int64_t)cell * 2 * NPHI;
       Vx[s] = sl_poly<P>(a, xi, eta);
       Vy[s] = sl_poly<P>(a + NPHI, xi, eta);
+      if (vout) {  // the stage velocities alone: [NS][trajectory][2]
+        const int64_t o = ((int64_t)s * g.ne * NG + (int64_t)ti * NG + gq) * 2;
+        vout[o] = Vx[s];
+        vout[o + 1] = Vy[s];
+      }
     }
     double dx = 0.0, dy = 0.0;
 #pragma unroll
@@ -272,8 +277,10 @@ __global__ void __launch_bounds__(128) k_sl_stages(SLDev g, int64_t n, double dt
       dx = fma(tab.b[j], Vx[j], dx);
       dy = fma(tab.b[j], Vy[j], dy);
     }
-    steps += sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * (dx - px), dt * (dy - py)}, max_steps, err);
-    sl_record<P>(g, (int64_t)ti * NG + gq, x, y, cell, steps, cmono, nf, s_val, foot, cellout, stepsout);
+    if (!vout) {
+      steps += sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * (dx - px), dt * (dy - py)}, max_steps, err);
+      sl_record<P>(g, (int64_t)ti * NG + gq, x, y, cell, steps, cmono, nf, s_val, foot, cellout, stepsout);
+    }
   }
   __syncthreads();
   sl_project<P>(g, n, nf, s_val, cstar);
@@ -301,7 +308,7 @@ static cudaError_t run_sl(const SLDev& g, int64_t n, double dt, const double* vb
 template <int P, int NS>
 static cudaError_t run_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
                                  const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
-                                 int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s) {
+                                 int max_steps, double* vmono, double* cmono, int* err, double* vout, cudaStream_t s) {
   using D = SLDeg<P>;
   const int64_t tv = (int64_t)2 * g.ne * D::NPHI;
   k_sl_mono<D::NPHI><<<(int)((tv + 255) / 256), 256, 0, s>>>(vbar, n, g.ne, 2, g.mono_c, vmono, 1);
@@ -312,7 +319,7 @@ static cudaError_t run_sl_stages(const SLDev& g, int64_t n, double dt, const SLT
     ++launches;
   }
   k_sl_stages<P, NS><<<(g.ne + D::TPB - 1) / D::TPB, 128, 0, s>>>(g, n, dt, tab, vmono, cmono, nf, cstar, foot, cell,
-                                                                  steps, max_steps, err);
+                                                                  steps, max_steps, err, vout);
   count_launch(launches);
   return cudaGetLastError();
 }
@@ -321,29 +328,33 @@ template <int P>
 static cudaError_t run_sl_stages_p(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
                                    const double* c, int nf, double* cstar, double* foot, int32_t* cell,
                                    int32_t* steps, int max_steps, double* vmono, double* cmono, int* err,
-                                   cudaStream_t s) {
+                                   double* vout, cudaStream_t s) {
   switch (tab.ns) {
-    case 1: return run_sl_stages<P, 1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
-    case 2: return run_sl_stages<P, 2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
-    case 4: return run_sl_stages<P, 4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 1: return run_sl_stages<P, 1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
+    case 2: return run_sl_stages<P, 2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
+    case 4: return run_sl_stages<P, 4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
   }
   return cudaErrorInvalidValue;
 }
 
-// The explicit tableaux of App. A (eq. IMEX1-IMEX3): R = 0 Euler, R = 1 the
-// two-stage scheme with gamma = 1 - 1/sqrt(2) and beta = 1/(2 gamma), R = 2
-// the four-stage scheme with its six printed digits.
+// The tableaux of App. A (eq. IMEX1-IMEX3), explicit and implicit: R = 0
+// Euler, R = 1 the two-stage scheme with gamma = 1 - 1/sqrt(2) and
+// beta = 1/(2 gamma), R = 2 the four-stage scheme with its six printed digits.
 bool sl_tableau(int R, SLTableau& t) {
   t = SLTableau{};
   if (R == 0) {
     t.ns = 1;
     t.b[0] = 1.0;
+    t.ai[0][0] = 1.0;
   } else if (R == 1) {
     const double gm = 1.0 - 1.0 / std::sqrt(2.0);
     t.ns = 2;
     t.at[1][0] = 1.0 / (2.0 * gm);
     t.b[0] = 1.0 - gm;
     t.b[1] = gm;
+    t.ai[0][0] = gm;
+    t.ai[1][0] = 1.0 - gm;
+    t.ai[1][1] = gm;
   } else if (R == 2) {
     const double gm = 0.435866;
     t.ns = 4;
@@ -357,25 +368,139 @@ bool sl_tableau(int R, SLTableau& t) {
     t.b[1] = 1.208496;
     t.b[2] = -0.644363;
     t.b[3] = gm;
+    t.ai[0][0] = gm;
+    t.ai[1][1] = gm;
+    t.ai[2][1] = 0.282066;
+    t.ai[2][2] = gm;
+    t.ai[3][1] = 1.208496;
+    t.ai[3][2] = -0.644363;
+    t.ai[3][3] = gm;
   } else {
     return false;
   }
   return true;
 }
 
-cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
-                             const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
-                             int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s) {
+static cudaError_t stages_dispatch(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                                   const double* c, int nf, double* cstar, double* foot, int32_t* cell,
+                                   int32_t* steps, int max_steps, double* vmono, double* cmono, int* err,
+                                   double* vout, cudaStream_t s) {
   if (nf < 0 || nf > kSLMaxFields || g.ne < 1 || !vbar || (nf > 0 && (!c || !cstar || !cmono)) ||
       (tab.ns != 1 && tab.ns != 2 && tab.ns != 4))
     return cudaErrorInvalidValue;
   switch (g.p) {
-    case 1: return run_sl_stages_p<1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
-    case 2: return run_sl_stages_p<2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
-    case 3: return run_sl_stages_p<3>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
-    case 4: return run_sl_stages_p<4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, s);
+    case 1: return run_sl_stages_p<1>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
+    case 2: return run_sl_stages_p<2>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
+    case 3: return run_sl_stages_p<3>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
+    case 4: return run_sl_stages_p<4>(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, vout, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                             const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
+                             int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s) {
+  return stages_dispatch(g, n, dt, tab, vbar, c, nf, cstar, foot, cell, steps, max_steps, vmono, cmono, err, nullptr,
+                         s);
+}
+
+cudaError_t launch_sl_stage_velocities(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                                       double* vout, double* vmono, int max_steps, int* err, cudaStream_t s) {
+  if (!vout) return cudaErrorInvalidValue;
+  return stages_dispatch(g, n, dt, tab, vbar, nullptr, 0, nullptr, nullptr, nullptr, nullptr, max_steps, vmono,
+                         nullptr, err, vout, s);
+}
+
+// Stage s of the SL-IMEX advection-diffusion step at every Gauss point x:
+//   C^n(x - dt sum_{j<=s} a_{s,j} V_j) + sum_{j<s} dt a_{s,j} H_j(x - (c_s - c_j) dt V_j),
+// each point reached from x along a straight segment (fields in monomial form:
+// cmono [1 + s][ne][nphi], C^n first, then H_0..H_{s-1}), projected by
+// eq. intstage into ci.
+template <int P>
+__global__ void __launch_bounds__(128) k_sl_advdiff_stage(SLDev g, int64_t n, double dt, SLStage st,
+                                                          const double* __restrict__ V,
+                                                          const double* __restrict__ cmono, double* __restrict__ ci,
+                                                          int max_steps, int* err) {
+  using D = SLDeg<P>;
+  constexpr int NPHI = D::NPHI, NG = D::NG, TPB = D::TPB;
+  __shared__ double s_val[kSLMaxFields][128];
+  const int lt = threadIdx.x / NG, gq = threadIdx.x - lt * NG;
+  const int ti = blockIdx.x * TPB + lt;
+  if (lt < TPB && ti < g.ne) {
+    const double* T = g.tri + (int64_t)ti * 16;
+    const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
+    const double x0 = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
+    const double y0 = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
+    const int64_t nt = (int64_t)g.ne * NG, tr = (int64_t)ti * NG + gq;
+    double vx[4], vy[4];
+    for (int j = 0; j <= st.s; ++j) {
+      vx[j] = __ldg(V + 2 * (j * nt + tr));
+      vy[j] = __ldg(V + 2 * (j * nt + tr) + 1);
+    }
+    // C^n at the implicit foot x^I_s
+    double dx = 0.0, dy = 0.0;
+    for (int j = 0; j <= st.s; ++j) {
+      dx = fma(st.a[j], vx[j], dx);
+      dy = fma(st.a[j], vy[j], dy);
+    }
+    double x = x0, y = y0, xi, eta;
+    int cell = ti;
+    sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * dx, dt * dy}, max_steps, err);
+    sl_ref(g, cell, x, y, xi, eta);
+    double acc = sl_poly<P>(cmono + (int64_t)cell * NPHI, xi, eta);
+    // the earlier stage fluxes, shifted along the characteristic
+    for (int j = 0; j < st.s; ++j) {
+      if (st.a[j] == 0.0) continue;
+      const double h = st.shift[j] * dt;
+      x = x0;
+      y = y0;
+      cell = ti;
+      sl_walk_path(g, x, y, cell, 1.0, SLConstVel{h * vx[j], h * vy[j]}, max_steps, err);
+      sl_ref(g, cell, x, y, xi, eta);
+      acc = fma(dt * st.a[j], sl_poly<P>(cmono + ((int64_t)(1 + j) * g.ne + cell) * NPHI, xi, eta), acc);
+    }
+    s_val[0][threadIdx.x] = acc;
+  }
+  __syncthreads();
+  sl_project<P>(g, n, 1, s_val, ci);
+}
+
+__global__ void k_sl_flux(const double* __restrict__ cst, const double* __restrict__ ci, double inv,
+                          double* __restrict__ h, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) h[i] = (cst[i] - ci[i]) * inv;
+}
+
+template <int P>
+static cudaError_t run_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
+                                     const double* fields, double* cmono, double* ci, int max_steps, int* err,
+                                     cudaStream_t s) {
+  using D = SLDeg<P>;
+  const int nf = 1 + st.s;
+  const int64_t tc = (int64_t)nf * g.ne * D::NPHI;
+  k_sl_mono<D::NPHI><<<(int)((tc + 255) / 256), 256, 0, s>>>(fields, n, g.ne, nf, g.mono_c, cmono, 0);
+  k_sl_advdiff_stage<P><<<(g.ne + D::TPB - 1) / D::TPB, 128, 0, s>>>(g, n, dt, st, V, cmono, ci, max_steps, err);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
+                                    const double* fields, double* cmono, double* ci, int max_steps, int* err,
+                                    cudaStream_t s) {
+  if (st.s < 0 || st.s > 3 || g.ne < 1 || !V || !fields || !cmono || !ci) return cudaErrorInvalidValue;
+  switch (g.p) {
+    case 1: return run_advdiff_stage<1>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 2: return run_advdiff_stage<2>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 3: return run_advdiff_stage<3>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 4: return run_advdiff_stage<4>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sl_flux(const double* cst, const double* ci, double inv, double* h, int64_t n, cudaStream_t s) {
+  k_sl_flux<<<(int)((n + 255) / 256), 256, 0, s>>>(cst, ci, inv, h, n);
+  count_launch(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,

@@ -149,13 +149,15 @@ constexpr int kSLMaxFields = 8;
 cudaError_t launch_sl_transport(const SLDev& g, int64_t n, double dt, const double* vbar, const double* c, int nf,
                                 double* cstar, double* foot, int32_t* cell, int32_t* steps, int max_steps,
                                 double* vmono, double* cmono, int* err, cudaStream_t s);
-// An explicit Runge-Kutta tableau (strictly lower At, weights b) of ns <= 4 stages.
+// An IMEX Runge-Kutta tableau of ns <= 4 stages: explicit At (strictly lower)
+// with weights b, and the implicit A (ai, with its diagonal; weights b too).
 struct SLTableau {
   int ns = 0;
   double at[4][4] = {};
   double b[4] = {};
+  double ai[4][4] = {};
 };
-// The explicit tableau of App. A for R = 0, 1, 2 (false for another R).
+// The tableaux of App. A for R = 0, 1, 2 (false for another R).
 bool sl_tableau(int R, SLTableau& t);
 // As launch_sl_transport, but the feet come from the stage trajectories of the
 // tableau (each stage point and the foot reached from the previous point along
@@ -165,6 +167,26 @@ bool sl_tableau(int R, SLTableau& t);
 cudaError_t launch_sl_stages(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
                              const double* c, int nf, double* cstar, double* foot, int32_t* cell, int32_t* steps,
                              int max_steps, double* vmono, double* cmono, int* err, cudaStream_t s);
+// The stage velocities V_j = vbar(x^E_j) of every trajectory alone (no foot):
+// vout [ns][ne * ng][2].
+cudaError_t launch_sl_stage_velocities(const SLDev& g, int64_t n, double dt, const SLTableau& tab, const double* vbar,
+                                       double* vout, double* vmono, int max_steps, int* err, cudaStream_t s);
+// Stage s (0-based) of the SL-IMEX advection-diffusion step: a[j] = a_{s,j}
+// (j <= s) and shift[j] = c_s - c_j of the implicit tableau.
+struct SLStage {
+  int s = 0;
+  double a[4] = {};
+  double shift[4] = {};
+};
+// ci = projection (eq. intstage) of C^n(x - dt sum_{j<=s} a[j] V_j) +
+// sum_{j<s} dt a[j] H_j(x - shift[j] dt V_j) over every Gauss point x;
+// fields [1 + s][n] = C^n, H_0, ..., H_{s-1}; V as launch_sl_stage_velocities;
+// cmono workspace [1 + s][ne][nphi].
+cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
+                                    const double* fields, double* cmono, double* ci, int max_steps, int* err,
+                                    cudaStream_t s);
+// h = (cst - ci) * inv, n values.
+cudaError_t launch_sl_flux(const double* cst, const double* ci, double inv, double* h, int64_t n, cudaStream_t s);
 
 void count_launch(int n = 1);
 uint64_t launch_count();

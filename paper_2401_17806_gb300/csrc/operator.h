@@ -61,6 +61,8 @@ struct dgsl_operator {
   } sl;
   // workspace of dgsl_ns_step: vbar | c | Mbar c | vbar* (2 n each) | vhat* (2 nd npsi) | b (n)
   double* ns = nullptr;
+  // workspace of dgsl_advdiff_step: V (4 stages x 2 per trajectory) | fields (5 n) | ci | rhs | c* (n each)
+  double* ad = nullptr;
   std::vector<void*> allocs;
   int64_t device_bytes = 0;
   std::mutex mu;
@@ -153,6 +155,11 @@ struct dgsl_operator {
   double* ensure_ns() {
     if (!ns) ns = dalloc<double>((size_t)9 * d.n + (size_t)2 * d.nd * d.npsi);
     return ns;
+  }
+  // Workspace of dgsl_advdiff_step (caller holds mu, after ensure_sl).
+  double* ensure_advdiff() {
+    if (!ad) ad = dalloc<double>((size_t)8 * d.ne * sl.g.ng + (size_t)8 * d.n);
+    return ad;
   }
   // Semi-Lagrangian walk data and workspace for nf fields (caller holds mu).
   void ensure_sl(int nf) {

@@ -118,6 +118,9 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_sl_transport_imex": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dgsl_advdiff_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info),
+                                    C.c_void_p]),
     "dgsl_cg_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
@@ -325,6 +328,21 @@ class Operator:
             self.h, int(R), float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
             opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
             opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
+
+    def dgsl_advdiff_step(self, R, dt, alpha, vbar, c_in, c_out, opts=None, stream=None, check=True):
+        """One SL-IMEX advection-diffusion step (R = 0, 1, 2): vbar [2 * n_dof],
+        c_in, c_out [n_dof] float64 (may alias).  Returns the dgsl_solve_info of
+        the stage solves (1, 2 or 4)."""
+        if opts is None:
+            opts = dgsl_default_solve_opts()
+        ns = {0: 1, 1: 2, 2: 4}.get(int(R), 4)
+        infos = (dgsl_solve_info * 4)()
+        code = load().dgsl_advdiff_step(self.h, int(R), float(dt), float(alpha),
+                                        _dptr(vbar, "float64", 2 * self.n_dof), _dptr(c_in, "float64", self.n_dof),
+                                        _dptr(c_out, "float64", self.n_dof), C.byref(opts), infos, _stream(stream))
+        if check:
+            _check(code)
+        return list(infos)[:ns]
 
     def dgsl_ns_step(self, dt, nu, vhat_in, vhat_out, p_out=None, opts=None, stream=None, check=True):
         """One first-order semi-Lagrangian Navier-Stokes step; vhat [2 * n_dual]
