@@ -427,6 +427,21 @@ Sums read_sums(dgsl_operator* op, const double* dev_part, int nparts, cudaStream
 // One right-hand side.  Outer loop: r = b - A x in FP64 (assembled FP64
 // couplings); inner: CG on A d = r in FP64 (PREC_F64) or on the FP32 / BF16
 // couplings with FP32 vectors; x += d in FP64.
+// Solve options with the defaults filled in for NULL, checked, and checked
+// against the couplings the operator stores.  Returns DGSL_OK or the error.
+int resolve_solve_opts(const dgsl_operator* op, const dgsl_solve_opts* opts, dgsl_solve_opts& o) {
+  dgsl_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
+  if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
+    return fail(DGSL_EINVAL, "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI");
+  if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
+  if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
+  if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+  return DGSL_OK;
+}
+
 int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double* x, const dgsl_solve_opts& o,
               dgsl_solve_info* info, cudaStream_t s) {
   NvtxRange nvtx(kind == DGSL_SCHUR ? "dgsl_cg_solve Schur" : "dgsl_cg_solve Helmholtz");
@@ -550,16 +565,8 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
     if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
     if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
     dgsl_solve_opts o;
-    dgsl_default_solve_opts(&o);
-    if (opts) o = *opts;
-    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
-    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
-    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
-      return fail(DGSL_EINVAL, "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI");
+    if (int e = resolve_solve_opts(cop, opts, o)) return e;
     dgsl_operator* op = const_cast<dgsl_operator*>(cop);
-    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
-    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
-    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
     std::lock_guard<std::mutex> lock(op->mu);
     DGSL_CUDA(cudaSetDevice(op->d.device));
     op->ensure_work();
@@ -585,16 +592,8 @@ extern "C" int dgsl_ns_step(const dgsl_operator* cop, double dt, double nu, cons
       return fail(DGSL_EINVAL, "dt must be finite and > 0, nu finite and >= 0");
     if (!cop->d.G || !cop->d.Minv || !cop->d.Uloc) return fail(DGSL_EINVAL, "the step needs opts.factored");
     dgsl_solve_opts o;
-    dgsl_default_solve_opts(&o);
-    if (opts) o = *opts;
-    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
-    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
-    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
-      return fail(DGSL_EINVAL, "bad precond");
+    if (int e = resolve_solve_opts(cop, opts, o)) return e;
     dgsl_operator* op = const_cast<dgsl_operator*>(cop);
-    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
-    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
-    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
     std::lock_guard<std::mutex> lock(op->mu);
     DGSL_CUDA(cudaSetDevice(op->d.device));
     op->ensure_work();
@@ -659,16 +658,8 @@ extern "C" int dgsl_advdiff_step(const dgsl_operator* cop, int R, double dt, dou
     if (!(dt > 0.0) || !std::isfinite(dt) || !(alpha >= 0.0) || !std::isfinite(alpha))
       return fail(DGSL_EINVAL, "dt must be finite and > 0, alpha finite and >= 0");
     dgsl_solve_opts o;
-    dgsl_default_solve_opts(&o);
-    if (opts) o = *opts;
-    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
-    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
-    if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
-      return fail(DGSL_EINVAL, "bad precond");
+    if (int e = resolve_solve_opts(cop, opts, o)) return e;
     dgsl_operator* op = const_cast<dgsl_operator*>(cop);
-    if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
-    if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
-    if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
     std::lock_guard<std::mutex> lock(op->mu);
     DGSL_CUDA(cudaSetDevice(op->d.device));
     op->ensure_work();
@@ -880,15 +871,9 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
       return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: operator has " + std::to_string(cop->d.n) +
                                    " DOFs, above the fixed scratch limit of " + std::to_string(kNoAllocMaxDof));
     dgsl_solve_opts o;
-    dgsl_default_solve_opts(&o);
-    if (opts) o = *opts;
-    if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
-    if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    if (int e = resolve_solve_opts(cop, opts, o)) return e;
     if (o.precond != DGSL_PRECOND_NONE)
       return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: no preconditioner (its blocks do not fit the fixed scratch)");
-    if (!cop->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
-    if (o.precision == DGSL_PREC_F32_IR && !cop->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
-    if (o.precision == DGSL_PREC_BF16_IR && !cop->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     DGSL_CUDA(cudaSetDevice(cop->d.device));
     unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(cop->d.device));
