@@ -28,7 +28,7 @@ def _setup(N, p, seed):
     return op, conn, per, op.maps()["perm"], xy, tri
 
 
-@pytest.mark.parametrize("R,N,p", [(0, 6, 2), (1, 6, 3), (2, 5, 2)])
+@pytest.mark.parametrize("R,N,p", [(0, 6, 2), (1, 6, 3), (2, 5, 2), (1, 7, 1), (2, 4, 4)])
 def test_advdiff_step_parity(dgsl_lib, R, N, p):
     from paper_2401_17806_gb300 import dgsl
     op, conn, per, perm, xy, tri = _setup(N, p, 60 + N)
@@ -66,6 +66,10 @@ def test_advdiff_constant_and_arguments(dgsl_lib):
         with pytest.raises(dgsl.DgslError) as e:
             op.dgsl_advdiff_step(bad[0], bad[1], bad[2], vb, c, out)
         assert e.value.code == dgsl.EINVAL
+    with pytest.raises(dgsl.DgslError) as e:  # segments of ~10^8 cells: stopped at the cap
+        op.dgsl_advdiff_step(1, 1.0e6, 0.1, vb, c, out)
+    assert e.value.code == dgsl.ENOTCONV
+    op.dgsl_advdiff_step(1, 0.1, 0.1, vb, c, out)  # the context is still usable
 
 
 @pytest.mark.parametrize("R,order", [(1, 2.5), (2, 3.3)])
