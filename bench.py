@@ -539,7 +539,9 @@ def ns_leg(args):
     solve warm-started from the last step's pressure): steps per second,
     device-timed.  Then the temporal order on a 64 x 64, p = 2 mesh:
     the error against the exact decay exp(-8 pi^2 nu t) at t = 0.1 for dt =
-    0.05, 0.025, 0.0125 (nu = 0.01)."""
+    0.05, 0.025, 0.0125 (nu = 0.01).  Key "imex": the SL-IMEX stages
+    (dgsl_ns_imex_step) for R = 1, 2 timed the same way, and their temporal
+    order (R = 0, 1, 2) on 32 x 32, p = 3 with 2, 4, 8 and 16 steps."""
     import numpy as np
     import torch
     from paper_2401_17806_gb300 import build, dgsl, synth
@@ -586,6 +588,35 @@ def ns_leg(args):
         for _ in range(n):
             opo.dgsl_ns_step(T / n, nu, w, w, opts=o2)
         errs.append(float(torch.linalg.norm(w - ref) / torch.linalg.norm(ref)))
+    # the SL-IMEX stages (dgsl_ns_imex_step): time per step on the same mesh, order on 32 x 32, p = 3
+    imex = {}
+    for R in (1, 2):
+        v = tg_dual(op)
+        pr = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            op.dgsl_ns_imex_step(R, WORKLOAD["dt"], WORKLOAD["nu"], v, v, pr, opts=opts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = 0
+        for _ in range(args.steps):
+            its += sum(i.iters for i in op.dgsl_ns_imex_step(R, WORKLOAD["dt"], WORKLOAD["nu"], v, v, pr, opts=opts))
+        e1.record()
+        torch.cuda.synchronize()
+        imex["R%d" % R] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "cg_iters_per_step": its / args.steps}
+    op3 = dgsl.Operator(*synth.jittered_periodic_mesh(32, 3), 3, factored=True)
+    o3 = dgsl.solve_opts(tol=1e-11, precision=dgsl.PREC_F64, precond=dgsl.PRECOND_BLOCK_JACOBI)
+    w0 = tg_dual(op3)
+    ref3 = w0 * np.exp(-8.0 * np.pi ** 2 * nu * T)
+    for R in (0, 1, 2):
+        errs = []
+        for n in (2, 4, 8, 16):
+            w = w0.clone()
+            for _ in range(n):
+                op3.dgsl_ns_imex_step(R, T / n, nu, w, w, opts=o3)
+            errs.append(float(torch.linalg.norm(w - ref3) / torch.linalg.norm(ref3)))
+        imex.setdefault("temporal_order", {"mesh": "32x32, p=3", "nu": nu, "t": T,
+                                           "dt": [T / 2, T / 4, T / 8, T / 16]})["R%d" % R] = {
+            "rel_error": errs, "observed_order": [float(np.log2(errs[k] / errs[k + 1])) for k in range(3)]}
     print(json.dumps({
         "metric": "first-order semi-Lagrangian Navier-Stokes steps/s", "workload": "ns", "data": "synthetic",
         "value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
@@ -598,6 +629,7 @@ def ns_leg(args):
         "temporal_order": {"mesh": "64x64, p=2", "nu": nu, "t": T, "dt": [T / 2, T / 4, T / 8], "rel_error": errs,
                            "observed_order": [float(np.log2(errs[0] / errs[1])), float(np.log2(errs[1] / errs[2]))]},
         "clocks": clk,
+        "imex": imex,
     }))
 
 

@@ -382,6 +382,30 @@ int dgsl_ns_step(const dgsl_operator* op, double dt, double nu, const double* vh
                  double* vhat_out, double* p_out, const dgsl_solve_opts* opts,
                  dgsl_solve_info* info, void* stream);
 
+/* One semi-Lagrangian IMEX step of the incompressible Navier-Stokes
+ * equations (no temperature or gravity) with the tableaux of App. A,
+ * R = 0, 1, 2.  Stages as dgsl_advdiff_step for the two main-grid velocity
+ * components, starting from vbar^n = L_dm(vhat_in) (eq. d2m), with:
+ *  - the stage velocity of each trajectory V_s = vbar^E_s(x^E_s), where the
+ *    explicit stage field vbar^E_s is formed like the implicit stage value
+ *    with the explicit row a~_s and shifts c~_s - c_j (V_1 = vbar^n(x));
+ *  - per stage: the viscous solves (Mbar + a_ss dt nu K) vbar* = Mbar vbar^I
+ *    (eq. ad5), vhat* = L_md(vbar*) (eq. m2d), the pressure solve
+ *    S pi = G^T vhat* with S = (a_ss dt)^2 G^T Mhat^-1 G (eq. pressure_final)
+ *    and vhat_s = vhat* - (a_ss dt)^2 Mhat^-1 G pi (eq. nc.2);
+ *  - the stage flux Hhat_s = (vhat_s - L_md(vbar^I_s)) / (a_ss dt) on the dual
+ *    grid, shifted as its main-grid copy L_dm(Hhat_s);
+ *  - vhat_out = vhat_Ns (stiffly accurate tableaux).
+ * vhat_in, vhat_out: device double[2][n_dual] (may alias); p_out: device
+ * double[n_dof] or NULL (the last stage's pi; with opts->use_x0 its contents
+ * start the first pressure solve, and every later stage starts from the
+ * previous one); info: host array of 3 Ns (per stage: Helmholtz x, y,
+ * Schur) or NULL.  Needs an operator built with opts.factored.
+ * Synchronous.  Errors as dgsl_advdiff_step. */
+int dgsl_ns_imex_step(const dgsl_operator* op, int R, double dt, double nu, const double* vhat_in,
+                      double* vhat_out, double* p_out, const dgsl_solve_opts* opts,
+                      dgsl_solve_info* info, void* stream);
+
 /* ------------------------------------------------------------ advection-diffusion step */
 /* One semi-Lagrangian IMEX step of the advection-diffusion model (Sec. 3 and
  * its advection-diffusion subsection; tableaux of App. A, R = 0, 1, 2):

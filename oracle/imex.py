@@ -227,3 +227,97 @@ def advdiff_step(ops, conn: Connectivity, period, p, vbar, C, dt, alpha, R, max_
         Cs = OPS.direct_solve(Hm, ops.apply_Mbar(CI))
         H.append(((Cs - CI) / (A[s, s] * dt)).reshape(ne, nphi))
     return Cs
+
+
+def ns_imex_step(ops, conn: Connectivity, period, p, vhat, dt, nu, R, max_steps=4096):
+    """One SL-IMEX step of the incompressible Navier-Stokes equations (no
+    temperature or gravity) with the tableaux of App. A: vhat f64[2 * Nd *
+    Npsi] (component-major, natural order) -> (vhat^{n+1}, pressure of the
+    last stage).
+
+    Readings, extending those of advdiff_step to a velocity that changes
+    within the step (stages s = 1..Ns, explicit (A~, c~), implicit (A, c)):
+     - the main-grid velocity vbar^n = L_dm(vhat^n) (eq. d2m) is transported;
+     - the explicit stage velocity field is
+         vbar^E_s = proj[vbar^n(x - dt sum_{j<s} a~_{s,j} V_j)
+                         + sum_{j<s} dt a~_{s,j} Hbar_j(x - (c~_s - c_j) dt V_j)],
+       the same projection as the implicit stage value with the explicit
+       row, and the stage velocity of the trajectory from x is
+       V_s = vbar^E_s(x^E_s) (V_1 = vbar^n(x));
+     - the implicit stage value vbar^I_s is formed as in advdiff_step, each
+       component solves (Mbar + a_ss dt nu K) vbar* = Mbar vbar^I_s (eq. ad5),
+       vhat* = L_md(vbar*) (eq. m2d), the pressure solves S pi = G^T vhat* with
+       S = (a_ss dt)^2 G^T Mhat^-1 G (eq. pressure_final for the stage) and
+       vhat_s = vhat* - (a_ss dt)^2 Mhat^-1 G pi (eq. nc.2);
+     - the stage flux Hhat_s = (vhat_s - L_md(vbar^I_s)) / (a_ss dt) lives on
+       the dual grid, where the velocity is defined; its main-grid copy
+       Hbar_s = L_dm(Hhat_s) is the field that is shifted;
+     - stiffly accurate tableaux: vhat^{n+1} = vhat_Ns."""
+    from . import operators as OPS
+    nd, npsi, ne, nphi = ops.nd, ops.npsi, conn.n_tri, ops.nphi
+    At, bt, ct, A, b, c = tableau(R)
+    ns = len(b)
+    pts, w = SL.quadrature(p)
+    ng = len(w)
+    nbr, trans, back = SL.frames(conn, period)
+    X = B.triangle_points(conn.tri_xy, pts)
+    phi_g = B.eval_phi(p, pts)
+    Mbar, _ = main_mass(conn, p)
+    e1 = conn.tri_xy[:, 1] - conn.tri_xy[:, 0]
+    e2 = conn.tri_xy[:, 2] - conn.tri_xy[:, 0]
+    absJ = np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+
+    def project(vals):  # [2, Ne, Ng] -> [2, Ne, Nphi]
+        rhs = np.einsum("gl,g,kig->kil", phi_g, w, vals) * absJ[None, :, None]
+        return np.stack([np.linalg.solve(Mbar, rhs[k][..., None])[..., 0] for k in range(2)])
+
+    def at(field, i, x, d):  # field [2, Ne, Nphi] at x + d
+        y, cy, _ = locate_from(conn.tri_xy, nbr, trans, back, x, i, d, max_steps)
+        _, xi, eta = SL.barycentric(conn.tri_xy[cy], y)
+        return field[:, cy, :] @ B.eval_phi(p, np.array([[xi, eta]]))[0]
+
+    vh = np.asarray(vhat, dtype=np.float64).reshape(2, nd * npsi)
+    vn = np.stack([ops.d2m(vh[k]) for k in range(2)]).reshape(2, ne, nphi)
+    V = np.zeros((ns, ne, ng, 2))
+    Hbar = []
+
+    def stage_field(row, cs, s, with_diag):
+        """proj[vbar^n(x - dt sum_j row_j V_j) + sum_{j<s} dt row_j Hbar_j(x - (cs - c_j) dt V_j)]."""
+        vals = np.zeros((2, ne, ng))
+        for i in range(ne):
+            for g in range(ng):
+                x = X[i, g]
+                jmax = s + 1 if with_diag else s
+                d = -dt * sum(row[j] * V[j, i, g] for j in range(jmax)) if jmax else np.zeros(2)
+                v = at(vn, i, x, d)
+                for j in range(s):
+                    if row[j] != 0.0:
+                        v = v + dt * row[j] * at(Hbar[j], i, x, -(cs - c[j]) * dt * V[j, i, g])
+                vals[:, i, g] = v
+        return project(vals)
+
+    pr = None
+    vs = None
+    for s in range(ns):
+        # stage velocity of every trajectory
+        if s == 0:
+            for i in range(ne):
+                for g in range(ng):
+                    V[0, i, g] = at(vn, i, X[i, g], np.zeros(2))
+        else:
+            vE = stage_field(At[s], ct[s], s, False)
+            for i in range(ne):
+                for g in range(ng):
+                    d = -dt * sum(At[s, j] * V[j, i, g] for j in range(s))
+                    V[s, i, g] = at(vE, i, X[i, g], d)
+        vI = stage_field(A[s], c[s], s, True).reshape(2, -1)
+        h = A[s, s] * dt
+        Hm = ops.helmholtz_matrix(nu * h)
+        vst = np.stack([OPS.direct_solve(Hm, ops.apply_Mbar(vI[k])) for k in range(2)])
+        vhs = np.stack([ops.m2d(vst[k]) for k in range(2)]).ravel()
+        pr = OPS.schur_solve_direct(ops.schur_matrix(h), ops.G.T @ vhs)
+        vs = ops.velocity_update(vhs, pr, h * h).reshape(2, -1)
+        vIh = np.stack([ops.m2d(vI[k]) for k in range(2)])
+        Hh = (vs - vIh) / h
+        Hbar.append(np.stack([ops.d2m(Hh[k]) for k in range(2)]).reshape(2, ne, nphi))
+    return vs.ravel(), pr

@@ -692,8 +692,8 @@ extern "C" int dgsl_advdiff_step(const dgsl_operator* cop, int R, double dt, dou
         sg.a[j] = tab.ai[st][j];
         sg.shift[j] = c[st] - c[j];
       }
-      DGSL_CUDA(dgsl::launch_sl_advdiff_stage(op->sl.g, n, dt, sg, V, F, op->sl.cmono, ci, kSLMaxSteps, op->sl.err,
-                                              s));
+      DGSL_CUDA(dgsl::launch_sl_advdiff_stage(op->sl.g, n, n, dt, sg, V, F, op->sl.cmono, ci, kSLMaxSteps,
+                                              op->sl.err, s));
       DGSL_CUDA(launch_apply_assembled_f64(d, 0.0, 1.0, ci, rhs, s));
       DGSL_CUDA(cudaMemcpyAsync(cst, ci, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       const double add = tab.ai[st][st] * dt;
@@ -708,6 +708,126 @@ extern "C" int dgsl_advdiff_step(const dgsl_operator* cop, int R, double dt, dou
       return fail(DGSL_ENOTCONV, "a segment crossed more than " + std::to_string(kSLMaxSteps) + " cells");
     if (info)
       for (int k = 0; k < tab.ns; ++k) info[k] = inf[k];
+    if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "a solve did not converge" : "device wait timed out";
+    return worst;
+  });
+}
+
+extern "C" int dgsl_ns_imex_step(const dgsl_operator* cop, int R, double dt, double nu, const double* vhat_in,
+                                 double* vhat_out, double* p_out, const dgsl_solve_opts* opts, dgsl_solve_info* info,
+                                 void* stream) {
+  NvtxRange nvtx("dgsl_ns_imex_step");
+  DGSL_TRY({
+    check_dev(cop);
+    dgsl::SLTableau tab;
+    if (!dgsl::sl_tableau(R, tab)) return fail(DGSL_EINVAL, "R must be 0, 1 or 2");
+    if (!vhat_in || !vhat_out) return fail(DGSL_EINVAL, "vhat_in and vhat_out must be non-NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(nu >= 0.0) || !std::isfinite(nu))
+      return fail(DGSL_EINVAL, "dt must be finite and > 0, nu finite and >= 0");
+    if (!cop->d.G || !cop->d.Minv || !cop->d.Uloc) return fail(DGSL_EINVAL, "the step needs opts.factored");
+    dgsl_solve_opts o;
+    if (int e = resolve_solve_opts(cop, opts, o)) return e;
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    op->ensure_work();
+    op->ensure_sl(5);
+    const DevOp& d = op->d;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = d.n;
+    const int64_t nv = (int64_t)d.nd * d.npsi;
+    const int64_t nt = (int64_t)d.ne * op->sl.g.ng;
+    double* V = op->ensure_nsimex();  // [ns][nt][2] stage velocities
+    double* F = V + 8 * nt;           // [1 + ns][2][n]: vbar^n, Hbar_0, ..., Hbar_{ns-1}
+    double* vI = F + 10 * n;          // [2][n] stage value (also the explicit stage field)
+    double* vst = vI + 2 * n;         // [2][n] after the viscous solve
+    double* rhs = vst + 2 * n;        // [2][n]
+    double* b = rhs + 2 * n;          // [n] divergence
+    double* prs = b + n;              // [n] pressure scratch
+    double* tmp = prs + n;            // [n]
+    double* vhs = tmp + n;            // [2][nv] vhat*
+    double* vIh = vhs + 2 * nv;       // [2][nv] L_md(vI), then the stage flux Hhat
+    double* vs = vIh + 2 * nv;        // [2][nv] stage velocity vhat_s
+    double* pr = p_out ? p_out : prs;
+    DGSL_CUDA(cudaMemsetAsync(V, 0, (size_t)8 * nt * sizeof(double), s));
+    DGSL_CUDA(cudaMemsetAsync(op->sl.err, 0, sizeof(int), s));
+    // vbar^n = L_dm(vhat^n) (eq. d2m)
+    for (int k = 0; k < 2; ++k) {
+      DGSL_CUDA(launch_d2m_rhs(d, vhat_in + k * nv, tmp, s));
+      DGSL_CUDA(launch_mass_inv(d, tmp, F + k * n, 1, s));
+    }
+    double c[4] = {};
+    double ct[4] = {};
+    for (int i = 0; i < tab.ns; ++i)
+      for (int j = 0; j < 4; ++j) {
+        c[i] += tab.ai[i][j];
+        ct[i] += tab.at[i][j];
+      }
+    dgsl_solve_opts oh = o;
+    oh.use_x0 = 1;
+    dgsl_solve_opts osch = o;
+    osch.use_x0 = o.use_x0 && p_out ? 1 : 0;
+    int worst = DGSL_OK;
+    dgsl_solve_info inf[12];
+    for (int st = 0; st < tab.ns; ++st) {
+      // the stage velocity of every trajectory
+      dgsl::SLStage se;
+      se.s = st;
+      for (int j = 0; j < st; ++j) {
+        se.a[j] = tab.at[st][j];
+        se.shift[j] = ct[st] - c[j];
+      }
+      const double* field = F;  // vbar^n for the first stage
+      if (st > 0) {
+        for (int k = 0; k < 2; ++k)
+          DGSL_CUDA(dgsl::launch_sl_advdiff_stage(op->sl.g, n, 2 * n, dt, se, V, F + k * n, op->sl.cmono, vI + k * n,
+                                                  kSLMaxSteps, op->sl.err, s));
+        field = vI;
+      }
+      // (the two components are n apart in both F and vI)
+      DGSL_CUDA(dgsl::launch_sl_stage_velocity(op->sl.g, n, dt, se, field, V, op->sl.vmono, kSLMaxSteps, op->sl.err,
+                                               s));
+      // the implicit stage value
+      dgsl::SLStage si;
+      si.s = st;
+      for (int j = 0; j <= st; ++j) {
+        si.a[j] = tab.ai[st][j];
+        si.shift[j] = c[st] - c[j];
+      }
+      for (int k = 0; k < 2; ++k)
+        DGSL_CUDA(dgsl::launch_sl_advdiff_stage(op->sl.g, n, 2 * n, dt, si, V, F + k * n, op->sl.cmono, vI + k * n,
+                                                kSLMaxSteps, op->sl.err, s));
+      const double h = tab.ai[st][st] * dt;
+      // viscous solves (eq. ad5), back to the dual grid (eq. m2d), pressure (eq. pressure_final), update (eq. nc.2)
+      for (int k = 0; k < 2; ++k) {
+        DGSL_CUDA(launch_apply_assembled_f64(d, 0.0, 1.0, vI + k * n, rhs + k * n, s));
+        DGSL_CUDA(cudaMemcpyAsync(vst + k * n, vI + k * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const int r = solve_one(op, DGSL_HELMHOLTZ, nu * h, rhs + k * n, vst + k * n, oh, &inf[3 * st + k], s);
+        if (r != DGSL_OK && worst == DGSL_OK) worst = r;
+        DGSL_CUDA(launch_m2d(d, vst + k * n, vhs + k * nv, s));
+      }
+      DGSL_CUDA(launch_div(d, vhs, b, s));
+      const int r = solve_one(op, DGSL_SCHUR, h, b, pr, osch, &inf[3 * st + 2], s);
+      if (r != DGSL_OK && worst == DGSL_OK) worst = r;
+      osch.use_x0 = 1;  // later stages start from the last stage's pressure
+      DGSL_CUDA(launch_velocity_update(d, h * h, vhs, pr, vs, s));
+      if (st + 1 < tab.ns) {
+        // the stage flux Hhat_s = (vhat_s - L_md(vI)) / h and its main-grid copy Hbar_s = L_dm(Hhat_s)
+        for (int k = 0; k < 2; ++k) DGSL_CUDA(launch_m2d(d, vI + k * n, vIh + k * nv, s));
+        DGSL_CUDA(dgsl::launch_sl_flux(vs, vIh, 1.0 / h, vIh, 2 * nv, s));
+        for (int k = 0; k < 2; ++k) {
+          DGSL_CUDA(launch_d2m_rhs(d, vIh + k * nv, tmp, s));
+          DGSL_CUDA(launch_mass_inv(d, tmp, F + (int64_t)(1 + st) * 2 * n + k * n, 1, s));
+        }
+      }
+    }
+    DGSL_CUDA(cudaMemcpyAsync(vhat_out, vs, 2 * (size_t)nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    DGSL_CUDA(cudaMemcpyAsync(op->sl.h_err, op->sl.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DGSL_CUDA(cudaStreamSynchronize(s));
+    if (*op->sl.h_err)
+      return fail(DGSL_ENOTCONV, "a segment crossed more than " + std::to_string(kSLMaxSteps) + " cells");
+    if (info)
+      for (int k = 0; k < 3 * tab.ns; ++k) info[k] = inf[k];
     if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "a solve did not converge" : "device wait timed out";
     return worst;
   });

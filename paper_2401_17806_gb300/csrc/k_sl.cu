@@ -471,28 +471,84 @@ __global__ void k_sl_flux(const double* __restrict__ cst, const double* __restri
   if (i < n) h[i] = (cst[i] - ci[i]) * inv;
 }
 
+// V_s of every trajectory: the two-component field (monomials vmono
+// [cell][2][nphi]) at x - dt sum_{j<s} a[j] V_j, reached along the straight
+// segment; V [stages][trajectory][2].
 template <int P>
-static cudaError_t run_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
-                                     const double* fields, double* cmono, double* ci, int max_steps, int* err,
+__global__ void __launch_bounds__(128) k_sl_stage_velocity(SLDev g, double dt, SLStage st, double* __restrict__ V,
+                                                           const double* __restrict__ vmono, int max_steps, int* err) {
+  using D = SLDeg<P>;
+  constexpr int NPHI = D::NPHI, NG = D::NG;
+  const int64_t nt = (int64_t)g.ne * NG;
+  const int64_t tr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tr >= nt) return;
+  const int ti = (int)(tr / NG), gq = (int)(tr - (int64_t)ti * NG);
+  const double* T = g.tri + (int64_t)ti * 16;
+  const double xi0 = __ldg(g.pts + 2 * gq), eta0 = __ldg(g.pts + 2 * gq + 1);
+  double x = __ldg(T + 0) + xi0 * __ldg(T + 2) + eta0 * __ldg(T + 4);
+  double y = __ldg(T + 1) + xi0 * __ldg(T + 3) + eta0 * __ldg(T + 5);
+  double dx = 0.0, dy = 0.0;
+  for (int j = 0; j < st.s; ++j) {
+    dx = fma(st.a[j], V[2 * (j * nt + tr)], dx);
+    dy = fma(st.a[j], V[2 * (j * nt + tr) + 1], dy);
+  }
+  int cell = ti;
+  sl_walk_path(g, x, y, cell, 1.0, SLConstVel{dt * dx, dt * dy}, max_steps, err);
+  double xi, eta;
+  sl_ref(g, cell, x, y, xi, eta);
+  const double* a = vmono + (int64_t)cell * 2 * NPHI;
+  V[2 * (st.s * nt + tr)] = sl_poly<P>(a, xi, eta);
+  V[2 * (st.s * nt + tr) + 1] = sl_poly<P>(a + NPHI, xi, eta);
+}
+
+template <int P>
+static cudaError_t run_stage_velocity(const SLDev& g, int64_t fstride, double dt, const SLStage& st,
+                                      const double* field2, double* V, double* vmono, int max_steps, int* err,
+                                      cudaStream_t s) {
+  using D = SLDeg<P>;
+  const int64_t tv = (int64_t)2 * g.ne * D::NPHI;
+  k_sl_mono<D::NPHI><<<(int)((tv + 255) / 256), 256, 0, s>>>(field2, fstride, g.ne, 2, g.mono_c, vmono, 1);
+  const int64_t nt = (int64_t)g.ne * D::NG;
+  k_sl_stage_velocity<P><<<(int)((nt + 127) / 128), 128, 0, s>>>(g, dt, st, V, vmono, max_steps, err);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sl_stage_velocity(const SLDev& g, int64_t fstride, double dt, const SLStage& st,
+                                     const double* field2, double* V, double* vmono, int max_steps, int* err,
                                      cudaStream_t s) {
+  if (st.s < 0 || st.s > 3 || g.ne < 1 || !field2 || !V || !vmono) return cudaErrorInvalidValue;
+  switch (g.p) {
+    case 1: return run_stage_velocity<1>(g, fstride, dt, st, field2, V, vmono, max_steps, err, s);
+    case 2: return run_stage_velocity<2>(g, fstride, dt, st, field2, V, vmono, max_steps, err, s);
+    case 3: return run_stage_velocity<3>(g, fstride, dt, st, field2, V, vmono, max_steps, err, s);
+    case 4: return run_stage_velocity<4>(g, fstride, dt, st, field2, V, vmono, max_steps, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P>
+static cudaError_t run_advdiff_stage(const SLDev& g, int64_t n, int64_t fstride, double dt, const SLStage& st,
+                                     const double* V, const double* fields, double* cmono, double* ci, int max_steps,
+                                     int* err, cudaStream_t s) {
   using D = SLDeg<P>;
   const int nf = 1 + st.s;
   const int64_t tc = (int64_t)nf * g.ne * D::NPHI;
-  k_sl_mono<D::NPHI><<<(int)((tc + 255) / 256), 256, 0, s>>>(fields, n, g.ne, nf, g.mono_c, cmono, 0);
+  k_sl_mono<D::NPHI><<<(int)((tc + 255) / 256), 256, 0, s>>>(fields, fstride, g.ne, nf, g.mono_c, cmono, 0);
   k_sl_advdiff_stage<P><<<(g.ne + D::TPB - 1) / D::TPB, 128, 0, s>>>(g, n, dt, st, V, cmono, ci, max_steps, err);
   count_launch(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
-                                    const double* fields, double* cmono, double* ci, int max_steps, int* err,
-                                    cudaStream_t s) {
-  if (st.s < 0 || st.s > 3 || g.ne < 1 || !V || !fields || !cmono || !ci) return cudaErrorInvalidValue;
+cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, int64_t fstride, double dt, const SLStage& st,
+                                    const double* V, const double* fields, double* cmono, double* ci, int max_steps,
+                                    int* err, cudaStream_t s) {
+  if (st.s < 0 || st.s > 3 || g.ne < 1 || !V || !fields || !cmono || !ci || fstride < n) return cudaErrorInvalidValue;
   switch (g.p) {
-    case 1: return run_advdiff_stage<1>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
-    case 2: return run_advdiff_stage<2>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
-    case 3: return run_advdiff_stage<3>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
-    case 4: return run_advdiff_stage<4>(g, n, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 1: return run_advdiff_stage<1>(g, n, fstride, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 2: return run_advdiff_stage<2>(g, n, fstride, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 3: return run_advdiff_stage<3>(g, n, fstride, dt, st, V, fields, cmono, ci, max_steps, err, s);
+    case 4: return run_advdiff_stage<4>(g, n, fstride, dt, st, V, fields, cmono, ci, max_steps, err, s);
   }
   return cudaErrorInvalidValue;
 }

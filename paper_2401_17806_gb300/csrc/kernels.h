@@ -180,11 +180,17 @@ struct SLStage {
 };
 // ci = projection (eq. intstage) of C^n(x - dt sum_{j<=s} a[j] V_j) +
 // sum_{j<s} dt a[j] H_j(x - shift[j] dt V_j) over every Gauss point x;
-// fields [1 + s][n] = C^n, H_0, ..., H_{s-1}; V as launch_sl_stage_velocities;
-// cmono workspace [1 + s][ne][nphi].
-cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, double dt, const SLStage& st, const double* V,
-                                    const double* fields, double* cmono, double* ci, int max_steps, int* err,
-                                    cudaStream_t s);
+// fields: 1 + s fields of n values, fstride apart (C^n, H_0, ..., H_{s-1});
+// V as launch_sl_stage_velocities; cmono workspace [1 + s][ne][nphi].
+cudaError_t launch_sl_advdiff_stage(const SLDev& g, int64_t n, int64_t fstride, double dt, const SLStage& st,
+                                    const double* V, const double* fields, double* cmono, double* ci, int max_steps,
+                                    int* err, cudaStream_t s);
+// V_s (s = st.s) of every trajectory: the two-component main-grid field
+// field2 (components fstride apart) at x - dt sum_{j<s} st.a[j] V_j; vmono
+// workspace [ne][2][nphi].
+cudaError_t launch_sl_stage_velocity(const SLDev& g, int64_t fstride, double dt, const SLStage& st,
+                                     const double* field2, double* V, double* vmono, int max_steps, int* err,
+                                     cudaStream_t s);
 // h = (cst - ci) * inv, n values.
 cudaError_t launch_sl_flux(const double* cst, const double* ci, double inv, double* h, int64_t n, cudaStream_t s);
 

@@ -63,6 +63,9 @@ struct dgsl_operator {
   double* ns = nullptr;
   // workspace of dgsl_advdiff_step: V (4 stages x 2 per trajectory) | fields (5 n) | ci | rhs | c* (n each)
   double* ad = nullptr;
+  // workspace of dgsl_ns_imex_step: V (8 per trajectory) | fields (5 x 2 n) | vI, vst, rhs (2 n each) |
+  // b, pr, tmp (n each) | vhs, vIh, vs (2 nd npsi each)
+  double* nsi = nullptr;
   std::vector<void*> allocs;
   int64_t device_bytes = 0;
   std::mutex mu;
@@ -160,6 +163,12 @@ struct dgsl_operator {
   double* ensure_advdiff() {
     if (!ad) ad = dalloc<double>((size_t)8 * d.ne * sl.g.ng + (size_t)8 * d.n);
     return ad;
+  }
+  // Workspace of dgsl_ns_imex_step (caller holds mu, after ensure_sl).
+  double* ensure_nsimex() {
+    if (!nsi)
+      nsi = dalloc<double>((size_t)8 * d.ne * sl.g.ng + (size_t)19 * d.n + (size_t)6 * d.nd * d.npsi);
+    return nsi;
   }
   // Semi-Lagrangian walk data and workspace for nf fields (caller holds mu).
   void ensure_sl(int nf) {

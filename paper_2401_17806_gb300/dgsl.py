@@ -118,6 +118,9 @@ _SIGS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_sl_transport_imex": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dgsl_ns_imex_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info),
+                                    C.c_void_p]),
     "dgsl_advdiff_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info),
                                     C.c_void_p]),
@@ -328,6 +331,23 @@ class Operator:
             self.h, int(R), float(dt), _dptr(vbar, "float64", 2 * self.n_dof),
             opt(c, "float64", n_fields * self.n_dof), opt(cstar, "float64", n_fields * self.n_dof), int(n_fields),
             opt(foot, "float64", 2 * nt), opt(cell, "int32", nt), opt(steps, "int32", nt), _stream(stream)))
+
+    def dgsl_ns_imex_step(self, R, dt, nu, vhat_in, vhat_out, p_out=None, opts=None, stream=None, check=True):
+        """One SL-IMEX Navier-Stokes step (R = 0, 1, 2): vhat [2 * n_dual] float64
+        (may alias), p_out [n_dof] or None.  Returns the dgsl_solve_info of the
+        stage solves (per stage: Helmholtz x, Helmholtz y, Schur)."""
+        if opts is None:
+            opts = dgsl_default_solve_opts()
+        ns = {0: 1, 1: 2, 2: 4}.get(int(R), 4)
+        infos = (dgsl_solve_info * 12)()
+        code = load().dgsl_ns_imex_step(self.h, int(R), float(dt), float(nu),
+                                        _dptr(vhat_in, "float64", 2 * self.n_dual),
+                                        _dptr(vhat_out, "float64", 2 * self.n_dual),
+                                        _dptr(p_out, "float64", self.n_dof) if p_out is not None else None,
+                                        C.byref(opts), infos, _stream(stream))
+        if check:
+            _check(code)
+        return list(infos)[:3 * ns]
 
     def dgsl_advdiff_step(self, R, dt, alpha, vbar, c_in, c_out, opts=None, stream=None, check=True):
         """One SL-IMEX advection-diffusion step (R = 0, 1, 2): vbar [2 * n_dof],
