@@ -22,7 +22,7 @@ LIB = os.path.join(OUTDIR, "libdgsl.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 HOST_SOURCES = ["host.cpp"]
-CUDA_SOURCES = ["api.cu", "k_apply.cu", "k_cg.cu", "k_batch.cu", "k_batch_pc.cu", "k_sl.cu", "server.cu"]
+CUDA_SOURCES = ["api.cu", "steps.cu", "k_apply.cu", "k_cg.cu", "k_batch.cu", "k_batch_pc.cu", "k_sl.cu", "server.cu"]
 
 
 def _nvcc():
