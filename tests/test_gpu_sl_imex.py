@@ -163,3 +163,28 @@ def test_stage_transport_full_size_sampled(dgsl_lib):
         rhs = np.einsum("gl,g,ag->al", phi_g, w, vals[f]) * np.abs(area2)[:, None]
         ref = np.linalg.solve(Mbar, rhs[..., None])[..., 0]
         np.testing.assert_allclose(cstar[f][tris], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_smallest_mesh_long_trajectories(dgsl_lib):
+    """3 x 3 mesh (18 triangles), dt = 0.9: trajectories wrap around the
+    torus several times through the few periodic neighbours.  The walk of
+    Sec. 2.5 and the stage trajectories of R = 0, 1, 2 agree with the oracle."""
+    from test_gpu_sl import _run as run_walk
+    op, conn, per, perm = _setup(3, 2, 1)
+    X = B.triangle_points(conn.tri_xy, B.nodes(2))
+    vbar = np.stack(_tg(X[..., 0], X[..., 1])).reshape(2, -1)
+    fields = [synth.standard_normal(op.n_dof, 5)]
+    nf = np.stack([f.reshape(conn.n_tri, -1) for f in fields])
+    dt = 0.9
+    foot, cell, steps, cstar = run_walk(op, dt, vbar, fields)
+    fo, co, so, cso = SL.transport(conn, per, 2, vbar.reshape(2, conn.n_tri, -1), nf, dt)
+    assert so.max() >= 10
+    assert np.array_equal(cell, co) and np.array_equal(steps, so)
+    np.testing.assert_allclose(foot, fo, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(cstar, cso, rtol=0, atol=1e-11 * np.abs(cso).max())
+    for R in (0, 1, 2):
+        foot, cell, steps, cstar = _run(op, R, dt, vbar, fields)
+        fo, co, so, cso = IM.rk_transport(conn, per, 2, vbar.reshape(2, conn.n_tri, -1), nf, dt, R)
+        assert np.array_equal(cell, co)
+        np.testing.assert_allclose(foot, fo, rtol=0, atol=1e-11)
+        np.testing.assert_allclose(cstar, cso, rtol=0, atol=1e-11 * np.abs(cso).max())
