@@ -374,7 +374,11 @@ int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const 
  * govern the three solves (tolerance, precision, preconditioner); the
  * Helmholtz solves start from c, and the pressure solve starts from the
  * contents of p_out when opts->use_x0 is set and p_out is given (the last
- * step's pressure), else from 0.  info: host array of 3 or NULL (Helmholtz x,
+ * step's pressure), else from 0.  With opts->use_x0 == 2 and p_out it starts
+ * from the linear extrapolation 2 p^n - p^{n-1}: the operator keeps the
+ * pressure of the last step called this way (the first such call only
+ * records it).  Steps of another run on the same operator only make that
+ * guess worse; the result still meets opts->tol.  info: host array of 3 or NULL (Helmholtz x,
  * Helmholtz y, Schur).  Needs an operator built with opts.factored.
  * Synchronous.  Returns the first non-OK solve status, or DGSL_ENOTCONV if a
  * trajectory crossed more than 65536 cells. */

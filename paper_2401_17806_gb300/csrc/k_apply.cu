@@ -729,4 +729,20 @@ cudaError_t launch_sum_to_first(double* part, int nparts, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// y = 2 a - prev and prev = a, elementwise (y may be a): the linear
+// extrapolation of a quantity from its last two values.
+__global__ void k_extrapolate(const double* a, double* prev, double* y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double cur = a[i];
+  y[i] = 2.0 * cur - prev[i];
+  prev[i] = cur;
+}
+
+cudaError_t launch_extrapolate(const double* a, double* prev, double* y, int64_t n, cudaStream_t s) {
+  k_extrapolate<<<(int)((n + 255) / 256), 256, 0, s>>>(a, prev, y, n);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 }  // namespace dgsl

@@ -57,6 +57,8 @@ cudaError_t launch_velocity_update(const DevOp& op, double coef, const double* F
 // y = Mbar^-1 x (per triangle Mref^-1 x_i / A_i) for ncomp main fields of n values
 // (y must not alias x).
 cudaError_t launch_mass_inv(const DevOp& op, const double* x, double* y, int ncomp, cudaStream_t s);
+// y = 2 a - prev, then prev = a (n values; y may be a).
+cudaError_t launch_extrapolate(const double* a, double* prev, double* y, int64_t n, cudaStream_t s);
 
 // ---- vector helpers for the refinement loop
 // r = b - A x (FP64 assembled form, A = coefM Mbar + coefK K), optional mean

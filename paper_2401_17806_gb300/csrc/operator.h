@@ -59,8 +59,9 @@ struct dgsl_operator {
     int* err = nullptr;
     int* h_err = nullptr;  // pinned
   } sl;
-  // workspace of dgsl_ns_step: vbar | c | Mbar c | vbar* (2 n each) | vhat* (2 nd npsi) | b (n)
+  // workspace of dgsl_ns_step: vbar | c | Mbar c | vbar* (2 n each) | vhat* (2 nd npsi) | b (n) | p_prev (n)
   double* ns = nullptr;
+  bool ns_prev_valid = false;  // p_prev holds the pressure of the last step that asked for extrapolation
   // workspace of dgsl_advdiff_step: V (4 stages x 2 per trajectory) | fields (5 n) | ci | rhs | c* (n each)
   double* ad = nullptr;
   // workspace of dgsl_ns_imex_step: V (8 per trajectory) | fields (5 x 2 n) | vI, vst, rhs (2 n each) |
@@ -156,7 +157,7 @@ struct dgsl_operator {
   }
   // Workspace of dgsl_ns_step (caller holds mu).
   double* ensure_ns() {
-    if (!ns) ns = dalloc<double>((size_t)9 * d.n + (size_t)2 * d.nd * d.npsi);
+    if (!ns) ns = dalloc<double>((size_t)10 * d.n + (size_t)2 * d.nd * d.npsi);
     return ns;
   }
   // Workspace of dgsl_advdiff_step (caller holds mu, after ensure_sl).

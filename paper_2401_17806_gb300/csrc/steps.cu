@@ -69,7 +69,14 @@ extern "C" int dgsl_ns_step(const dgsl_operator* cop, double dt, double nu, cons
     double* pr = p_out ? p_out : vbar;  // (vbar is free again)
     dgsl_solve_opts osch = o;
     osch.use_x0 = o.use_x0 && p_out ? 1 : 0;  // warm start from the caller's last pressure
+    double* p_prev = b + n;
+    const bool extrap = o.use_x0 == 2 && p_out;
+    if (extrap && op->ns_prev_valid) DGSL_CUDA(launch_extrapolate(p_out, p_prev, p_out, n, s));  // 2 p^n - p^{n-1}
     const int st = solve_one(op, DGSL_SCHUR, dt, b, pr, osch, &inf[2], s);
+    if (extrap && !op->ns_prev_valid) {
+      DGSL_CUDA(cudaMemcpyAsync(p_prev, p_out, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      op->ns_prev_valid = true;
+    }
     if (st != DGSL_OK && worst == DGSL_OK) worst = st;
     DGSL_CUDA(launch_velocity_update(d, dt * dt, vhs, pr, vhat_out, s));
     DGSL_CUDA(cudaStreamSynchronize(s));

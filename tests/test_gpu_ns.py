@@ -106,3 +106,27 @@ def test_ns_step_pressure_warm_start(dgsl_lib):
     assert iw[2].iters < ic[2].iters
     assert float(torch.linalg.norm(warm_p - cold_p) / torch.linalg.norm(cold_p)) <= 1e-8
     assert float(torch.linalg.norm(warm_v - cold_v) / torch.linalg.norm(cold_v)) <= 1e-10
+
+
+def test_ns_step_extrapolated_pressure(dgsl_lib):
+    """use_x0 = 2: the pressure solve starts from 2 p^n - p^{n-1} (the operator
+    keeps the last pressure).  Four steps end at the same velocity as with the
+    last pressure as the start (both solved to 1e-12), and the last step's
+    pressure solve takes fewer iterations."""
+    from paper_2401_17806_gb300 import dgsl
+    X = None
+    res = {}
+    for mode in (1, 2):
+        op, _, _, _, _ = _setup(16, 2, 64)
+        if X is None:
+            X = op.node_coords(1)
+        u, w = _tg(X[:, 0], X[:, 1])
+        v = dev(np.concatenate([u, w]))
+        p = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
+        o = dgsl.solve_opts(tol=1e-12, precision=dgsl.PREC_F64, use_x0=mode)
+        for _ in range(4):
+            infos = op.dgsl_ns_step(0.01, 0.01, v, v, p, opts=o)
+        torch.cuda.synchronize()
+        res[mode] = (v.clone(), infos[2].iters)
+    assert float(torch.linalg.norm(res[2][0] - res[1][0]) / torch.linalg.norm(res[1][0])) <= 1e-9
+    assert res[2][1] < res[1][1], (res[1][1], res[2][1])
