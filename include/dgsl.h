@@ -155,6 +155,15 @@ enum { DGSL_MAIN = 0, DGSL_DUAL = 1 };
  * frame). */
 int dgsl_node_coords(const dgsl_operator* op, int grid, double* xy);
 
+/* The neighbour tables of the semi-Lagrangian walk (Sec. 2.5), host arrays
+ * in internal triangle order, each optional: nbr int32[n_tri][4] (the
+ * neighbours across local edges 0..2, then in bits 2k..2k+1 of the fourth
+ * word the local index of edge k in that neighbour) and trans
+ * double[n_tri][3][2] (the whole periods that carry a point of the triangle's
+ * frame into the neighbour's frame across local edge k).  Pure host call;
+ * also for host-only operators. */
+int dgsl_query_sl_tables(const dgsl_operator* op, int32_t* nbr, double* trans);
+
 /* Host FP64 copies of the blocks, internal edge order (any may be NULL):
  *   G    [n_edge][2 side][2 comp][n_phi m][n_phi k] = Q_{s,j}[L_s(m), k, comp]
  *        (eq. ad5.2 restricted to the dual nodes of side s)

@@ -204,6 +204,18 @@ int dgsl_query_maps(const dgsl_operator* op, dgsl_maps* m) {
   return DGSL_OK;
 }
 
+int dgsl_query_sl_tables(const dgsl_operator* op, int32_t* nbr, double* trans) {
+  if (!op) return fail(DGSL_EINVAL, "NULL argument");
+  DGSL_TRY({
+    const dgsl::SLHost h = dgsl::build_sl_host(op->hm, op->ro);
+    if (nbr) std::memcpy(nbr, h.nbr.data(), h.nbr.size() * sizeof(int32_t));
+    if (trans)
+      for (int i = 0; i < op->hm.ne; ++i)
+        for (int k = 0; k < 6; ++k) trans[(size_t)i * 6 + k] = h.tri[(size_t)i * 16 + 10 + k];
+    return DGSL_OK;
+  });
+}
+
 int dgsl_node_coords(const dgsl_operator* op, int grid, double* xy) {
   if (!op || !xy) return fail(DGSL_EINVAL, "NULL argument");
   if (grid != DGSL_MAIN && grid != DGSL_DUAL) return fail(DGSL_EINVAL, "grid must be DGSL_MAIN or DGSL_DUAL");

@@ -114,6 +114,7 @@ _SIGS = {
     "dgsl_sl_quadrature": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     "dgsl_ns_step": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.POINTER(dgsl_solve_opts), C.POINTER(dgsl_solve_info), C.c_void_p]),
+    "dgsl_query_sl_tables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_sl_transport": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_sl_transport_imex": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -252,6 +253,13 @@ class Operator:
         m = dgsl_maps(*[C.c_void_p(out[f].ctypes.data) for f, _ in dgsl_maps._fields_])
         _check(load().dgsl_query_maps(self.h, C.byref(m)))
         return out
+
+    def sl_tables(self):
+        """(nbr int32[n_tri, 4], trans float64[n_tri, 3, 2]) of the walk, internal order."""
+        nbr = np.zeros((self.n_tri, 4), np.int32)
+        trans = np.zeros((self.n_tri, 3, 2))
+        _check(load().dgsl_query_sl_tables(self.h, C.c_void_p(nbr.ctypes.data), C.c_void_p(trans.ctypes.data)))
+        return nbr, trans
 
     def node_coords(self, grid):
         n = self.n_dof if grid == MAIN else self.n_dual

@@ -108,3 +108,22 @@ def test_sl_quadrature_matches_the_oracle_rule(dgsl_lib):
         np.testing.assert_allclose(w, wo, rtol=0, atol=1e-15)
     with pytest.raises(dgsl.DgslError):
         dgsl.sl_quadrature(5)
+
+
+@pytest.mark.parametrize("N,seed", [(3, 0), (7, 1), (20, 2)])
+def test_sl_tables_bit_exact(dgsl_lib, N, seed):
+    """The walk's neighbour table, packed back indices and frame translations
+    (Sec. 2.5) equal the oracle's, bit for bit, after the RCM renumbering."""
+    from oracle import sl as SL
+    op, (xy, tri, per) = host_op(N, 2, seed)
+    nbr, trans = op.sl_tables()
+    perm = op.maps()["perm"]
+    c = OM.connectivity(xy, tri, per)
+    nbr_o, trans_o, back_o = SL.frames(c, per)
+    for ti in range(op.n_tri):
+        t = perm[ti]
+        for k in range(3):
+            assert perm[nbr[ti, k]] == nbr_o[t, k]
+            assert (int(nbr[ti, 3]) >> (2 * k)) & 3 == back_o[t, k]
+        np.testing.assert_array_equal(trans[ti], trans_o[t])
+    assert (nbr[:, 3] >> 6).max() == 0  # nothing above the three 2-bit fields
