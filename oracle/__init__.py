@@ -1,6 +1,9 @@
 """Oracle: a plain, slow FP64 CPU restatement of the staggered DG operators
 and solves of Tavelli & Boscheri (Sec. 2.1-2.4, eqs. D, ad5.2, Mi, Mj, u,
-ad5, pressure_final).
+ad5, pressure_final), of the semi-Lagrangian walk and transport (Sec. 2.5,
+sl.py), of the IMEX tableaux, stage trajectories and SL-IMEX steps of
+App. A and Sec. 3 (imex.py), and of the first-order Navier-Stokes step
+(ns.py).
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the C-ABI library,
 its Python binding, the bench's timed legs) may import or call this package;
