@@ -127,3 +127,24 @@ def test_sl_tables_bit_exact(dgsl_lib, N, seed):
             assert (int(nbr[ti, 3]) >> (2 * k)) & 3 == back_o[t, k]
         np.testing.assert_array_equal(trans[ti], trans_o[t])
     assert (nbr[:, 3] >> 6).max() == 0  # nothing above the three 2-bit fields
+
+
+def test_device_calls_reject_host_only_operators(dgsl_lib):
+    """The transport and time-step entries check the operator before they touch
+    any pointer: on a host-only operator each returns DGSL_ENODEVICE (the
+    pointers below are never dereferenced)."""
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, per = synth.jittered_periodic_mesh(4, 0)
+    op = dgsl.Operator(xy, tri, per, 2, host_only=True)
+    lib = dgsl.load()
+    fake = 8
+    codes = [
+        lib.dgsl_sl_transport(op.h, 0.1, fake, None, None, 0, None, None, None, None),
+        lib.dgsl_sl_transport_imex(op.h, 1, 0.1, fake, None, None, 0, None, None, None, None),
+        lib.dgsl_advdiff_step(op.h, 1, 0.1, 0.01, fake, fake, fake, None, None, None),
+        lib.dgsl_ns_step(op.h, 0.1, 0.01, fake, fake, None, None, None, None),
+        lib.dgsl_ns_imex_step(op.h, 1, 0.1, 0.01, fake, fake, None, None, None, None),
+    ]
+    assert codes == [dgsl.ENODEVICE] * 5
+    nbr, trans = op.sl_tables()  # the host query works on a host-only operator
+    assert nbr.shape == (op.n_tri, 4) and np.all(np.abs(trans) <= 1.0)
