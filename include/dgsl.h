@@ -99,6 +99,9 @@ typedef struct {
   int32_t store;       /* DGSL_STORE_* mask of block copies kept on device
                           (0 = F64|F32) */
   int32_t factored;    /* 1: also keep the per-edge G / Mhat^{-1} blocks */
+  void* stream;        /* cudaStream_t of the build's host-to-device copies
+                          (NULL: legacy default stream); the build returns
+                          after they have completed on it */
 } dgsl_build_opts;
 
 /* Builds connectivity (left/right triangles by first encounter), the RCM
@@ -343,26 +346,35 @@ int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* sta
 
 /* Same solve as dgsl_cg_solve (precond must be DGSL_PRECOND_NONE: the fixed
  * scratch has no room for the preconditioner's blocks; else DGSL_EINVAL), for
- * callers that cannot allocate device memory
- * when they solve: code that runs while a CUDA stream is being captured into a
- * graph, real-time loops and services that reserve all device memory at start-up
- * under a fixed budget, or hosts whose own allocator owns the GPU.  This entry
- * point calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
- * is one fixed device array inside the library (about 27.3 MB: thirteen vectors
- * of 262,144 doubles plus reduction slots), created when the library is loaded and
- * held by every GPU that loads it until the process exits.  The paper has no
- * counterpart; this is a deployment convenience.
+ * callers that cannot allocate device memory when they solve: real-time loops
+ * and services that reserve all device memory at start-up under a fixed budget
+ * (an allocation mid-run could fail or stall them), and hosts whose own
+ * allocator owns the GPU's memory.  This entry point calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its scratch is one fixed device array
+ * inside the library (about 28 MB: thirteen vectors of 262,144 doubles plus
+ * reduction slots) that every GPU which loads the library's code holds until
+ * the process exits.  The paper has no counterpart; this is a deployment
+ * convenience.
  *  - Limit: op's n_dof <= 262,144 (per right-hand side); larger operators are
  *    rejected with DGSL_EINVAL before anything runs.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture begins.
+ *  - The array is reserved on a device when the library's code is loaded there.
+ *    Under CUDA's default lazy module loading that happens at the first call of
+ *    this entry point on that device, which also looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current: make one call
+ *    (any small solve) before reserving the rest of the memory budget.
+ *  - It cannot run while its stream is being captured into a CUDA graph: the
+ *    refinement loop copies the residual norm to the host and synchronises the
+ *    stream after every step.  A call on a capturing stream (or one whose
+ *    capture state cannot be read) returns DGSL_EINVAL before enqueuing
+ *    anything, leaving the capture intact.
  *  - Every call on a device shares the one array, which keeps whatever the last
  *    call left in it; everything a solve needs zeroed is cleared by the call.
  *    Calls are serialized by a lock and return only after their GPU work has
  *    finished; two solves that overlapped on the GPU would race on the array.
- *  - Arguments, results and errors as dgsl_cg_solve, except that
- *    info->cg_kernel_ms is reported as 0 (no timing events are created). */
+ *  - The grids and reduction order are those of dgsl_cg_solve, so the result is
+ *    the same, bit for bit.  Arguments, results and errors as dgsl_cg_solve,
+ *    except that info->cg_kernel_ms is reported as 0 (no timing events are
+ *    created). */
 int dgsl_cg_solve_noalloc(const dgsl_operator* op, int kind, double coef, const double* b,
                           double* x, int n_rhs, const dgsl_solve_opts* opts,
                           dgsl_solve_info* info, void* stream);
@@ -506,6 +518,10 @@ typedef struct {
   int64_t submitted, completed, queued, in_flight;
   int64_t engine_launches;
   int64_t bytes_in_use;     /* workspace + operators of requests in flight */
+  int64_t admitted_running; /* requests published to an engine launch that was
+                               already running, and admitted and finished by it
+                               (continuous batching: they joined solves already
+                               on the device) */
 } dgsl_server_stats;
 
 int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** out);

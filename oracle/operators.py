@@ -181,19 +181,28 @@ def project_mean(v):
     return v - v.mean()
 
 
-def schur_solve_direct(S, b):
-    """Mean-zero solution of S x = Pi b.  The nullspace of S is span{1}, so
-    grounding DOF 0 (deleting its row and column) leaves a nonsingular SPD
-    system; its sparse LU solution (x_0 = 0) is then shifted to mean zero.
-    This equals the solution of the bordered system [[S, 1], [1^T, 0]]
-    without the fill-in of the dense border."""
+def schur_direct_solver(S):
+    """Factorises S once and returns b -> the mean-zero solution of
+    S x = Pi b.  The nullspace of S is span{1}, so grounding DOF 0 (deleting
+    its row and column) leaves a nonsingular SPD system; its sparse LU
+    solution (x_0 = 0) is then shifted to mean zero.  This equals the
+    solution of the bordered system [[S, 1], [1^T, 0]] without the fill-in of
+    the dense border."""
     S = sp.csr_matrix(S)
     n = S.shape[0]
-    rhs = project_mean(b)
-    A = S[1:, 1:].tocsc()
-    x = np.zeros(n)
-    x[1:] = spla.splu(A).solve(rhs[1:])
-    return project_mean(x)
+    lu = spla.splu(S[1:, 1:].tocsc())
+
+    def solve(b):
+        rhs = project_mean(b)
+        x = np.zeros(n)
+        x[1:] = lu.solve(rhs[1:])
+        return project_mean(x)
+    return solve
+
+
+def schur_solve_direct(S, b):
+    """Mean-zero solution of S x = Pi b (see schur_direct_solver)."""
+    return schur_direct_solver(S)(b)
 
 
 def direct_solve(A, b):
@@ -225,6 +234,55 @@ def cg(apply, b, tol=1e-12, maxit=100000, mean_zero=False):
         rr = rr_new
         it += 1
     return x, it, np.sqrt(rr) / bn
+
+
+def cg_lanczos_extremes(apply, b, iters, mean_zero=False):
+    """Extreme eigenvalues of A estimated from plain CG's own coefficients
+    (the Lanczos connection of CG; Saad, Iterative Methods for Sparse Linear
+    Systems, 2nd ed., Sec. 6.7.3): after k steps with step lengths alpha_j and
+    direction updates beta_j, the symmetric tridiagonal T_k with
+        T[j, j]   = 1/alpha_j + beta_{j-1}/alpha_{j-1}   (beta_{-1} = 0)
+        T[j, j+1] = sqrt(beta_j) / alpha_j
+    is the Lanczos matrix of A started from b, so its extreme eigenvalues
+    approach A's from inside: lambda_max from below, the smallest eigenvalue
+    on the Krylov space (the smallest nonzero one for the mean-zero Schur
+    operator) from above.  The recurrence stops once ||r|| <= 1e-13 ||b||:
+    beyond that its coefficients are rounding noise.  Returns (lambda_min,
+    lambda_max, k)."""
+    if mean_zero:
+        b = project_mean(b)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    stop = (1e-13 ** 2) * rr
+    alphas, betas = [], []
+    for _ in range(iters):
+        q = apply(p)
+        if mean_zero:
+            q = project_mean(q)
+        pq = p @ q
+        if not pq > 0.0:
+            break
+        alpha = rr / pq
+        r = r - alpha * q
+        rr_new = r @ r
+        beta = rr_new / rr
+        alphas.append(alpha)
+        betas.append(beta)
+        rr = rr_new
+        if rr <= stop:
+            break
+        p = r + beta * p
+    k = len(alphas)
+    diag = np.empty(k)
+    off = np.empty(max(0, k - 1))
+    for j in range(k):
+        diag[j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            off[j] = np.sqrt(betas[j]) / alphas[j]
+    T = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1]), k
 
 
 def block_jacobi_blocks(A, nphi):

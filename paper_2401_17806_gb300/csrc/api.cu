@@ -98,7 +98,7 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
   NvtxRange nvtx("dgsl_build_operators");
   if (!mesh || !out) return fail(DGSL_EINVAL, "mesh and out must be non-NULL");
   *out = nullptr;
-  dgsl_build_opts o{0, 0, 0, 0};
+  dgsl_build_opts o{0, 0, 0, 0, nullptr};
   if (opts) o = *opts;
   if (o.store == 0) o.store = DGSL_STORE_F64 | DGSL_STORE_F32;
   try {
@@ -120,6 +120,7 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
     for (int c = 0; c <= d.ncol; ++c) d.colour_offsets[c] = op->hm.colour_offsets[c];
     if (!o.host_only) {
       DGSL_CUDA(cudaSetDevice(o.device));
+      op->upload_stream = (cudaStream_t)o.stream;
       upload_dual_tables(o.device);
       // column rows padded to a multiple of 4 triangles: every 4-triangle group of
       // a row starts on a 16-byte boundary (bulk copies of tile indices)
@@ -151,7 +152,8 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
           for (int s = 0; s < 2; ++s) tedge[(size_t)hb.elr[2 * e + s] * 3 + hb.eloc[2 * e + s]] = 2 * e + s;
         d.tedge = op->upload(tedge);
       }
-      DGSL_CUDA(cudaDeviceSynchronize());
+      DGSL_CUDA(cudaStreamSynchronize(op->upload_stream));
+      op->upload_stream = nullptr;  // later uploads (first-use data) use the legacy default stream
     }
     if (o.host_only || o.factored) {
       op->hb = std::move(hb);
@@ -593,12 +595,17 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
 // dgsl_cg_solve, for callers that must not allocate device memory at solve
 // time.  Its scratch (residual, correction, search directions, matvec output,
 // per-CTA partial sums, barrier and result words) lives in one file-scope
-// device array of fixed size, allocated when the library is loaded and held by
-// every GPU that loads it until the process exits.
+// device array of fixed size.  The array belongs to this file's device code:
+// it is reserved on a device when that code is loaded there (with CUDA's lazy
+// module loading, the default, at the first call of this entry point on the
+// device) and stays reserved until the process exits.
 namespace {
 
 constexpr int64_t kNoAllocMaxDof = int64_t(1) << 18;   // 262,144 DOFs per right-hand side
-constexpr int kNoAllocMaxParts = 1024;                 // per-CTA partial slots
+// Per-CTA partial-sum slots: room for the grids dgsl_cg_solve uses (at most
+// 8 CTAs per SM) on a device of up to 256 SMs, so both entry points launch the
+// same grids and reduce in the same order.
+constexpr int kNoAllocMaxParts = 2048;
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxDof * sizeof(double);
 // CG vectors (cg_vec_bytes: 8 per-triangle padded vectors; at most 32/3 n doubles, for p = 1)
 constexpr size_t kNoAllocCgSlots = 11;
@@ -625,8 +632,8 @@ void* noalloc_scratch(int device) {
   return g_noalloc_ptr[device];
 }
 
-int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef, const double* b, double* x,
-                      const dgsl_solve_opts& o, dgsl_solve_info* info, cudaStream_t s) {
+int solve_one_noalloc(const DevOp& d, unsigned char* base, int max_parts, int kind, double coef, const double* b,
+                      double* x, const dgsl_solve_opts& o, dgsl_solve_info* info, cudaStream_t s) {
   const int64_t n = d.n;
   double* r64 = reinterpret_cast<double*>(base);
   double* d64 = reinterpret_cast<double*>(base + kNoAllocVecBytes);
@@ -634,7 +641,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   float* d32 = r32 + kNoAllocMaxDof;
   void* vbuf = base + 2 * kNoAllocVecBytes;
   double* part = reinterpret_cast<double*>(base + (2 + kNoAllocCgSlots) * kNoAllocVecBytes);
-  double* part2 = part + 8 * kNoAllocMaxParts;
+  double* part2 = part + 8 * kNoAllocMaxParts;  // fixed offsets; max_parts <= kNoAllocMaxParts slots used
   unsigned char* tail = reinterpret_cast<unsigned char*>(part2 + 2 * kNoAllocMaxParts);
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(tail);
   CGResult* res = reinterpret_cast<CGResult*>(tail + 256);
@@ -655,7 +662,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   const double coefM = kind == DGSL_SCHUR ? 0.0 : 1.0;
   const uint64_t timeout_ns = 10ull * 1000 * 1000 * 1000;
   int np = 0;
-  DGSL_CUDA(launch_sum2(b, n, part2, kNoAllocMaxParts, &np, s));
+  DGSL_CUDA(launch_sum2(b, n, part2, max_parts, &np, s));
   auto sb = sums(part2, np);
   const double b_mean = mean_zero ? sb.first / (double)n : 0.0;
   const double bnorm2 = mean_zero ? std::max(0.0, sb.second - (double)n * b_mean * b_mean) : sb.second;
@@ -668,9 +675,9 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
   cw.part = part;
   cw.bar = bar;
   cw.res = res;
-  cw.max_parts = kNoAllocMaxParts;
+  cw.max_parts = max_parts;
   for (;;) {
-    DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, r64, part2, kNoAllocMaxParts, &np, s));
+    DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, r64, part2, max_parts, &np, s));
     const double rnorm = std::sqrt(sums(part2, np).second);
     relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     if (bnorm == 0.0 || relres <= o.tol) break;
@@ -714,7 +721,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int kind, double coef
     }
   }
   if (mean_zero) {
-    DGSL_CUDA(launch_sum2(x, n, part2, kNoAllocMaxParts, &np, s));
+    DGSL_CUDA(launch_sum2(x, n, part2, max_parts, &np, s));
     DGSL_CUDA(launch_sum_to_first(part2, np, s));
     DGSL_CUDA(launch_remove_mean_f64(x, part2, n, s));
   }
@@ -748,13 +755,24 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     if (int e = resolve_solve_opts(cop, opts, o)) return e;
     if (o.precond != DGSL_PRECOND_NONE)
       return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: no preconditioner (its blocks do not fit the fixed scratch)");
+    // The refinement loop reads the residual norm back to the host after every
+    // step, which a stream that is being captured cannot do: refuse before
+    // anything is enqueued, so the caller's capture stays intact.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return fail(DGSL_EINVAL,
+                  "dgsl_cg_solve_noalloc: the stream is being captured (or the capture state cannot be read); "
+                  "this solve synchronises with the host every refinement step and cannot be captured");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     DGSL_CUDA(cudaSetDevice(cop->d.device));
+    const int max_parts = cg_max_blocks(cop->d, 0);
+    if (max_parts > kNoAllocMaxParts)
+      return fail(DGSL_EINVAL, "dgsl_cg_solve_noalloc: the device has more SMs than the fixed scratch serves");
     unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(cop->d.device));
     int worst = DGSL_OK;
     for (int k = 0; k < n_rhs; ++k) {
-      int st = solve_one_noalloc(cop->d, base, kind, coef, b + (size_t)k * cop->d.n, x + (size_t)k * cop->d.n, o,
-                                 info ? info + k : nullptr, (cudaStream_t)stream);
+      int st = solve_one_noalloc(cop->d, base, max_parts, kind, coef, b + (size_t)k * cop->d.n,
+                                 x + (size_t)k * cop->d.n, o, info ? info + k : nullptr, (cudaStream_t)stream);
       if (st != DGSL_OK && worst == DGSL_OK) worst = st;
     }
     if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";

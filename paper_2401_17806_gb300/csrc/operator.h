@@ -119,10 +119,16 @@ struct dgsl_operator {
     device_bytes += (int64_t)bytes;
     return static_cast<T*>(p);
   }
+  // Stream of host-to-device copies: the build's stream (dgsl_build_opts.stream)
+  // while dgsl_build_operators runs, the legacy default stream afterwards.
+  cudaStream_t upload_stream = nullptr;
   template <class T>
   T* upload(const std::vector<T>& v) {
     T* p = dalloc<T>(v.size());
-    if (!v.empty()) DGSL_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!v.empty()) {
+      DGSL_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, upload_stream));
+      DGSL_CUDA(cudaStreamSynchronize(upload_stream));  // v may be a temporary
+    }
     return p;
   }
   ~dgsl_operator() {

@@ -335,7 +335,9 @@ struct dgsl_server {
   int published = 0;                      // slots published to the current launch
   std::vector<uint64_t> slot_ticket;      // [kMaxSlots]
   std::vector<char> collected;            // [kMaxSlots]
+  std::vector<char> slot_late;            // [kMaxSlots] published while the launch was already running
   int64_t submitted = 0, completed = 0, launches = 0;
+  int64_t admitted_running = 0;           // late slots the running engine admitted and finished
 
   // Device bytes of op not yet charged to the budget.
   int64_t op_cost(const dgsl_operator* op) const {
@@ -418,6 +420,7 @@ struct dgsl_server {
       q.state = RQ_ADMITTED;
       R.inbox_h->slots[published] = fill_desc(q.r, o, ws, q.ticket, q.held);
       slot_ticket[published] = q.ticket;
+      slot_late[published] = running ? 1 : 0;
       ++published;
       ++added;
       queue.pop_front();
@@ -447,6 +450,7 @@ struct dgsl_server {
       Request& q = reqs[slot_ticket[i]];
       info_from(R.done_h[i], &q.info);
       collected[i] = 1;
+      if (slot_late[i]) ++admitted_running;  // a completion means the engine admitted the slot
       finish(q);
     }
   }
@@ -486,6 +490,7 @@ extern "C" int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** ou
     s->arena.init(base, want);
     s->slot_ticket.assign(kMaxSlots, 0);
     s->collected.assign(kMaxSlots, 0);
+    s->slot_late.assign(kMaxSlots, 0);
     dgsl_server* raw = s.get();
     s->th = std::thread([raw] { raw->loop(); });
     *out = s.release();
@@ -582,6 +587,7 @@ extern "C" int dgsl_server_get_stats(dgsl_server* srv, dgsl_server_stats* out) {
   out->in_flight = srv->submitted - srv->completed - (int64_t)srv->queue.size();
   out->engine_launches = srv->launches;
   out->bytes_in_use = srv->bytes_in_use;
+  out->admitted_running = srv->admitted_running;
   return DGSL_OK;
 }
 

@@ -39,7 +39,7 @@ class dgsl_mesh(C.Structure):
 
 class dgsl_build_opts(C.Structure):
     _fields_ = [("host_only", C.c_int32), ("device", C.c_int32), ("store", C.c_int32),
-                ("factored", C.c_int32)]
+                ("factored", C.c_int32), ("stream", C.c_void_p)]
 
 
 class dgsl_info(C.Structure):
@@ -84,7 +84,8 @@ class dgsl_engine_opts(C.Structure):
 
 class dgsl_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
-                ("in_flight", C.c_int64), ("engine_launches", C.c_int64), ("bytes_in_use", C.c_int64)]
+                ("in_flight", C.c_int64), ("engine_launches", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("admitted_running", C.c_int64)]
 
 
 _LIB = None
@@ -211,14 +212,15 @@ def dgsl_default_solve_opts():
 class Operator:
     """Owning handle of one built operator (``dgsl_build_operators``)."""
 
-    def __init__(self, xy, tri, period, p, host_only=False, device=0, store=0, factored=False):
+    def __init__(self, xy, tri, period, p, host_only=False, device=0, store=0, factored=False, stream=None):
         lib = load()
         self._xy = np.ascontiguousarray(xy, dtype=np.float64)
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
         m = dgsl_mesh(self._xy.shape[0], self._xy.ctypes.data_as(C.POINTER(C.c_double)),
                       self._tri.shape[0], self._tri.ctypes.data_as(C.POINTER(C.c_int32)),
                       (C.c_double * 2)(float(period[0]), float(period[1])))
-        o = dgsl_build_opts(int(host_only), int(device), int(store), int(factored))
+        o = dgsl_build_opts(int(host_only), int(device), int(store), int(factored),
+                            _stream(stream).value if stream is not None else None)
         h = C.c_void_p()
         _check(lib.dgsl_build_operators(C.byref(m), int(p), C.byref(o), C.byref(h)))
         self.h = h

@@ -54,26 +54,40 @@ def test_c1_manufactured_fp64_to_1e12(dgsl_lib):
     assert abs(x.sum()) <= 1e-12 * np.abs(x).sum()
 
 
+EPS64 = 2.0 ** -52
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("N,p", [(8, 2), (20, 3), (12, 4)])
 def test_schur_solve_parity(dgsl_lib, prec, N, p):
+    """Residual against the oracle's operator, and the error bar: <= 1e-10
+    wherever kappa * eps64 <= 1e-11 (kappa of the projected operator by dense
+    eigh), reached by solving to relres <= 1e-10 / kappa; elsewhere the error
+    is reported with kappa and bounded by kappa times the residual."""
     from paper_2401_17806_gb300 import dgsl
     op, orc, m = _setup(N, p, 2)
     dt = 1e-3
     b = synth.standard_normal(op.n_dof, 31)
-    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b, tol=1e-12, precision=prec)
-    assert info.status == dgsl.OK, info.status
-    assert info.relres <= 1e-12
     S = orc.schur_matrix(dt)
+    ev = np.linalg.eigvalsh(S.toarray())
+    kappa = ev[-1] / ev[1]
+    strict = kappa * EPS64 <= 1e-11
+    tol = max(1e-10 / kappa, 4e-15) if strict else 1e-12
+    x, info, _ = _solve(op, m, dgsl.SCHUR, dt, b, tol=tol, precision=prec)
+    # below 1e-13 the FP64 refinement may stop at its rounding floor first
+    assert info.status == dgsl.OK or (info.status == dgsl.ENOTCONV and info.relres <= 1e-13), info.status
+    assert info.relres <= max(tol, 1e-13)
     pb = OP.project_mean(b)
-    ev = np.linalg.eigvalsh(S.toarray()) if op.n_dof <= 5000 else None
-    kappa = ev[-1] / ev[1] if ev is not None else 1e6
-    # the oracle's residual also contains the operator parity (~1e-13 relative),
-    # amplified by ||x|| / ||b|| <= kappa / ||S||
-    assert np.linalg.norm(pb - S @ x) / np.linalg.norm(pb) <= max(2e-12, 1e-13 * kappa)
+    res = np.linalg.norm(pb - S @ x) / np.linalg.norm(pb)
+    # the oracle's residual also holds the operator parity (~1e-13 relative)
+    assert res <= max(2e-12, 1e-13 * kappa)
     xd = OP.schur_solve_direct(S, b)
-    # error bound: kappa * residual (kappa of the projected operator)
-    assert rel(x, xd) <= max(1e-10, 10 * kappa * 1e-12)
+    err = rel(x, xd)
+    print(f"SCHUR_ERRBAR N={N} p={p} prec={prec} kappa={kappa:.3e} tol={tol:.1e} relres={res:.3e} err={err:.3e}")
+    if strict:
+        assert err <= 1e-10, (err, kappa)
+    else:
+        assert err <= 10 * kappa * max(res, EPS64), (err, kappa)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -166,8 +180,11 @@ def test_full_size_solve_sampled_residual(dgsl_lib):
     Sx = OP.sampled_rows(conn, p, x, ids, dt * dt)
     r = b64.reshape(-1, op.n_phi)[ids] - Sx
     # a global relative residual of 1e-10 bounds the sampled block's norm by
-    # ||r||; compare against the same sample of b
+    # ||r|| (rigorous); and a residual spread over the whole mesh gives the
+    # sample about the global ratio: allow 5x for the sampling spread
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b64)
+    bs = b64.reshape(-1, op.n_phi)[ids]
+    assert np.linalg.norm(r) <= 5e-10 * np.linalg.norm(bs)
 
 
 def test_bf16_couplings_refined_to_fp64(dgsl_lib):

@@ -47,4 +47,8 @@ def test_max_size_sampled_rows_and_solve(dgsl_lib):
     xs_nat = to_natural(xs.cpu().numpy(), m["perm"], op.n_phi)
     hx = OP.sampled_rows(conn, p, xs_nat, ids, 1e-4, 1.0)
     bs = x64.reshape(-1, op.n_phi)[ids]
-    assert rel(hx, bs) <= 1e-8  # sampled rows of the residual; the whole residual is 1e-10 of |b|
+    # rigorous: the sampled residual is part of the whole, <= 1e-10 ||b||
+    assert np.linalg.norm(hx - bs) <= 1e-10 * np.linalg.norm(x64)
+    # a residual spread over the mesh gives the sample about the global ratio
+    # (5x allowed for the sampling spread)
+    assert rel(hx, bs) <= 5e-10

@@ -16,6 +16,7 @@ from oracle import basis as B
 from oracle import fields as OF
 from oracle import imex as IM
 from oracle import mesh as OM
+from oracle import operators as OP
 from oracle import sl as SL
 from paper_2401_17806_gb300 import synth
 
@@ -265,3 +266,83 @@ def test_ns_imex_second_order_on_the_taylor_green_vortex():
             v, _ = IM.ns_imex_step(ops, conn, per, 3, v, T / n, nu, 1)
         errs.append(np.linalg.norm(v - ref) / np.linalg.norm(ref))
     assert np.log2(errs[0] / errs[1]) > 2.2, errs
+
+
+def _translate_project(conn, per, p, delta):
+    """Brute-force matrix of c -> proj[c(x + delta)] for main-grid scalar
+    fields (eq. intstage projection of the field evaluated at the Gauss points
+    moved by delta, each point located by testing every triangle)."""
+    from oracle.assemble import main_mass
+    pts, w = SL.quadrature(p)
+    nphi = B.n_phi(p)
+    X = B.triangle_points(conn.tri_xy, pts)
+    phi_g = B.eval_phi(p, pts)                          # [ng, nphi]
+    Mbar, _ = main_mass(conn, p)
+    n = conn.n_tri * nphi
+    T = np.zeros((n, n))
+    for i in range(conn.n_tri):
+        e1 = conn.tri_xy[i, 1] - conn.tri_xy[i, 0]
+        e2 = conn.tri_xy[i, 2] - conn.tri_xy[i, 0]
+        absJ = abs(e1[0] * e2[1] - e1[1] * e2[0])
+        E = np.zeros((len(w), n))                       # point values as a function of c
+        for g in range(len(w)):
+            cell, y = SL.locate(conn.tri_xy, per, X[i, g] + delta)[0]
+            _, xi, eta = SL.barycentric(conn.tri_xy[cell], y)
+            E[g, cell * nphi:(cell + 1) * nphi] = B.eval_phi(p, np.array([[xi, eta]]))[0]
+        rows = np.linalg.solve(Mbar[i], (phi_g.T * w) @ E * absJ)
+        T[i * nphi:(i + 1) * nphi] = rows
+    return T
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_ns_imex_linearised_about_a_uniform_flow_is_the_stage_recurrence(R):
+    """About a uniform velocity U every trajectory is the straight line
+    x - tau dt U, so the step's derivative in a perturbation w is linear
+    algebra: per stage s (implicit tableau (A, c) of App. A)
+      w^I_s = T(c_s) w^n + sum_{j<s} dt a_{s,j} T(c_s - c_j) H_j,
+      (Mbar + a_ss dt nu K) w* = Mbar w^I_s,  w^_* = L_md w*,
+      S pi = G^T w^_*,  w^_s = w^_* - (a_ss dt)^2 Mhat^-1 G pi,
+      H_s = L_dm[(w^_s - L_md w^I_s) / (a_ss dt)],
+    with T(tau) the brute-force translation by -tau dt U and projection.
+    The oracle's step at U + eps w must agree with U + eps L(w) to O(eps)
+    (measured 1e-7 at eps = 1e-7, allowed 1e-5):
+    a wrong shift c_s - c_j or a wrong stage flux changes L(w) at O(1), a
+    wrong a_{s,j} by about its own relative error (1e-4 in one row is
+    detected)."""
+    conn, per, ops = _advdiff_setup(4, 2)
+    p, dt, nu = 2, 0.05, 0.02
+    U = np.array([0.3, -0.2])
+    nv = ops.nd * ops.npsi
+    Uhat = np.concatenate([np.full(nv, U[0]), np.full(nv, U[1])])
+    w = synth.standard_normal(2 * nv, 17)
+    eps = 1e-7
+    v1, _ = IM.ns_imex_step(ops, conn, per, p, Uhat + eps * w, dt, nu, R)
+    numeric = (v1 - Uhat) / eps
+    _, _, _, A, _, c = IM.tableau(R)
+    ns = len(c)
+    Tm = {}
+
+    def T(tau):
+        key = round(float(tau), 15)
+        if key not in Tm:
+            Tm[key] = _translate_project(conn, per, p, -tau * dt * U)
+        return Tm[key]
+
+    wh = w.reshape(2, nv)
+    wn = np.stack([ops.d2m(wh[k]) for k in range(2)])
+    Hs = []
+    ws = None
+    for s in range(ns):
+        wI = np.stack([T(c[s]) @ wn[k] + sum(dt * A[s, j] * (T(c[s] - c[j]) @ Hs[j][k]) for j in range(s))
+                       for k in range(2)])
+        h = A[s, s] * dt
+        Hm = ops.helmholtz_matrix(nu * h)
+        wst = np.stack([OP.direct_solve(Hm, ops.apply_Mbar(wI[k])) for k in range(2)])
+        whs = np.concatenate([ops.m2d(wst[k]) for k in range(2)])
+        pi = OP.schur_solve_direct(ops.schur_matrix(h), ops.G.T @ whs)
+        ws = ops.velocity_update(whs, pi, h * h).reshape(2, nv)
+        Hh = (ws - np.stack([ops.m2d(wI[k]) for k in range(2)])) / h
+        Hs.append(np.stack([ops.d2m(Hh[k]) for k in range(2)]))
+    lin = ws.ravel()
+    print("LINEARISED", R, np.linalg.norm(numeric - lin) / np.linalg.norm(lin))
+    assert np.linalg.norm(numeric - lin) <= 1e-5 * np.linalg.norm(lin), np.linalg.norm(numeric - lin) / np.linalg.norm(lin)
