@@ -34,8 +34,7 @@ METRIC = "Schur-CG DOF*iters/s"
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per matrix row per CG iteration of the persistent
 # CG kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# over a 200-iteration launch, 256x256, p = 3, FP32 couplings; the capture and
-# command are summarised in profiles/k_cg_f32_256x256_p3.md).  Keyed by (p,
+# over a 200-iteration launch, 256x256, p = 3, FP32 couplings).  Keyed by (p,
 # precision); a kernel change invalidates it.
 NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 171.1}
 
@@ -940,10 +939,65 @@ def oracle_cg_rate(orc, b, iters):
     return orc.n * it / el, it, el
 
 
+def host_cpu_info():
+    """Cores this process may run on (os.sched_getaffinity) and the CPU model
+    (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return cores, model or platform.processor() or platform.machine()
+
+
+def _oracle_worker(iters):
+    """One forked worker: the oracle's CG for a fixed number of iterations on
+    the operator built by the parent (shared copy-on-write)."""
+    rate, it, el = oracle_cg_rate(_ORACLE[0], _ORACLE[1], iters)
+    return _ORACLE[0].n * it, el
+
+
+_ORACLE = []
+
+
+def oracle_all_cores(orc, b, iters, cores):
+    """DOF*iterations/s of `cores` single-threaded copies of the oracle's CG
+    running at once (forked after the operator is built; this process never
+    touches the GPU): the host's whole throughput on independent solves."""
+    import multiprocessing as mp
+    _ORACLE[:] = [orc, b]
+    ctx = mp.get_context("fork")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [1] * cores)          # warm every worker
+        t = time.perf_counter()
+        res = pool.map(_oracle_worker, [iters] * cores)
+        el = time.perf_counter() - t
+    return sum(w for w, _ in res) / el
+
+
 def cpu_leg_main(args):
+    """Host-only subprocess: the oracle on one thread and on every core."""
     orc, b = oracle_setup(args.N, args.p)
-    rate, it, el = oracle_cg_rate(orc, b, args.cpu_iters)
-    print(json.dumps({"value": rate, "iters": it, "seconds": el, "n_dof": int(orc.n)}))
+    rate1, it, el = oracle_cg_rate(orc, b, args.cpu_iters)
+    cores, model = host_cpu_info()
+    rate_all = oracle_all_cores(orc, b, args.cpu_iters, cores) if cores > 1 else rate1
+    print(json.dumps({"value": rate1, "iters": it, "seconds": el, "n_dof": int(orc.n), "cores": cores,
+                      "cpu_model": model, "value_all_cores": rate_all}))
 
 
 def run_cpu_baseline(args):
@@ -956,10 +1010,13 @@ def run_cpu_baseline(args):
     except Exception as e:  # reported, never fatal to the GPU number
         return {"value": None, "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
                 "sample": f"failed: {type(e).__name__}"}
-    return {"value": out["value"], "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
+    return {"value": out["value_all_cores"], "unit": "DOF*iters/s", "cores": out["cores"], "kind": "oracle",
+            "cpu_model": out["cpu_model"],
+            "single_thread": {"value": out["value"], "cores": 1},
             "sample": (f"{out['iters']} FP64 CG iterations of the Schur solve on the same "
-                       f"{args.N}x{args.N}, p={args.p} mesh ({out['n_dof']} DOF), scipy/numpy "
-                       f"single-threaded, operator build excluded")}
+                       f"{args.N}x{args.N}, p={args.p} mesh ({out['n_dof']} DOF) per worker, the oracle's "
+                       f"scipy/numpy code single-threaded in each of {out['cores']} forked workers at once "
+                       f"(all cores of os.sched_getaffinity) and alone on one thread; operator build excluded")}
 
 
 def reference_main(args):
@@ -967,27 +1024,32 @@ def reference_main(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
     orc, b = oracle_setup(args.N, args.p)
-    for _ in range(args.warmup):
-        oracle_cg_rate(orc, b, 2)
-    t = time.perf_counter()
-    dof_iters = 0
-    for _ in range(args.steps):
-        _, it, _ = oracle_cg_rate(orc, b, args.cpu_iters)
-        dof_iters += orc.n * it
-    el = time.perf_counter() - t
+    cores, model = host_cpu_info()
+    import multiprocessing as mp
+    _ORACLE[:] = [orc, b]
+    ctx = mp.get_context("fork")            # this process never touches the GPU
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker, [2] * cores)
+        t = time.perf_counter()
+        dof_iters = 0
+        for _ in range(args.steps):
+            dof_iters += sum(w for w, _ in pool.map(_oracle_worker, [args.cpu_iters] * cores))
+        el = time.perf_counter() - t
     value = dof_iters / el
     sample = (f"each step: {args.cpu_iters} FP64 CG iterations of the Schur solve on the "
-              f"{args.N}x{args.N}, p={args.p} mesh, single thread")
+              f"{args.N}x{args.N}, p={args.p} mesh in each of {cores} single-threaded forked workers at once")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF*iters/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args), "N": args.N, "p": args.p, "n_dof": int(orc.n)},
-        "cpu_baseline": {"value": value, "unit": "DOF*iters/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "DOF*iters/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": model, "sample": sample},
         "e2e": {"value": value, "unit": "DOF*iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 

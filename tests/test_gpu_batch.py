@@ -183,7 +183,9 @@ def test_server_continuous_batching(problems):
                 bd = torch.tensor(to_internal(b, perm, op.n_phi), device="cuda")
                 x = torch.full_like(bd, np.nan)
                 bufs.append((k, bd, x))
-                torch.cuda.synchronize()
+                # only this stream: a device-wide synchronize would wait for the
+                # running engine itself and serialise the submissions
+                torch.cuda.current_stream().synchronize()
                 tickets.append(srv.dgsl_submit(dgsl.request(op, kind, coef, bd, x)))
             time.sleep(0.002)
         done = {}
