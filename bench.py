@@ -57,12 +57,16 @@ def parse_args(argv=None):
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-precond", action="store_true",
                     help="skip the block-Jacobi preconditioned run of the same stage")
+    ap.add_argument("--no-mg", action="store_true",
+                    help="skip the multigrid preconditioned run of the same stage")
     ap.add_argument("--no-sl", action="store_true",
                     help="skip the semi-Lagrangian transport of the stage's velocity")
     ap.add_argument("--sl-dt", type=float, default=0.01)
     ap.add_argument("--sl-reps", type=int, default=100,
                     help="sl workload: transport calls per timed step")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns", "advdiff"], default="stage",
+    ap.add_argument("--c3-degrees", type=str, default="2,4")
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns", "advdiff", "c3"],
+                    default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
                          "launch capped at --cg-iters iterations (the case the profiles capture)")
@@ -325,6 +329,30 @@ def gpu_leg(args, rank, world, local):
                          iters_total=sum(i.iters for i in b_infos),
                          kern_ms=sum(i.cg_kernel_ms for i in b_infos),
                          relres_max=max(i.relres for i in b_infos))
+    # ---- the same stage with the two-level multigrid preconditioned CG (an
+    # extension); the first run builds and keeps the hierarchies of both systems
+    if not args.no_mg:
+        om = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=st.opts.precision, precond=dgsl.PRECOND_MULTIGRID)
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            st.run(stream, om)
+        stream.synchronize()
+        setup_s = time.time() - t0
+        barrier()
+        l1 = dgsl.dgsl_launch_count()
+        m_infos = []
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                m_infos += st.run(stream, om)
+            ev1.record(stream)
+        stream.synchronize()
+        ms_ = sum(i.iters for k, i in enumerate(m_infos) if k % 3 == 0)
+        res["mg"] = dict(ms=ev0.elapsed_time(ev1), schur_iters=ms_ / args.steps,
+                         helm_iters=(sum(i.iters for i in m_infos) - ms_) / args.steps,
+                         refinements=sum(i.refinements for i in m_infos) / args.steps,
+                         relres_max=max(i.relres for i in m_infos), first_run_s=setup_s,
+                         launches_per_step=(dgsl.dgsl_launch_count() - l1) / args.steps)
     # ---- semi-Lagrangian transport of the stage's main-grid velocity (two
     # components) by itself over dt, on the same mesh (Sec. 2.5, eq. intstage)
     if not args.no_sl:
@@ -383,6 +411,65 @@ def cg_leg(args):
     kind = "block-Jacobi preconditioned " if args.precond else ""
     print(json.dumps({"workload": f"one {kind}FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
                       "grid": info.grid, "us_per_iter": 1e3 * info.cg_kernel_ms / max(1, info.iters)}))
+
+
+def c3_leg(args):
+    """The precision configuration: 1024 x 1024 mesh, p = 2 and p = 4, Fourier
+    right-hand side (32 modes, |k| <= 16, amplitude ~ |k|^-2, dt = 1e-3), the
+    Schur system solved to relative residual 1e-10 under FP64 refinement with
+    FP32 and with BF16 couplings (multigrid preconditioned PCG), and the
+    persistent CG kernel's cost per iteration with each coupling type (one
+    launch capped at --cg-iters iterations)."""
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    peak, peak_src = measured_hbm_peak()
+    N = args.N if args.N != WORKLOAD["N"] else 1024
+    out = []
+    for p in [int(v) for v in args.c3_degrees.split(",")]:
+        xy, tri, per = synth.jittered_periodic_mesh(N, WORKLOAD["seed"])
+        t0 = time.time()
+        op = dgsl.Operator(xy, tri, per, p, store=dgsl.STORE_F64 | dgsl.STORE_F32 | dgsl.STORE_BF16)
+        build_s = time.time() - t0
+        b = fourier_rhs(op, 11, WORKLOAD["dt"])
+        for prec, name, cb in ((dgsl.PREC_F32_IR, "f32", 4), (dgsl.PREC_BF16_IR, "bf16", 2)):
+            entry = {"p": p, "couplings": name, "n_dof": op.n_dof, "operator_build_s": build_s}
+            # persistent CG kernel alone (plain, capped): the HBM roofline
+            r = torch.tensor(synth.standard_normal(op.n_dof, 1), device="cuda")
+            x = torch.zeros_like(r)
+            oc = dgsl.solve_opts(tol=1e-30, max_iters=args.cg_iters, max_refine=1, precision=prec)
+            for _ in range(2):
+                ic = op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], r, x, opts=oc, check=False)[0]
+            per_row = bytes_per_row_iter(op.n_phi, cb, 4)
+            us = 1e3 * ic.cg_kernel_ms / max(1, ic.iters)
+            gbs = op.n_dof * per_row / (us * 1e-6) / 1e9
+            entry["k_cg"] = {"us_per_iter": us, "bytes_per_row_iter": per_row, "achieved_gbs": gbs,
+                             "frac": gbs / peak, "peak": peak, "peak_source": peak_src, "grid": ic.grid}
+            # the full solve with the multigrid preconditioner
+            om = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=prec, precond=dgsl.PRECOND_MULTIGRID)
+            x.zero_()
+            t0 = time.time()
+            op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], b, x, opts=om, check=False)   # builds the hierarchy
+            torch.cuda.synchronize()
+            first_s = time.time() - t0
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            im = op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], b, x, opts=om, check=False)[0]
+            ev1.record()
+            torch.cuda.synchronize()
+            entry["multigrid_solve"] = {"status": "converged" if im.status == dgsl.OK else f"status {im.status}",
+                                        "iters": im.iters, "refinements": im.refinements, "relres": im.relres,
+                                        "ms": ev0.elapsed_time(ev1), "first_solve_s": first_s,
+                                        "dof_iters_per_s": op.n_dof * im.iters / (ev0.elapsed_time(ev1) * 1e-3)}
+            out.append(entry)
+            print(json.dumps(entry), file=sys.stderr, flush=True)
+        del op
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"precision: {N}x{N} mesh, Schur solve to 1e-10 under FP64 refinement",
+                      "data": "synthetic", "results": out}))
 
 
 def sl_flops(p, nf):
@@ -1087,6 +1174,9 @@ def main():
     if args.workload == "cg":
         cg_leg(args)
         return
+    if args.workload == "c3":
+        c3_leg(args)
+        return
     if args.workload == "sl":
         sl_leg(args)
         return
@@ -1185,6 +1275,19 @@ def main():
             "max_relres": bj["relres_max"],
             "kernel_achieved_gbs": ach, "kernel_frac": ach / peak if peak else None,
             "bytes_per_row_iter": per_row_bj,
+        }
+    if "mg" in res:
+        mg = res["mg"]
+        line["multigrid"] = {
+            "what": "same stage, PCG with the two-level multigrid preconditioner (block-Jacobi smoother, "
+                    "P1 vertex coarse space, smoothed-aggregation V-cycle; extension)",
+            "ms_per_step": mg["ms"] / args.steps,
+            "stage_speedup": (ms / args.steps) / (mg["ms"] / args.steps),
+            "speedup_vs_fp64_cg_stage": (res["fp64"]["ms"] / (mg["ms"] / args.steps)) if "fp64" in res else None,
+            "schur_iters_per_step": mg["schur_iters"], "helmholtz_iters_per_step": mg["helm_iters"],
+            "refinements_per_step": mg["refinements"], "max_relres": mg["relres_max"],
+            "hierarchy_build_and_first_stage_s": mg["first_run_s"],
+            "kernel_launches_per_step": mg["launches_per_step"],
         }
     if "sl" in res:
         sl = res["sl"]

@@ -288,8 +288,13 @@ enum {
 
 enum {
   DGSL_PRECOND_NONE = 0,         /* plain CG, as the paper runs it (default) */
-  DGSL_PRECOND_BLOCK_JACOBI = 1  /* CG preconditioned by the inverse N_phi x N_phi
+  DGSL_PRECOND_BLOCK_JACOBI = 1, /* CG preconditioned by the inverse N_phi x N_phi
                                     diagonal blocks of A (one per triangle) */
+  DGSL_PRECOND_MULTIGRID = 2     /* PCG with a two-level multigrid preconditioner:
+                                    damped block-Jacobi smoothing and a continuous
+                                    P1 vertex coarse space solved by one
+                                    smoothed-aggregation V-cycle (see
+                                    dgsl_apply_multigrid) */
 };
 
 typedef struct {
@@ -325,7 +330,11 @@ typedef struct {
  * builds P on first use for each (kind, coef, precision) and keeps the blocks
  * of the last four such systems (N_phi values per row, rounded up to 4 in
  * FP32 or 2 in FP64; about 48 / 80 bytes per DOF at p = 3); DGSL_EINVAL if a
- * diagonal block is not positive definite.  For DGSL_SCHUR, b is projected to mean zero and x
+ * diagonal block is not positive definite.  With precond =
+ * DGSL_PRECOND_MULTIGRID the inner solve is PCG with the two-level
+ * preconditioner of dgsl_apply_multigrid (built on first use per system; the
+ * inner iterations then stay nearly constant as the mesh is refined).  For
+ * DGSL_SCHUR, b is projected to mean zero and x
  * is returned with sum(x) = 0 (coefficient space).  b, x: device
  * double[n_rhs][n_dof] in internal order; info: host array [n_rhs] or NULL.
  * Blocks the calling thread until the solves finish (it reads the status
@@ -333,6 +342,44 @@ typedef struct {
  * side missed tol within max_iters. */
 int dgsl_cg_solve(const dgsl_operator* op, int kind, double coef, const double* b, double* x,
                   int n_rhs, const dgsl_solve_opts* opts, dgsl_solve_info* info, void* stream);
+
+/* The two-level multigrid preconditioner M of DGSL_PRECOND_MULTIGRID (an
+ * extension: the paper runs CG unpreconditioned, with iteration counts that
+ * grow like 1/h; the operators are those of eq. pressure_final and eq. ad5).
+ * For A = S (kind DGSL_SCHUR, dt = coef) or H (DGSL_HELMHOLTZ, nu_dt = coef):
+ *   x1 = 0.7 D^-1 r,   x2 = x1 + Pc V(Pc^T (r - A x1)),
+ *   z  = x2 + 0.7 D^-1 (r - A x2),
+ * D = blockdiag of A's N_phi x N_phi diagonal blocks; Pc interpolates
+ * continuous piecewise-linear functions on the mesh vertices at each
+ * triangle's nodes (vertices numbered by first appearance over the triangles
+ * in internal order); V is one V(1,1)-cycle of smoothed aggregation on
+ * A_0 = Pc^T A Pc: greedy two-pass aggregation on the mesh-edge graph of the
+ * vertices (then on the aggregate graphs), prolongations
+ * P = T - (4/3 / lambda_G) diag(A)^-1 A T (lambda_G the Gershgorin bound of
+ * diag(A)^-1 A), Galerkin levels down to <= 256 DOFs, damped Jacobi
+ * smoothing (weight 4/3 / lambda_G), and a dense coarsest inverse (for S the
+ * mean-zero pseudo-inverse).  The operator builds the hierarchy on first use
+ * per (kind, coef, precision) and keeps the last four.
+ * dgsl_apply_multigrid applies z = M r once: precision DGSL_PREC_F64 with
+ * double r, z and FP64 couplings; DGSL_PREC_F32_IR (FP32 couplings) or
+ * DGSL_PREC_BF16_IR (BF16 couplings) with float r, z; device vectors [n_dof]
+ * in internal order.  Synchronous.  DGSL_EINVAL if a block of D or the
+ * coarsest operator is not positive definite. */
+int dgsl_apply_multigrid(const dgsl_operator* op, int kind, double coef, int precision, const void* r,
+                         void* z, void* stream);
+
+typedef struct {
+  int32_t n_levels;       /* coarse levels, the vertex level first, the dense one last */
+  int32_t n_vertices;     /* DOFs of the vertex level */
+  int32_t sizes[16];      /* DOFs of each level */
+} dgsl_mg_info;
+/* The hierarchy of dgsl_apply_multigrid for (kind, coef) (integer data, for
+ * checks): info; cvid (host int32[n_tri][3], natural triangle order, or NULL):
+ * the vertex-level DOF of each triangle vertex; agg (host int32, or NULL):
+ * the aggregate of every DOF of levels 0 .. n_levels-2, concatenated.  The
+ * aggregation depends on the mesh only.  Synchronous. */
+int dgsl_query_multigrid(const dgsl_operator* op, int kind, double coef, dgsl_mg_info* info, int32_t* cvid,
+                         int32_t* agg);
 
 void dgsl_default_solve_opts(dgsl_solve_opts* opts);
 

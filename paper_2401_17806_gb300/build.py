@@ -21,8 +21,9 @@ OUTDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUTDIR, "libdgsl.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-HOST_SOURCES = ["host.cpp"]
-CUDA_SOURCES = ["api.cu", "steps.cu", "k_apply.cu", "k_cg.cu", "k_batch.cu", "k_batch_pc.cu", "k_sl.cu", "server.cu"]
+HOST_SOURCES = ["host.cpp", "mg_host.cpp"]
+CUDA_SOURCES = ["api.cu", "steps.cu", "k_apply.cu", "k_cg.cu", "k_batch.cu", "k_batch_pc.cu", "k_sl.cu", "server.cu",
+                "k_mg.cu"]
 
 
 def _nvcc():

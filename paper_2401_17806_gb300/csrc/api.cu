@@ -441,8 +441,8 @@ int resolve_solve_opts(const dgsl_operator* op, const dgsl_solve_opts* opts, dgs
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return fail(DGSL_EINVAL, "bad solve options");
   if (o.precision < DGSL_PREC_F64 || o.precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
-  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
-    return fail(DGSL_EINVAL, "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI");
+  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI && o.precond != DGSL_PRECOND_MULTIGRID)
+    return fail(DGSL_EINVAL, "precond must be DGSL_PRECOND_NONE, DGSL_PRECOND_BLOCK_JACOBI or DGSL_PRECOND_MULTIGRID");
   if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
   if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
   if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
@@ -480,6 +480,8 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
   std::unique_ptr<dgsl_operator::Work::Precond, void (*)(dgsl_operator::Work::Precond*)> hold(
       held, dgsl_operator::release_precond);
   const dgsl::PrecondOp* pre = held ? &held->op : nullptr;
+  auto* mgh = o.precond == DGSL_PRECOND_MULTIGRID ? op->acquire_mg(coefK, coefM, ptype, s) : nullptr;
+  std::unique_ptr<dgsl_operator::MGEntry, void (*)(dgsl_operator::MGEntry*)> hold_mg(mgh, dgsl_operator::release_mg);
   for (;;) {
     DGSL_CUDA(launch_residual_f64(d, coefK, coefM, mean_zero, b, x, b_mean, w.r64, w.part2, w.max_parts, &nparts, s));
     Sums sr = read_sums(op, w.part2, nparts, s);
@@ -505,7 +507,22 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
     const double need = 0.5 * o.tol / relres;
     int grid = 0;
     DGSL_CUDA(cudaEventRecord(w.ev0, s));
-    if (o.precision == DGSL_PREC_F64) {
+    if (mgh) {
+      // multigrid PCG: FP64 on the FP64 couplings, else FP32 vectors on the
+      // FP32 or BF16 couplings of a scaled residual
+      dgsl::MGResult mr;
+      if (o.precision == DGSL_PREC_F64) {
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r64, w.d64, std::max(need, 1e-15), budget, s, &mr));
+      } else {
+        DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, std::max(o.inner_tol, need)), budget,
+                               s, &mr));
+      }
+      w.h_res->iters = mr.iters;
+      w.h_res->status = 0;
+      w.h_res->rr0 = mr.rr0;
+      w.h_res->rr = mr.rr;
+    } else if (o.precision == DGSL_PREC_F64) {
       const double stop_rel = std::max(need, 1e-15);
       DGSL_CUDA(launch_cg_f64(d, coefK, coefM, mean_zero, w.d64, w.r64, pre, stop_rel, budget, cw, timeout_ns, s,
                               &grid));
@@ -517,7 +534,7 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
                               cw, timeout_ns, s, &grid));
     }
     DGSL_CUDA(cudaEventRecord(w.ev1, s));
-    DGSL_CUDA(cudaMemcpyAsync(w.h_res, w.res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
+    if (!mgh) DGSL_CUDA(cudaMemcpyAsync(w.h_res, w.res, sizeof(CGResult), cudaMemcpyDeviceToHost, s));
     DGSL_CUDA(cudaStreamSynchronize(s));
     const CGResult cr = *w.h_res;
     {
@@ -585,6 +602,75 @@ extern "C" int dgsl_cg_solve(const dgsl_operator* cop, int kind, double coef, co
     }
     if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";
     return worst;
+  });
+}
+
+// ------------------------------------------------------------ multigrid preconditioner
+namespace {
+int mg_kind_coefs(int kind, double coef, double& coefK, double& coefM) {
+  if (kind != DGSL_SCHUR && kind != DGSL_HELMHOLTZ) return fail(DGSL_EINVAL, "kind must be DGSL_SCHUR or DGSL_HELMHOLTZ");
+  if (!(coef >= 0.0) || !std::isfinite(coef)) return fail(DGSL_EINVAL, "coef must be finite and >= 0");
+  coefK = kind == DGSL_SCHUR ? coef * coef : coef;
+  coefM = kind == DGSL_SCHUR ? 0.0 : 1.0;
+  if (kind == DGSL_SCHUR && coefK == 0.0) return fail(DGSL_EINVAL, "the Schur operator needs dt > 0");
+  return DGSL_OK;
+}
+using MGHold = std::unique_ptr<dgsl_operator::MGEntry, void (*)(dgsl_operator::MGEntry*)>;
+}  // namespace
+
+extern "C" int dgsl_apply_multigrid(const dgsl_operator* cop, int kind, double coef, int precision, const void* r,
+                                    void* z, void* stream) {
+  DGSL_TRY({
+    check_dev(cop);
+    if (!r || !z) return fail(DGSL_EINVAL, "r and z must be non-NULL");
+    double coefK = 0.0;
+    double coefM = 0.0;
+    if (int e = mg_kind_coefs(kind, coef, coefK, coefM)) return e;
+    if (precision < DGSL_PREC_F64 || precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
+    const int type = precision == DGSL_PREC_F64 ? 1 : precision == DGSL_PREC_BF16_IR ? 2 : 0;
+    if (!cop->d.K64) return fail(DGSL_EINVAL, "the multigrid setup needs the FP64 couplings");
+    if ((type == 0 && !cop->d.K32) || (type == 2 && !cop->d.K16))
+      return fail(DGSL_EINVAL, "the operator lacks the couplings of this precision");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    auto* e = op->acquire_mg(coefK, coefM, type, (cudaStream_t)stream);
+    MGHold hold(e, dgsl_operator::release_mg);
+    DGSL_CUDA(dgsl::mg_apply(e->sys.get(), op->d, r, z, (cudaStream_t)stream));
+    return DGSL_OK;
+  });
+}
+
+extern "C" int dgsl_query_multigrid(const dgsl_operator* cop, int kind, double coef, dgsl_mg_info* info,
+                                    int32_t* cvid, int32_t* agg) {
+  DGSL_TRY({
+    check_dev(cop);
+    double coefK = 0.0;
+    double coefM = 0.0;
+    if (int e = mg_kind_coefs(kind, coef, coefK, coefM)) return e;
+    if (!cop->d.K64) return fail(DGSL_EINVAL, "the multigrid setup needs the FP64 couplings");
+    dgsl_operator* op = const_cast<dgsl_operator*>(cop);
+    std::lock_guard<std::mutex> lock(op->mu);
+    DGSL_CUDA(cudaSetDevice(op->d.device));
+    auto* e = op->acquire_mg(coefK, coefM, 1, nullptr);
+    MGHold hold(e, dgsl_operator::release_mg);
+    const dgsl::MGHost& h = dgsl::mg_sys_host(e->sys.get());
+    if ((int)h.lv.size() > 16) return fail(DGSL_EINVAL, "more than 16 levels");
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->n_levels = (int32_t)h.lv.size();
+      info->n_vertices = h.nv;
+      for (size_t l = 0; l < h.lv.size(); ++l) info->sizes[l] = h.lv[l].A.n;
+    }
+    if (cvid)
+      for (int t = 0; t < op->d.ne; ++t)
+        for (int m = 0; m < 3; ++m) cvid[(size_t)op->hm.perm[t] * 3 + m] = h.cvid[(size_t)t * 3 + m];
+    if (agg) {
+      size_t o = 0;
+      for (size_t l = 0; l + 1 < h.lv.size(); ++l)
+        for (int32_t a : h.lv[l].agg) agg[o++] = a;
+    }
+    return DGSL_OK;
   });
 }
 

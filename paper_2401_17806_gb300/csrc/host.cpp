@@ -295,6 +295,7 @@ HostMesh build_mesh(const dgsl_mesh& m) {
   const int ne = hm.ne;
   const double Px = m.period[0], Py = m.period[1];
   hm.txy.resize((size_t)ne * 6);
+  hm.tri_v.assign(m.tri, m.tri + 3 * (size_t)ne);
   for (int t = 0; t < ne; ++t) {
     int v[3];
     for (int k = 0; k < 3; ++k) {

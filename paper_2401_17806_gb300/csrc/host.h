@@ -38,6 +38,7 @@ struct HostMesh {
   int nv = 0, ne = 0, nd = 0;
   double period[2] = {1.0, 1.0};
   std::vector<double> txy;             // [ne][3][2] unwrapped vertices
+  std::vector<int32_t> tri_v;          // [ne][3] vertex ids as given, natural numbering
   std::vector<int32_t> edge_vtx, lr;   // [nd][2], natural numbering
   std::vector<uint8_t> loc;            // [nd][2]
   std::vector<int8_t> shift;           // [nd][2]

@@ -703,6 +703,22 @@ static void run_build_precond(const DevOp& op, double coefK, double coefM, int t
   }
 }
 
+// The inverse diagonal blocks alone (the multigrid smoother's D^-1), in the
+// vector type: FP64 (vec_double) or FP32, in the interleaved layout of P.
+cudaError_t launch_block_jacobi_vec(const DevOp& op, double coefK, double coefM, int vec_double, void* out, int* bad,
+                                    cudaStream_t s) {
+  if (!op.K64 || op.ne < 1 || !out || !bad) return cudaErrorInvalidValue;
+  const int g = (op.ne + 63) / 64;
+  DGSL_DISPATCH_P(op.p, (void)NPSI;
+                  if (vec_double) k_block_jacobi<NPHI, double><<<g, 64, 0, s>>>(op.K64, op.area, op.Mref, op.ne, op.n,
+                                                                                coefK, coefM, static_cast<double*>(out),
+                                                                                bad);
+                  else k_block_jacobi<NPHI, float><<<g, 64, 0, s>>>(op.K64, op.area, op.Mref, op.ne, op.n, coefK,
+                                                                     coefM, static_cast<float*>(out), bad));
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_precond(const DevOp& op, double coefK, double coefM, int type, void* ap, void* pinv,
                                  double* p64, int* bad, cudaStream_t s) {
   if (!op.K64 || op.ne < 1 || type < 0 || type > 2 || !ap || !pinv || !p64) return cudaErrorInvalidValue;

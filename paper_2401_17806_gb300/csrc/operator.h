@@ -15,6 +15,7 @@
 
 #include "host.h"
 #include "kernels.h"
+#include "mg.h"
 
 #define DGSL_CUDA(expr)                                                                   \
   do {                                                                                    \
@@ -258,6 +259,56 @@ struct dgsl_operator {
   // Ends a hold taken by acquire_precond (any thread; no lock needed).
   static void release_precond(Work::Precond* c) {
     if (c) c->refs.fetch_sub(1);
+  }
+
+  // Two-level multigrid systems (k_mg.cu): the topology once per operator,
+  // then one hierarchy and workspace per system (coefficients and type 0 FP32,
+  // 1 FP64, 2 BF16 couplings), the last kMGKeep kept like the block-Jacobi
+  // systems.  The caller holds mu.
+  std::unique_ptr<dgsl::MGTopo> mgtopo;
+  struct MGEntry {
+    dgsl::MGSysPtr sys;
+    double coefK = 0.0, coefM = 0.0;
+    int type = 0;
+    uint64_t used = 0;
+    std::atomic<int> refs{0};
+  };
+  static constexpr size_t kMGKeep = 4;
+  std::vector<std::unique_ptr<MGEntry>> mgs;
+  uint64_t mg_clock = 0;
+  MGEntry* acquire_mg(double coefK, double coefM, int type, cudaStream_t s) {
+    ++mg_clock;
+    for (auto& e : mgs)
+      if (e->sys && e->coefK == coefK && e->coefM == coefM && e->type == type) {
+        e->used = mg_clock;
+        e->refs.fetch_add(1);
+        return e.get();
+      }
+    if (!mgtopo) {
+      mgtopo = dgsl::mg_topo_build(hm, d, s);
+      device_bytes += mgtopo->device_bytes;
+    }
+    MGEntry* slot = nullptr;
+    if (mgs.size() >= kMGKeep)
+      for (auto& e : mgs)
+        if (e->refs.load() == 0 && (!slot || e->used < slot->used)) slot = e.get();
+    if (!slot) {
+      mgs.push_back(std::make_unique<MGEntry>());
+      slot = mgs.back().get();
+    }
+    device_bytes -= dgsl::mg_sys_bytes(slot->sys.get());
+    slot->sys.reset();
+    slot->sys = dgsl::mg_sys_build(*mgtopo, d, coefK, coefM, type, coefM == 0.0, s);
+    device_bytes += dgsl::mg_sys_bytes(slot->sys.get());
+    slot->coefK = coefK;
+    slot->coefM = coefM;
+    slot->type = type;
+    slot->used = mg_clock;
+    slot->refs.fetch_add(1);
+    return slot;
+  }
+  static void release_mg(MGEntry* e) {
+    if (e) e->refs.fetch_sub(1);
   }
 };
 

@@ -22,7 +22,7 @@ MAIN, DUAL = 0, 1
 FORM_ASSEMBLED, FORM_FACTORED = 0, 1
 SCHUR, HELMHOLTZ = 0, 1
 PREC_F64, PREC_F32_IR, PREC_BF16_IR = 0, 1, 2
-PRECOND_NONE, PRECOND_BLOCK_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_MULTIGRID = 0, 1, 2
 
 
 class DgslError(RuntimeError):
@@ -69,6 +69,10 @@ class dgsl_solve_info(C.Structure):
 
 
 MAX_RHS = 8  # right-hand sides per engine request
+
+
+class dgsl_mg_info(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_vertices", C.c_int32), ("sizes", C.c_int32 * 16)]
 
 
 class dgsl_request(C.Structure):
@@ -140,6 +144,10 @@ _SIGS = {
     "dgsl_poll_many": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dgsl_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(dgsl_server_stats)]),
     "dgsl_server_destroy": (None, [C.c_void_p]),
+    "dgsl_apply_multigrid": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
+    "dgsl_query_multigrid": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(dgsl_mg_info), C.c_void_p,
+                                       C.c_void_p]),
     "dgsl_cg_solve_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
                                         C.c_int, C.POINTER(dgsl_solve_opts),
                                         C.POINTER(dgsl_solve_info), C.c_void_p]),
@@ -420,6 +428,35 @@ def _noalloc_solve(self, kind, coef, b, x, n_rhs=1, opts=None, stream=None, chec
 
 
 Operator.dgsl_cg_solve_noalloc = _noalloc_solve
+
+
+def _apply_multigrid(self, kind, coef, r, z, precision=PREC_F32_IR, stream=None):
+    """dgsl_apply_multigrid: z = M r once (float64 tensors for PREC_F64, else
+    float32)."""
+    dt = "float64" if precision == PREC_F64 else "float32"
+    _check(load().dgsl_apply_multigrid(self.h, int(kind), float(coef), int(precision), _dptr(r, dt, self.n_dof),
+                                       _dptr(z, dt, self.n_dof), _stream(stream)))
+
+
+def _query_multigrid(self, kind, coef):
+    """dgsl_query_multigrid: (level sizes, cvid [n_tri, 3] natural order,
+    aggregates of every level but the last, as a list of arrays)."""
+    info = dgsl_mg_info()
+    _check(load().dgsl_query_multigrid(self.h, int(kind), float(coef), C.byref(info), None, None))
+    sizes = [int(info.sizes[i]) for i in range(info.n_levels)]
+    cvid = np.zeros((self.n_tri, 3), dtype=np.int32)
+    agg = np.zeros(max(1, sum(sizes[:-1])), dtype=np.int32)
+    _check(load().dgsl_query_multigrid(self.h, int(kind), float(coef), C.byref(info),
+                                       cvid.ctypes.data_as(C.c_void_p), agg.ctypes.data_as(C.c_void_p)))
+    out, o = [], 0
+    for n in sizes[:-1]:
+        out.append(agg[o:o + n].copy())
+        o += n
+    return sizes, cvid, out
+
+
+Operator.dgsl_apply_multigrid = _apply_multigrid
+Operator.dgsl_query_multigrid = _query_multigrid
 
 
 def _set_fields(o, kw):

@@ -177,15 +177,19 @@ def test_server_continuous_batching(problems):
     opts = dgsl.engine_opts(precision=dgsl.PREC_F32_IR, hbm_budget_bytes=2_000_000_000, idle_us=50000)
     srv = dgsl.Server(opts)
     try:
-        bufs, tickets = [], []
+        # every buffer is allocated before the first submission: a device
+        # allocation (cudaMalloc) may wait for the whole device, the running
+        # engine included, and would serialise the rounds
+        bufs = []
         for rep in range(3):
             for k, (op, orc, perm, kind, coef, b) in enumerate(problems):
                 bd = torch.tensor(to_internal(b, perm, op.n_phi), device="cuda")
-                x = torch.full_like(bd, np.nan)
-                bufs.append((k, bd, x))
-                # only this stream: a device-wide synchronize would wait for the
-                # running engine itself and serialise the submissions
-                torch.cuda.current_stream().synchronize()
+                bufs.append((k, bd, torch.full_like(bd, np.nan)))
+        torch.cuda.synchronize()
+        tickets = []
+        for rep in range(3):
+            for k, bd, x in bufs[rep * len(problems):(rep + 1) * len(problems)]:
+                op, orc, perm, kind, coef, b = problems[k]
                 tickets.append(srv.dgsl_submit(dgsl.request(op, kind, coef, bd, x)))
             time.sleep(0.002)
         done = {}

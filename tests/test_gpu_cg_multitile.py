@@ -56,6 +56,12 @@ class Problem:
             self.lu_H = spla.splu(self.H.tocsc())
         return self.lu_H.solve(b)
 
+    def tol(self, kind):
+        """Solve tolerance: 1e-10 / kappa where the strict error bar applies
+        (error <= kappa * relres), else 5e-11."""
+        kap = self.kappa(kind)
+        return max(1e-10 / kap, 4e-15) if kap * EPS64 <= 1e-11 else 5e-11
+
     def check(self, kind, b, x_int, tol_res=1e-10, label=""):
         """Full oracle residual <= tol_res, and the error bar of the module."""
         x = to_natural(x_int, self.perm, self.op.n_phi)
@@ -92,7 +98,7 @@ def big2(dgsl_lib):
     return Problem(96, 2, 5)
 
 
-@pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("prec,precond", [(0, 0), (1, 0), (1, 1), (0, 1), (1, 2), (0, 2)])
 def test_persistent_cg_several_tiles_per_cta(big, prec, precond):
     from paper_2401_17806_gb300 import dgsl
     op = big.op
@@ -100,12 +106,17 @@ def test_persistent_cg_several_tiles_per_cta(big, prec, precond):
         b = synth.standard_normal(op.n_dof, seed)
         bd = torch.tensor(to_internal(b, big.perm, op.n_phi), device="cuda")
         x = torch.zeros_like(bd)
-        info = op.dgsl_cg_solve(kind, coef, bd, x, opts=dgsl.solve_opts(tol=5e-11, precision=prec,
-                                                                           precond=precond))[0]
+        tol = big.tol(kind)
+        info = op.dgsl_cg_solve(kind, coef, bd, x, opts=dgsl.solve_opts(tol=tol, precision=prec, precond=precond),
+                                check=False)[0]
         torch.cuda.synchronize()
-        assert info.status == dgsl.OK and info.relres <= 5e-11, (kind, info.status, info.relres)
-        ntiles = -(-op.n_tri // 12)
-        assert ntiles >= 3 * info.grid, (ntiles, info.grid)
+        # below 1e-13 the refinement may stop at its FP64 rounding floor first
+        assert info.status == dgsl.OK or (info.status == dgsl.ENOTCONV and info.relres <= 1e-13), \
+            (kind, info.status, info.relres)
+        assert info.relres <= max(tol, 1e-13)
+        if precond != 2:      # the persistent CG (the multigrid solve has no persistent launch)
+            ntiles = -(-op.n_tri // 12)
+            assert ntiles >= 3 * info.grid, (ntiles, info.grid)
         big.check(kind, b, x.cpu().numpy(), label=f"k_cg kind={kind} prec={prec} precond={precond}")
 
 
@@ -124,21 +135,24 @@ def test_engine_slots_span_several_chunks_per_cta(big, big2):
         bs = [synth.standard_normal(prob.op.n_dof, seed + 100 * r) for r in range(nr)]
         bd = torch.tensor(np.concatenate([to_internal(b, prob.perm, prob.op.n_phi) for b in bs]), device="cuda")
         x = torch.full_like(bd, np.nan)
-        reqs.append(dgsl.request(prob.op, kind, coef, bd, x, tol=5e-11, n_rhs=nr))
+        reqs.append(dgsl.request(prob.op, kind, coef, bd, x, tol=prob.tol(kind), n_rhs=nr))
         keep.append((prob, kind, coef, bs, bd, x))
     infos = dgsl.dgsl_cg_solve_batch(reqs, opts)
     torch.cuda.synchronize()
     for (prob, kind, coef, bs, bd, x), info in zip(keep, infos):
-        assert info.status == dgsl.OK and info.relres <= 5e-11, (info.status, info.relres)
+        tol = prob.tol(kind)
+        assert info.status == dgsl.OK or (info.status == dgsl.ENOTCONV and info.relres <= 1e-13), \
+            (info.status, info.relres)
+        assert info.relres <= max(tol, 1e-13)
         xs = x.cpu().numpy().reshape(len(bs), -1)
         for r, b in enumerate(bs):
             prob.check(kind, b, xs[r], label=f"engine kind={kind} n={prob.op.n_dof} rhs={r}")
     # the last request alone gives the same bits
     prob, kind, coef, bs, bd, x = keep[-1]
     xa = torch.full_like(bd, np.nan)
-    ia = dgsl.dgsl_cg_solve_batch([dgsl.request(prob.op, kind, coef, bd, xa, tol=5e-11)], opts)[0]
+    ia = dgsl.dgsl_cg_solve_batch([dgsl.request(prob.op, kind, coef, bd, xa, tol=prob.tol(kind))], opts)[0]
     torch.cuda.synchronize()
-    assert ia.status == dgsl.OK
+    assert ia.status == infos[-1].status
     assert torch.equal(xa, x)
 
 
@@ -148,7 +162,7 @@ def test_p2_persistent_cg_fp32(big2):
     b = synth.standard_normal(op.n_dof, 51)
     bd = torch.tensor(to_internal(b, big2.perm, op.n_phi), device="cuda")
     x = torch.zeros_like(bd)
-    info = op.dgsl_cg_solve(dgsl.SCHUR, DT, bd, x, opts=dgsl.solve_opts(tol=5e-11, precision=1))[0]
+    info = op.dgsl_cg_solve(dgsl.SCHUR, DT, bd, x, opts=dgsl.solve_opts(tol=big2.tol(0), precision=1))[0]
     torch.cuda.synchronize()
     assert info.status == dgsl.OK
     big2.check(0, b, x.cpu().numpy(), label="k_cg p=2 fp32-ir")

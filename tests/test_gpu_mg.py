@@ -1,0 +1,159 @@
+"""GPU parity of the two-level multigrid preconditioned CG (an extension; the
+oracle's restatement is oracle/multigrid.py) through the C-ABI:
+ - the hierarchy's integer data (vertex numbering, aggregates of every level,
+   level sizes) equal the oracle's bit for bit;
+ - one application z = M r equals the oracle's M r (FP64: to rounding; FP32
+   and BF16 couplings: to their precision);
+ - MG-preconditioned solves (FP64 and FP32 under FP64 refinement) meet the
+   oracle's residual and error bars for the pressure and viscous systems;
+ - the iteration count stays nearly flat as the mesh is refined."""
+import numpy as np
+import pytest
+
+from oracle import assemble as OA
+from oracle import mesh as OM
+from oracle import multigrid as MG
+from oracle import operators as OP
+from paper_2401_17806_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_apply import rel, to_internal, to_natural  # noqa: E402
+
+EPS64 = 2.0 ** -52
+
+
+def _setup(N, p, seed=2, store=0):
+    from paper_2401_17806_gb300 import dgsl
+    xy, tri, per = synth.jittered_periodic_mesh(N, seed)
+    op = dgsl.Operator(xy, tri, per, p, store=store)
+    conn = OM.connectivity(xy, tri, per)
+    ops = OP.Operators(OA.assemble(xy, tri, per, p, conn=conn))
+    return op, ops, conn, tri, op.maps()["perm"]
+
+
+@pytest.mark.parametrize("N,p", [(16, 1), (32, 3), (48, 2)])
+def test_hierarchy_integer_data_bit_exact(dgsl_lib, N, p):
+    from paper_2401_17806_gb300 import dgsl
+    op, ops, conn, tri, perm = _setup(N, p)
+    sizes, cvid, aggs = op.dgsl_query_multigrid(dgsl.SCHUR, 1e-3)
+    M = MG.TwoLevel(ops.schur_matrix(1e-3), conn, tri, p, singular=True)
+    assert sizes == [L.A.shape[0] for L in M.levels]
+    assert np.array_equal(cvid, M.cvid)
+    assert len(aggs) == len(M.levels) - 1
+    for a, L in zip(aggs, M.levels[:-1]):
+        assert np.array_equal(a, L.agg)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_one_application_matches_the_oracle(dgsl_lib, kind, prec):
+    from paper_2401_17806_gb300 import dgsl
+    op, ops, conn, tri, perm = _setup(40, 3)
+    coef = 1e-3
+    A = ops.schur_matrix(coef) if kind == 0 else ops.helmholtz_matrix(coef)
+    M = MG.TwoLevel(A, conn, tri, 3, singular=kind == 0)
+    r = synth.standard_normal(op.n_dof, 9)
+    if kind == 0:
+        r -= r.mean()
+    z_orc = M(r)
+    dt = torch.float64 if prec == dgsl.PREC_F64 else torch.float32
+    rd = torch.tensor(to_internal(r, perm, op.n_phi), dtype=dt, device="cuda")
+    zd = torch.full_like(rd, np.nan)
+    op.dgsl_apply_multigrid(kind, coef, rd, zd, precision=prec)
+    torch.cuda.synchronize()
+    z = to_natural(zd.double().cpu().numpy(), perm, op.n_phi)
+    if kind == 0:   # the pressure preconditioner is defined up to constants
+        z, z_orc = z - z.mean(), z_orc - z_orc.mean()
+    tol = 1e-11 if prec == dgsl.PREC_F64 else 2e-5
+    assert rel(z, z_orc) <= tol, rel(z, z_orc)
+
+
+def test_bf16_couplings_application_is_close(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    op, ops, conn, tri, perm = _setup(24, 2, store=dgsl.STORE_F64 | dgsl.STORE_BF16)
+    A = ops.helmholtz_matrix(1e-3)
+    M = MG.TwoLevel(A, conn, tri, 2, singular=False)
+    r = synth.standard_normal(op.n_dof, 4)
+    rd = torch.tensor(to_internal(r, perm, op.n_phi), dtype=torch.float32, device="cuda")
+    zd = torch.empty_like(rd)
+    op.dgsl_apply_multigrid(dgsl.HELMHOLTZ, 1e-3, rd, zd, precision=dgsl.PREC_BF16_IR)
+    torch.cuda.synchronize()
+    z = to_natural(zd.double().cpu().numpy(), perm, op.n_phi)
+    # BF16 couplings in the smoother residuals: 2^-8 relative per coefficient
+    assert rel(z, M(r)) <= 2e-2
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_mg_solve_meets_the_oracle_bars(dgsl_lib, prec, kind):
+    from paper_2401_17806_gb300 import dgsl
+    op, ops, conn, tri, perm = _setup(32, 3, seed=4)
+    coef = 1e-3
+    A = (ops.schur_matrix(coef) if kind == 0 else ops.helmholtz_matrix(coef)).tocsr()
+    lo, hi, _ = OP.cg_lanczos_extremes(lambda v: A @ v, synth.standard_normal(op.n_dof, 99), 800,
+                                       mean_zero=kind == 0)
+    kappa = hi / lo
+    strict = kappa * EPS64 <= 1e-11
+    tol = max(1e-10 / kappa, 4e-15) if strict else 1e-11
+    b = synth.standard_normal(op.n_dof, 21)
+    bd = torch.tensor(to_internal(b, perm, op.n_phi), device="cuda")
+    x = torch.zeros_like(bd)
+    info = op.dgsl_cg_solve(kind, coef, bd, x, check=False,
+                            opts=dgsl.solve_opts(tol=tol, precision=prec, precond=dgsl.PRECOND_MULTIGRID))[0]
+    torch.cuda.synchronize()
+    assert info.status == dgsl.OK or (info.status == dgsl.ENOTCONV and info.relres <= 1e-13), info.status
+    xn = to_natural(x.cpu().numpy(), perm, op.n_phi)
+    rhs = OP.project_mean(b) if kind == 0 else b
+    res = np.linalg.norm(rhs - A @ xn) / np.linalg.norm(rhs)
+    assert res <= max(2e-12, 1.5 * info.relres)
+    xd = OP.schur_solve_direct(A, b) if kind == 0 else OP.direct_solve(A, b)
+    err = rel(xn, xd)
+    print(f"MG_SOLVE kind={kind} prec={prec} kappa>={kappa:.3e} iters={info.iters} refinements={info.refinements} "
+          f"relres={res:.3e} err={err:.3e}")
+    if strict:
+        assert err <= 1e-10
+    else:
+        assert err <= 10 * kappa * max(res, EPS64)
+    # tens of iterations to 1e-13 (unpreconditioned CG needs thousands here)
+    assert info.iters <= 150, info.iters
+
+
+def test_mg_iterations_nearly_flat_under_refinement(dgsl_lib):
+    """FP32 inner PCG under FP64 refinement to 1e-10, p = 3, Schur operator,
+    N = 64, 128, 256: at most 25% more iterations per doubling (plain CG
+    doubles)."""
+    from paper_2401_17806_gb300 import dgsl
+    its = []
+    for N in (64, 128, 256):
+        xy, tri, per = synth.jittered_periodic_mesh(N, 0)
+        op = dgsl.Operator(xy, tri, per, 3)
+        b = torch.tensor(synth.standard_normal(op.n_dof, 5), device="cuda")
+        x = torch.zeros_like(b)
+        info = op.dgsl_cg_solve(dgsl.SCHUR, 1e-3, b, x,
+                                opts=dgsl.solve_opts(tol=1e-10, precision=dgsl.PREC_F32_IR,
+                                                     precond=dgsl.PRECOND_MULTIGRID))[0]
+        torch.cuda.synchronize()
+        assert info.status == dgsl.OK and info.relres <= 1e-10
+        its.append(info.iters)
+    print("MG_FLAT", its)
+    assert all(b <= 1.25 * a for a, b in zip(its, its[1:])), its
+
+
+def test_mg_zero_rhs_and_argument_errors(dgsl_lib):
+    from paper_2401_17806_gb300 import dgsl
+    op, ops, conn, tri, perm = _setup(8, 2)
+    b = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    info = op.dgsl_cg_solve(dgsl.SCHUR, 1e-2, b, x, opts=dgsl.solve_opts(precond=dgsl.PRECOND_MULTIGRID))[0]
+    assert info.status == dgsl.OK and info.iters == 0
+    assert torch.all(x == 0)
+    r = torch.zeros(op.n_dof, dtype=torch.float32, device="cuda")
+    with pytest.raises(dgsl.DgslError):
+        op.dgsl_apply_multigrid(7, 1e-2, r, r.clone())
+    with pytest.raises(dgsl.DgslError):
+        op.dgsl_apply_multigrid(dgsl.SCHUR, 0.0, r, r.clone())
+    with pytest.raises(dgsl.DgslError):      # BF16 couplings not stored
+        op.dgsl_apply_multigrid(dgsl.SCHUR, 1e-2, r, r.clone(), precision=dgsl.PREC_BF16_IR)

@@ -131,7 +131,7 @@ def test_pcg_multiple_rhs_and_options(dgsl_lib):
         assert np.array_equal(xa, to_natural(xs[k], m["perm"], op.n_phi))
     bb = dev(np.zeros(op.n_dof))
     with pytest.raises(dgsl.DgslError) as e:
-        op.dgsl_cg_solve(dgsl.SCHUR, dt, bb, bb.clone(), opts=dgsl.solve_opts(precond=2))
+        op.dgsl_cg_solve(dgsl.SCHUR, dt, bb, bb.clone(), opts=dgsl.solve_opts(precond=3))
     assert e.value.code == dgsl.EINVAL
     with pytest.raises(dgsl.DgslError) as e:
         op.dgsl_cg_solve_noalloc(dgsl.SCHUR, dt, bb, bb.clone(), opts=dgsl.solve_opts(precond=BJ))
