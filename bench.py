@@ -65,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--sl-reps", type=int, default=100,
                     help="sl workload: transport calls per timed step")
     ap.add_argument("--c3-degrees", type=str, default="2,4")
-    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns", "advdiff", "c3"],
+    ap.add_argument("--workload", choices=["stage", "batch", "serve", "cg", "sl", "ns", "advdiff", "c3", "mg"],
                     default="stage",
                     help="stage: implicit stage (default line); batch: many solves in one launch; "
                          "serve: Poisson request sweep through the server; cg: one FP32 inner CG "
@@ -73,12 +73,19 @@ def parse_args(argv=None):
     ap.add_argument("--cg-iters", type=int, default=200)
     ap.add_argument("--precond", action="store_true",
                     help="cg, batch and serve workloads: block-Jacobi preconditioned CG")
-    ap.add_argument("--batch-solves", type=int, default=64)
-    ap.add_argument("--batch-nmax", type=int, default=64)
+    ap.add_argument("--batch-solves", type=int, default=512)
+    ap.add_argument("--batch-nmax", type=int, default=256)
+    ap.add_argument("--batch-paths", type=str, default="engine,engine-bj,multigrid")
+    ap.add_argument("--batch-split", action="store_true",
+                    help="batch workload: also time the right-hand sides as one request each")
     ap.add_argument("--rhs", type=int, default=8)
-    ap.add_argument("--serve-nmax", type=int, default=64)
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-nmax", type=int, default=1024)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000")
+    ap.add_argument("--serve-precond", choices=["none", "block-jacobi", "multigrid"], default="multigrid")
+    ap.add_argument("--serve-budget", type=float, default=150e9)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving sample of the default line")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=10, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -411,6 +418,36 @@ def cg_leg(args):
     kind = "block-Jacobi preconditioned " if args.precond else ""
     print(json.dumps({"workload": f"one {kind}FP32 CG launch, {args.N}x{args.N}, p={args.p}", "iters": info.iters,
                       "grid": info.grid, "us_per_iter": 1e3 * info.cg_kernel_ms / max(1, info.iters)}))
+
+
+def mg_leg(args):
+    """One multigrid-preconditioned Schur solve (FP32 inner PCG under FP64
+    refinement to 1e-10, Fourier right-hand side) on the N x N mesh, run
+    twice (the first builds the hierarchy); prints the second's event-timed
+    cost: the case the multigrid profiles capture."""
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl, synth
+    build.build()
+    torch.cuda.set_device(0)
+    xy, tri, per = synth.jittered_periodic_mesh(args.N, WORKLOAD["seed"])
+    op = dgsl.Operator(xy, tri, per, args.p)
+    b = fourier_rhs(op, 11, WORKLOAD["dt"])
+    x = torch.zeros_like(b)
+    om = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F32_IR, precond=dgsl.PRECOND_MULTIGRID)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        x.zero_()
+        torch.cuda.synchronize()
+        l0 = dgsl.dgsl_launch_count()
+        ev0.record()
+        info = op.dgsl_cg_solve(dgsl.SCHUR, WORKLOAD["dt"], b, x, opts=om, check=False)[0]
+        ev1.record()
+        torch.cuda.synchronize()
+    print(json.dumps({"workload": f"one multigrid PCG Schur solve, {args.N}x{args.N}, p={args.p}",
+                      "status": info.status, "iters": info.iters, "refinements": info.refinements,
+                      "relres": info.relres, "ms": ev0.elapsed_time(ev1),
+                      "us_per_iter": 1e3 * ev0.elapsed_time(ev1) / max(1, info.iters),
+                      "launches": dgsl.dgsl_launch_count() - l0}))
 
 
 def c3_leg(args):
@@ -796,10 +833,21 @@ def advdiff_leg(args):
     }))
 
 
+def engine_bytes_per_row_pass(nphi, cb, R):
+    """Algorithmic bytes per matrix row per CG pass of the batched engine for a
+    request with R right-hand sides: the row's 4 N_phi couplings and its share
+    of the column indices (both shared by the R right-hand sides) and 10 FP32
+    vector accesses per right-hand side."""
+    return 4 * nphi * cb + 16.0 / nphi + 10 * 4 * R
+
+
 def batch_leg(args):
-    """Independent Schur solves of random meshes (N uniform in 8..nmax, p uniform
-    in 1..4, per-solve seeds), each with `rhs` Fourier right-hand sides, all in
-    ONE persistent launch; versus one-solve-at-a-time FP64 CG on a sample."""
+    """The batching configuration: independent Schur solves of random meshes
+    (N uniform in 8..nmax, p uniform in 1..4, per-solve seeds), each with R
+    Fourier right-hand sides, all in ONE call: the persistent engine (one
+    cooperative launch; plain or block-Jacobi CG) and the multigrid path
+    (concurrent solves on worker streams); versus one-solve-at-a-time FP64 CG
+    on a sample of the right-hand sides."""
     import numpy as np
     import torch
     from paper_2401_17806_gb300 import build, dgsl, synth
@@ -814,8 +862,6 @@ def batch_leg(args):
     ops = [dgsl.Operator(*synth.jittered_periodic_mesh(int(N), 1000 + i), int(p), store=store)
            for i, (N, p) in enumerate(zip(Ns, ps))]
     build_s = time.time() - t0
-    # one request per mesh with its R right-hand sides (they share the coupling
-    # stream), and the same right-hand sides as one request each
     reqs, split, bufs = [], [], []
     for i, op in enumerate(ops):
         b = torch.cat([fourier_rhs(op, 5000 + i * R + j, dt) for j in range(R)])
@@ -826,18 +872,10 @@ def batch_leg(args):
         n = op.n_dof
         split += [dgsl.request(op, dgsl.SCHUR, dt, b[j * n:(j + 1) * n], xs[j * n:(j + 1) * n]) for j in range(R)]
     prec = dgsl.PREC_BF16_IR if args.precision == "bf16" else dgsl.PREC_F32_IR
-    pc = dgsl.PRECOND_BLOCK_JACOBI if args.precond else dgsl.PRECOND_NONE
-    opts = dgsl.engine_opts(precision=prec, precond=pc)
-    dgsl.dgsl_cg_solve_batch(reqs[:min(2, len(reqs))], opts)   # warm-up
-    torch.cuda.synchronize()
-    precond_build_s = 0.0
-    if args.precond:  # build every preconditioned system once (one CG iteration each), outside the timing
-        t = time.perf_counter()
-        dgsl.dgsl_cg_solve_batch(reqs, dgsl.engine_opts(precision=prec, precond=pc, max_iters=1, max_refine=1))
-        torch.cuda.synchronize()
-        precond_build_s = time.perf_counter() - t
+    cb = 2 if args.precision == "bf16" else 4
+    peak, peak_src = measured_hbm_peak()
 
-    def timed(rs):
+    def timed(rs, opts):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = dgsl.dgsl_launch_count()
         ev0.record()
@@ -846,13 +884,41 @@ def batch_leg(args):
         torch.cuda.synchronize()
         return out, ev0.elapsed_time(ev1), dgsl.dgsl_launch_count() - l0
 
-    infos, ms, launches = timed(reqs)
-    sinfos, ms_split, _ = timed(split)
-    ok = [i.status == dgsl.OK for i in infos]
-    nrhs_total = len(split)
-    dof_iters = sum(ops[k // R].n_dof * sinfos[k].iters for k in range(nrhs_total))
+    result = {}
+    for name in args.batch_paths.split(","):
+        pc = {"engine": dgsl.PRECOND_NONE, "engine-bj": dgsl.PRECOND_BLOCK_JACOBI,
+              "multigrid": dgsl.PRECOND_MULTIGRID}[name]
+        opts = dgsl.engine_opts(precision=prec, precond=pc)
+        t = time.perf_counter()
+        if pc != dgsl.PRECOND_NONE:  # build every system's preconditioner once, outside the timing
+            dgsl.dgsl_cg_solve_batch(reqs, dgsl.engine_opts(precision=prec, precond=pc, max_iters=1, max_refine=1))
+        else:
+            dgsl.dgsl_cg_solve_batch(reqs[:2], opts)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t
+        infos, ms, launches = timed(reqs, opts)
+        iters = sorted(i.iters for i in infos)
+        entry = {"solves_per_s": nsol / (ms * 1e-3), "rhs_solves_per_s": nsol * R / (ms * 1e-3), "ms_total": ms,
+                 "converged": int(sum(i.status == dgsl.OK for i in infos)), "requests": nsol,
+                 "iters_p50": iters[len(iters) // 2], "iters_max": iters[-1],
+                 "max_relres": max(i.relres for i in infos), "gpu_launches": launches,
+                 "preconditioner_setup_s": setup_s}
+        if name == "engine":
+            # the engine's algorithmic bytes: every request's passes over its couplings
+            alg = sum(i.iters * op.n_dof * engine_bytes_per_row_pass(op.n_phi, cb, R) for i, op in zip(infos, ops))
+            entry["engine_achieved_gbs"] = alg / (ms * 1e-3) / 1e9
+            entry["engine_frac"] = entry["engine_achieved_gbs"] / peak
+            entry["bytes_per_row_pass_per_rhs"] = float(np.mean([engine_bytes_per_row_pass(op.n_phi, cb, R) / R
+                                                                 for op in ops]))
+            entry["peak_source"] = peak_src
+            if args.batch_split:
+                sinfos, ms_split, _ = timed(split, opts)
+                entry["split_rhs_solves_per_s"] = nsol * R / (ms_split * 1e-3)
+                entry["multi_rhs_speedup"] = ms_split / ms
+        result[name] = entry
+        print(json.dumps({name: entry}), file=sys.stderr, flush=True)
     # one-solve-at-a-time FP64 CG on a sample of the same right-hand sides
-    sample = rng.choice(nrhs_total, size=min(16, nrhs_total), replace=False)
+    sample = rng.choice(nsol * R, size=min(16, nsol * R), replace=False)
     o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
     t64 = 0.0
     for k in sample:
@@ -866,134 +932,230 @@ def batch_leg(args):
         torch.cuda.synchronize()
         t64 += time.perf_counter() - t
     base_rate = len(sample) / t64
-    iters = sorted(i.iters for i in sinfos)
-    line = {
-        "metric": "batched Schur solves/s (one persistent launch)", "workload": "batch",
-        "value": nsol / (ms * 1e-3), "unit": "solves/s",
-        "rhs_solves_per_s": nrhs_total / (ms * 1e-3), "dof_iters_per_s": dof_iters / (ms * 1e-3),
-        "split_rhs_solves_per_s": nrhs_total / (ms_split * 1e-3),
-        "multi_rhs_speedup": ms_split / ms,
-        "ms_total": ms, "gpu_launches": launches, "dtype": {"bf16": "bf16+f32+f64"}.get(args.precision, "f32+f64"),
+    for e in result.values():
+        e["speedup_vs_fp64_one_at_a_time"] = e["rhs_solves_per_s"] / base_rate
+    print(json.dumps({
+        "metric": "batched Schur solves/s", "workload": "batch", "data": "synthetic",
+        "dtype": {"bf16": "bf16+f32+f64"}.get(args.precision, "f32+f64"),
         "config": {"solves": nsol, "rhs_per_solve": R, "N_range": [8, args.batch_nmax], "p_range": [1, 4],
                    "tol": WORKLOAD["tol"], "dt": dt, "operator_build_s": build_s,
-                   "precond": "block-Jacobi" if args.precond else "none",
-                   "precond_build_s": precond_build_s,
-                   "sample": f"{nsol} solves x {R} RHS (bounded sample of the 512-solve, N<=256 distribution)"},
-        "converged": int(sum(ok)), "requests": len(reqs), "rhs": nrhs_total, "iters_p50": iters[len(iters) // 2],
-        "iters_max": iters[-1], "max_relres": max(i.relres for i in infos),
-        "split_converged": int(sum(i.status == dgsl.OK for i in sinfos)),
-        "fp64_one_at_a_time": {"rhs_solves_per_s": base_rate, "sample_rhs": len(sample),
-                               "speedup_rhs_solves_per_s": (nrhs_total / (ms * 1e-3)) / base_rate},
-        "data": "synthetic",
-    }
-    print(json.dumps(line))
+                   "total_dof": int(sum(op.n_dof for op in ops))},
+        "paths": result,
+        "fp64_one_at_a_time": {"rhs_solves_per_s": base_rate, "sample_rhs": len(sample)}}))
 
 
-def serve_leg(args):
-    """Open-loop Poisson arrivals through the server: mesh N log-uniform in
-    16..nmax (rounded to a pool of powers of two), p uniform in 1..4, 1..8 RHS
-    per request (one multi-RHS request each), FP32 inner CG + FP64 refinement
-    to 1e-10.  Latency = request done - arrival.  Baseline: the same trace served FIFO by one-at-a-time
-    FP64 CG, with service times measured on this GPU for every pool operator."""
-    import numpy as np
+SERVE_SIZES = (16, 32, 64, 128, 256, 512, 1024)
+
+
+def serve_pool(sizes, dt):
+    """One operator per (N, p) of the pool (p = 1..4) and 8 Fourier right-hand
+    sides each."""
     import torch
-    from paper_2401_17806_gb300 import build, dgsl, synth
-    build.build()
-    torch.cuda.set_device(0)
-    dt = WORKLOAD["dt"]
-    sizes = [n for n in (16, 32, 64, 128, 256, 512, 1024) if n <= args.serve_nmax]
-    t0 = time.time()
+    from paper_2401_17806_gb300 import dgsl, synth
     pool = {}
     for N in sizes:
         for p in range(1, 5):
             op = dgsl.Operator(*synth.jittered_periodic_mesh(N, 300 + N + p), p)
             rhs = torch.cat([fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)])
             pool[(N, p)] = (op, rhs)
-    build_s = time.time() - t0
-    # FP64 one-at-a-time service time per pool operator (one solve each)
+    return pool
+
+
+def fp64_service_times(pool, dt, full_nmax=256, cap=200):
+    """Service time of one Schur solve to 1e-10 by one-at-a-time FP64 CG
+    (unpreconditioned, the paper's solver) for every pool operator: measured
+    in full for N <= full_nmax; above it, the measured cost of one iteration
+    (a capped solve) times the iteration count of the same degree at
+    full_nmax scaled by N / full_nmax (CG iterations grow like 1/h)."""
+    import torch
+    from paper_2401_17806_gb300 import dgsl
     o64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64)
-    svc = {}
-    for key, (op, rhs) in pool.items():
+    svc, how, iters = {}, {}, {}
+    for (N, p), (op, rhs) in sorted(pool.items()):
         b0 = rhs[:op.n_dof].clone()
         x = torch.zeros_like(b0)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=o64, check=False)
-        torch.cuda.synchronize()
-        svc[key] = time.perf_counter() - t
-    pc = dgsl.PRECOND_BLOCK_JACOBI if args.precond else dgsl.PRECOND_NONE
-    if args.precond:  # every pool operator's preconditioned Schur system, built before the sweep
-        wx = [torch.zeros(op.n_dof, dtype=torch.float64, device="cuda") for op, _ in pool.values()]
-        warm = [dgsl.request(op, dgsl.SCHUR, dt, rhs[:op.n_dof], x) for (op, rhs), x in zip(pool.values(), wx)]
-        dgsl.dgsl_cg_solve_batch(warm, dgsl.engine_opts(precond=pc, max_iters=1, max_refine=1))
-        torch.cuda.synchronize()
-    rng = np.random.default_rng(77)
+        if N <= full_nmax:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            info = op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=o64, check=False)[0]
+            torch.cuda.synchronize()
+            svc[(N, p)] = time.perf_counter() - t
+            iters[(N, p)] = info.iters
+            how[(N, p)] = "measured"
+        else:
+            oc = dgsl.solve_opts(tol=1e-30, precision=dgsl.PREC_F64, max_iters=cap, max_refine=1)
+            op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=oc, check=False)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            info = op.dgsl_cg_solve(dgsl.SCHUR, dt, b0, x, opts=oc, check=False)[0]
+            torch.cuda.synchronize()
+            per_iter = (time.perf_counter() - t) / max(1, info.iters)
+            ref = max(n for n in pool if n[1] == p and n[0] <= full_nmax)
+            est = iters[ref] * N / ref[0]
+            svc[(N, p)] = per_iter * est
+            iters[(N, p)] = est
+            how[(N, p)] = f"extrapolated: {per_iter * 1e3:.3f} ms/iteration x {est:.0f} iterations"
+    return svc, how, iters
+
+
+def serve_trace(pool, svc, rate, seconds, seed, precond, budget, nmax, max_rhs=8):
+    """One open-loop Poisson trace through the server (multi-RHS requests:
+    N log-uniform in 16..nmax rounded to the pool, p uniform in 1..4, 1..max_rhs
+    right-hand sides), with its FIFO one-at-a-time FP64 CG counterpart on the
+    same arrivals (service times svc)."""
+    import numpy as np
+    import torch
+    from paper_2401_17806_gb300 import dgsl
+    dt = WORKLOAD["dt"]
+    sizes = sorted({n for n, _ in pool})
+    rng = np.random.default_rng(seed)
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.5) + 8))
+    arr = arr[arr < seconds]
+    lnN = rng.uniform(np.log(16), np.log(nmax), len(arr))
+    Nr = [min(sizes, key=lambda s: abs(np.log(s) - v)) for v in lnN]
+    pr = rng.integers(1, 5, len(arr))
+    kr = rng.integers(1, max_rhs + 1, len(arr))
+    xs = [torch.zeros(int(k) * pool[(int(N), int(p))][0].n_dof, dtype=torch.float64, device="cuda")
+          for N, p, k in zip(Nr, pr, kr)]
+    torch.cuda.synchronize()
+    srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=int(budget), idle_us=2000, precond=precond))
+    owner, outstanding = {}, []
+    done_t = np.full(len(arr), np.nan)
+    status = np.zeros(len(arr), dtype=np.int64)
+    relres = np.full(len(arr), np.nan)
+    start = time.perf_counter()
+    i = 0
+    while True:
+        now = time.perf_counter() - start
+        while i < len(arr) and arr[i] <= now:
+            op, rhs = pool[(int(Nr[i]), int(pr[i]))]
+            k = int(kr[i])
+            t = srv.dgsl_submit(dgsl.request(op, dgsl.SCHUR, dt, rhs[:k * op.n_dof], xs[i], n_rhs=k))
+            owner[t] = i
+            outstanding.append(t)
+            i += 1
+        if outstanding:
+            flags, infos = srv.dgsl_poll_many(np.array(outstanding, dtype=np.uint64))
+            tnow = time.perf_counter() - start
+            keep = []
+            for t, f, inf in zip(outstanding, flags, infos):
+                if f == 1:
+                    done_t[owner[t]] = tnow
+                    status[owner[t]] = inf.status
+                    relres[owner[t]] = inf.relres
+                else:
+                    keep.append(t)
+            outstanding = keep
+        if i >= len(arr) and not outstanding:
+            break
+        if time.perf_counter() - start > seconds + 300:
+            break
+        time.sleep(0.0002)
+    stats = srv.stats()
+    srv.close()
+    lat = done_t - arr
+    fin = np.isfinite(lat)
+    end = np.nanmax(done_t) if fin.any() else seconds
+    free_at, blat = 0.0, []
+    for a, N, p, k in zip(arr, Nr, pr, kr):
+        begin = max(a, free_at)
+        free_at = begin + int(k) * svc[(int(N), int(p))]
+        blat.append(free_at - a)
+    blat = np.array(blat)
+    nsolves = int(sum(int(k) for k, f in zip(kr, fin) if f))
+    return {
+        "rate": rate, "requests": int(len(arr)), "completed": int(fin.sum()),
+        "right_hand_sides": int(kr.sum()), "all_converged": bool(np.all(status[fin] == 0)),
+        "max_relres": float(np.nanmax(relres)) if fin.any() else None,
+        "requests_per_s": float(fin.sum() / end), "solves_per_s": float(nsolves / end),
+        "p50_ms": float(np.nanpercentile(lat, 50) * 1e3), "p99_ms": float(np.nanpercentile(lat, 99) * 1e3),
+        "engine_launches": stats["engine_launches"], "admitted_while_running": stats["admitted_running"],
+        "fp64_one_at_a_time": {"requests_per_s": float(len(arr) / free_at),
+                               "solves_per_s": float(kr.sum() / free_at),
+                               "p50_ms": float(np.percentile(blat, 50) * 1e3),
+                               "p99_ms": float(np.percentile(blat, 99) * 1e3)}}
+
+
+def serve_leg(args):
+    """Open-loop Poisson arrivals through the server: mesh N log-uniform in
+    16..nmax (rounded to the pool of powers of two), p uniform in 1..4, 1..8
+    RHS per request (one multi-RHS request each), FP32 inner CG + FP64
+    refinement to 1e-10, every right-hand side's relative residual reported.
+    Latency = request done - arrival.  Baseline: the same trace served FIFO by
+    one-at-a-time FP64 CG (service times measured on this GPU, extrapolated
+    above N = 256)."""
+    import torch
+    from paper_2401_17806_gb300 import build, dgsl
+    build.build()
+    torch.cuda.set_device(0)
+    dt = WORKLOAD["dt"]
+    sizes = [n for n in SERVE_SIZES if n <= args.serve_nmax]
+    t0 = time.time()
+    pool = serve_pool(sizes, dt)
+    build_s = time.time() - t0
+    svc, how, _ = fp64_service_times(pool, dt)
+    pc = {"none": dgsl.PRECOND_NONE, "block-jacobi": dgsl.PRECOND_BLOCK_JACOBI,
+          "multigrid": dgsl.PRECOND_MULTIGRID}[args.serve_precond]
+    warm_requests(pool, pc, dt)
     results = []
-    for rate in [float(v) for v in args.serve_rates.split(",")]:
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * args.serve_seconds * 1.5) + 8))
-        arr = arr[arr < args.serve_seconds]
-        lnN = rng.uniform(np.log(16), np.log(args.serve_nmax), len(arr))
-        Nr = [min(sizes, key=lambda s: abs(np.log(s) - v)) for v in lnN]
-        pr = rng.integers(1, 5, len(arr))
-        kr = rng.integers(1, 9, len(arr))
-        xs = [torch.zeros(int(k) * pool[(int(N), int(p))][0].n_dof, dtype=torch.float64, device="cuda")
-              for N, p, k in zip(Nr, pr, kr)]
-        torch.cuda.synchronize()
-        srv = dgsl.Server(dgsl.engine_opts(hbm_budget_bytes=40_000_000_000, idle_us=2000, precond=pc))
-        owner, tickets = {}, []
-        start = time.perf_counter()
-        done_t = np.full(len(arr), np.nan)
-        outstanding = []
-        i = 0
-        while True:
-            now = time.perf_counter() - start
-            while i < len(arr) and arr[i] <= now:
-                op, rhs = pool[(int(Nr[i]), int(pr[i]))]
-                k = int(kr[i])
-                t = srv.dgsl_submit(dgsl.request(op, dgsl.SCHUR, dt, rhs[:k * op.n_dof], xs[i], n_rhs=k))
-                owner[t] = i
-                outstanding.append(t)
-                i += 1
-            if outstanding:
-                flags, infos = srv.dgsl_poll_many(np.array(outstanding, dtype=np.uint64))
-                tnow = time.perf_counter() - start
-                keep = []
-                for t, f in zip(outstanding, flags):
-                    if f == 1:
-                        done_t[owner[t]] = tnow
-                    else:
-                        keep.append(t)
-                outstanding = keep
-            if i >= len(arr) and not outstanding:
-                break
-            if time.perf_counter() - start > args.serve_seconds + 120:
-                break
-        stats = srv.stats()
-        srv.close()
-        lat = done_t - arr
-        fin = np.isfinite(lat)
-        end = np.nanmax(done_t) if fin.any() else args.serve_seconds
-        # FIFO one-at-a-time FP64 on the same trace
-        free_at, blat = 0.0, []
-        for a, N, p, k in zip(arr, Nr, pr, kr):
-            begin = max(a, free_at)
-            free_at = begin + int(k) * svc[(int(N), int(p))]
-            blat.append(free_at - a)
-        blat = np.array(blat)
-        results.append({
-            "rate": rate, "requests": int(len(arr)), "completed": int(fin.sum()),
-            "solves_per_s": float(fin.sum() / end), "p50_ms": float(np.nanpercentile(lat, 50) * 1e3),
-            "p99_ms": float(np.nanpercentile(lat, 99) * 1e3), "engine_launches": stats["engine_launches"],
-            "fp64_one_at_a_time": {"solves_per_s": float(len(arr) / free_at),
-                                   "p50_ms": float(np.percentile(blat, 50) * 1e3),
-                                   "p99_ms": float(np.percentile(blat, 99) * 1e3)}})
+    for k, rate in enumerate(float(v) for v in args.serve_rates.split(",")):
+        results.append(serve_trace(pool, svc, rate, args.serve_seconds, 77 + k, pc, args.serve_budget,
+                                   args.serve_nmax))
+        print(json.dumps(results[-1]), file=sys.stderr, flush=True)
     print(json.dumps({
         "metric": "served Schur solves/s and p50/p99 latency", "workload": "serve", "data": "synthetic",
         "config": {"N_pool": sizes, "p_range": [1, 4], "rhs_per_request": [1, 8], "tol": WORKLOAD["tol"],
-                   "precond": "block-Jacobi" if args.precond else "none",
+                   "precond": args.serve_precond, "hbm_budget_bytes": args.serve_budget,
                    "seconds_per_rate": args.serve_seconds, "operator_pool_build_s": build_s,
-                   "sample": f"N log-uniform in 16..{args.serve_nmax} (bounded sample of 16..1024)"},
+                   "fp64_service_times": {f"{n}x{n} p={p}": h for (n, p), h in sorted(how.items())},
+                   "sample": f"N log-uniform in 16..{args.serve_nmax}"},
         "sweep": results}))
+
+
+def serve_sample(args):
+    """The serving half of the metric in the default line: one fixed seeded
+    trace of the serving configuration (N log-uniform in 16..1024, p in 1..4,
+    1..8 right-hand sides per request, FP32 couplings with FP64 refinement to
+    1e-10, 150 GB budget) at 30 requests/s for 10 s through the multigrid
+    server, against the same arrivals served one at a time by FP64 CG."""
+    import torch
+    from paper_2401_17806_gb300 import dgsl
+    dt = WORKLOAD["dt"]
+    t0 = time.time()
+    pool = serve_pool(SERVE_SIZES, dt)
+    build_s = time.time() - t0
+    svc, how, _ = fp64_service_times(pool, dt)
+    warm_requests(pool, dgsl.PRECOND_MULTIGRID, dt)
+    r = serve_trace(pool, svc, 30.0, 10.0, 1234, dgsl.PRECOND_MULTIGRID, 150e9, 1024)
+    fp = r["fp64_one_at_a_time"]
+    r.update({
+        "metric": "served Schur solves/s and p50/p99 latency at 1e-10",
+        "sample": "one seeded Poisson trace, 30 requests/s for 10 s; N log-uniform 16..1024 (pool of powers of "
+                  "two), p uniform 1..4, 1..8 right-hand sides; multigrid-preconditioned FP32 CG under FP64 "
+                  "refinement, 8 concurrent solves, 150 GB budget",
+        "baseline": "the same arrivals served FIFO by one-at-a-time unpreconditioned FP64 CG on this GPU: service "
+                    "times measured for N <= 256, extrapolated above (per-iteration cost x iterations scaled by N)",
+        "solves_per_s_vs_fp64": r["solves_per_s"] / fp["solves_per_s"] if fp["solves_per_s"] else None,
+        "p99_vs_fp64": fp["p99_ms"] / r["p99_ms"] if r["p99_ms"] else None,
+        "operator_pool_build_s": build_s,
+        "fp64_service_s": {f"{n}x{n} p={p}": round(v, 4) for (n, p), v in sorted(svc.items())},
+    })
+    del pool
+    torch.cuda.empty_cache()
+    return r
+
+
+def warm_requests(pool, pc, dt):
+    """One request per pool operator before a trace, so that every operator's
+    preconditioner (block-Jacobi blocks or multigrid hierarchy) is built."""
+    import torch
+    from paper_2401_17806_gb300 import dgsl
+    if pc == dgsl.PRECOND_NONE:
+        return
+    wx = [torch.zeros(op.n_dof, dtype=torch.float64, device="cuda") for op, _ in pool.values()]
+    warm = [dgsl.request(op, dgsl.SCHUR, dt, rhs[:op.n_dof], x) for (op, rhs), x in zip(pool.values(), wx)]
+    dgsl.dgsl_cg_solve_batch(warm, dgsl.engine_opts(precond=pc, max_iters=1, max_refine=1))
+    torch.cuda.synchronize()
 
 
 # ---------------------------------------------------------------- oracle legs
@@ -1177,6 +1339,9 @@ def main():
     if args.workload == "c3":
         c3_leg(args)
         return
+    if args.workload == "mg":
+        mg_leg(args)
+        return
     if args.workload == "sl":
         sl_leg(args)
         return
@@ -1196,6 +1361,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(args)
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = serve_sample(args)
     if world > 1:
         torch.distributed.barrier()
     if rank != 0:
@@ -1289,6 +1457,8 @@ def main():
             "hierarchy_build_and_first_stage_s": mg["first_run_s"],
             "kernel_launches_per_step": mg["launches_per_step"],
         }
+    if serve is not None:
+        line["serving"] = serve
     if "sl" in res:
         sl = res["sl"]
         line["sl_transport"] = {

@@ -362,8 +362,12 @@ int dgsl_cg_solve(const dgsl_operator* op, int kind, double coef, const double* 
  * per (kind, coef, precision) and keeps the last four.
  * dgsl_apply_multigrid applies z = M r once: precision DGSL_PREC_F64 with
  * double r, z and FP64 couplings; DGSL_PREC_F32_IR (FP32 couplings) or
- * DGSL_PREC_BF16_IR (BF16 couplings) with float r, z; device vectors [n_dof]
- * in internal order.  Synchronous.  DGSL_EINVAL if a block of D or the
+ * DGSL_PREC_BF16_IR (BF16 couplings in the two smoother residuals) with float
+ * r, z; device vectors [n_dof] in internal order.  Synchronous.  In the solve
+ * with DGSL_PREC_BF16_IR the PCG matvec, which defines the system solved,
+ * keeps the FP32 couplings (both must be stored): BF16 rounding of the
+ * couplings moves the small eigenvalues of the pressure operator, and only
+ * the preconditioner may be that inexact.  DGSL_EINVAL if a block of D or the
  * coarsest operator is not positive definite. */
 int dgsl_apply_multigrid(const dgsl_operator* op, int kind, double coef, int precision, const void* r,
                          void* z, void* stream);
@@ -535,7 +539,14 @@ typedef struct {
   int64_t idle_us;          /* server: how long an idle engine waits for work (default 500) */
   int32_t precond;          /* DGSL_PRECOND_* for every request (default NONE); with
                                BLOCK_JACOBI each operator keeps the couplings of A P and
-                               P of its systems (see dgsl_cg_solve), counted in the budget */
+                               P of its systems (see dgsl_cg_solve), counted in the budget;
+                               with MULTIGRID the requests are not packed into the
+                               persistent engine (a multigrid iteration is a sequence of
+                               per-level launches): each runs the library's multigrid
+                               solve on one of 8 worker streams, requests of different
+                               operators concurrently, those of one operator in turn;
+                               each operator's growth (hierarchy, workspace) is charged
+                               to the budget */
   int32_t pad;
 } dgsl_engine_opts;
 

@@ -52,8 +52,16 @@ uint16_t f32_to_bf16_bits(float f) {
 
 namespace {
 
+// Couplings in the interleaved row layout.  Every row of K sums to zero
+// (K 1 = 0: the nodal basis is a partition of unity and G 1 = 0 on the
+// torus), so (K x)_row = sum_{c != row} a_c (x_c - x_row): the kernels form
+// a_c (x_c - x_row), and diff stores the self-coupling slot as 0 (the FP32 and
+// BF16 copies; the FP64 copy keeps it, where it multiplies x_row - x_row).
+// Rounded couplings then still annihilate constants, and the relative error of
+// the smooth (small-eigenvalue) components stays at the rounding level instead
+// of growing with the condition number.
 template <class T>
-std::vector<T> to_ell(const HostBlocks& hb, int64_t n, T (*cvt)(double)) {
+std::vector<T> to_ell(const HostBlocks& hb, int64_t n, T (*cvt)(double), bool diff) {
   const int N = hb.nphi, NC = 4 * N;
   const int VEC = 16 / (int)sizeof(T);
   const int NG = (NC + VEC - 1) / VEC;
@@ -64,6 +72,7 @@ std::vector<T> to_ell(const HostBlocks& hb, int64_t n, T (*cvt)(double)) {
       for (int c = 0; c < NC; ++c) {
         const int b = c / N, kk = c % N;
         double v = b == 0 ? hb.Kd[((size_t)i * N + k) * N + kk] : hb.Ko[(((size_t)i * 3 + (b - 1)) * N + k) * N + kk];
+        if (diff && b == 0 && kk == k) v = 0.0;
         out[((size_t)(c / VEC) * n + row) * VEC + c % VEC] = cvt(v);
       }
     }
@@ -139,9 +148,9 @@ int dgsl_build_operators(const dgsl_mesh* mesh, int p, const dgsl_build_opts* op
       }
       d.Mref = op->upload(op->ro.Mref);
       d.Mrefinv = op->upload(dgsl::mref_inverse(op->ro));
-      if (o.store & DGSL_STORE_F64) d.K64 = op->upload(to_ell<double>(hb, d.n, cvt_d));
-      if (o.store & DGSL_STORE_F32) d.K32 = op->upload(to_ell<float>(hb, d.n, cvt_f));
-      if (o.store & DGSL_STORE_BF16) d.K16 = op->upload(to_ell<uint16_t>(hb, d.n, cvt_b));
+      if (o.store & DGSL_STORE_F64) d.K64 = op->upload(to_ell<double>(hb, d.n, cvt_d, false));
+      if (o.store & DGSL_STORE_F32) d.K32 = op->upload(to_ell<float>(hb, d.n, cvt_f, true));
+      if (o.store & DGSL_STORE_BF16) d.K16 = op->upload(to_ell<uint16_t>(hb, d.n, cvt_b, true));
       if (o.factored) {
         d.G = op->upload(hb.G);
         d.Minv = op->upload(hb.Minv);
@@ -446,8 +455,13 @@ int resolve_solve_opts(const dgsl_operator* op, const dgsl_solve_opts* opts, dgs
   if (!op->d.K64) return fail(DGSL_EINVAL, "FP64 couplings are needed for the refinement residual");
   if (o.precision == DGSL_PREC_F32_IR && !op->d.K32) return fail(DGSL_EINVAL, "FP32 couplings not stored");
   if (o.precision == DGSL_PREC_BF16_IR && !op->d.K16) return fail(DGSL_EINVAL, "BF16 couplings not stored");
+  if (o.precision == DGSL_PREC_BF16_IR && o.precond == DGSL_PRECOND_MULTIGRID && !op->d.K32)
+    return fail(DGSL_EINVAL, "the multigrid solve with BF16 couplings also needs the FP32 couplings");
   return DGSL_OK;
 }
+
+// Iterations of one multigrid inner solve (a converging one needs tens).
+constexpr int kMGInnerCap = 2000;
 
 int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double* x, const dgsl_solve_opts& o,
               dgsl_solve_info* info, cudaStream_t s) {
@@ -510,13 +524,16 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
     if (mgh) {
       // multigrid PCG: FP64 on the FP64 couplings, else FP32 vectors on the
       // FP32 or BF16 couplings of a scaled residual
+      // (an inner solve that stalls, e.g. on BF16 couplings, ends after
+      // kMGInnerCap iterations and leaves the decision to the refinement rule)
       dgsl::MGResult mr;
+      const int mg_budget = std::min(budget, kMGInnerCap);
       if (o.precision == DGSL_PREC_F64) {
-        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r64, w.d64, std::max(need, 1e-15), budget, s, &mr));
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r64, w.d64, std::max(need, 1e-15), mg_budget, s, &mr));
       } else {
         DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
-        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, std::max(o.inner_tol, need)), budget,
-                               s, &mr));
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, std::max(o.inner_tol, need)),
+                               mg_budget, s, &mr));
       }
       w.h_res->iters = mr.iters;
       w.h_res->status = 0;
@@ -629,7 +646,7 @@ extern "C" int dgsl_apply_multigrid(const dgsl_operator* cop, int kind, double c
     if (precision < DGSL_PREC_F64 || precision > DGSL_PREC_BF16_IR) return fail(DGSL_EINVAL, "bad precision");
     const int type = precision == DGSL_PREC_F64 ? 1 : precision == DGSL_PREC_BF16_IR ? 2 : 0;
     if (!cop->d.K64) return fail(DGSL_EINVAL, "the multigrid setup needs the FP64 couplings");
-    if ((type == 0 && !cop->d.K32) || (type == 2 && !cop->d.K16))
+    if ((type == 0 && !cop->d.K32) || (type == 2 && (!cop->d.K16 || !cop->d.K32)))
       return fail(DGSL_EINVAL, "the operator lacks the couplings of this precision");
     dgsl_operator* op = const_cast<dgsl_operator*>(cop);
     std::lock_guard<std::mutex> lock(op->mu);

@@ -602,6 +602,9 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
           const int lt = threadIdx.x / NPHI, k = threadIdx.x - lt * NPHI;
           const V* xs = xs_all + lt * 4 * NPHI;
           const unsigned char* sv = st + (size_t)threadIdx.x * 16;
+          // the operator's couplings in difference form (those of A P plainly)
+          constexpr bool DIFF = !PRE && DiffForm<T>::value;
+          const V xrow = DIFF ? xs[k] : V(0);
           V wv = V(0);
 #pragma unroll
           for (int gg = 0; gg < NG; ++gg) {
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
 #pragma unroll
             for (int u = 0; u < VEC; ++u) {
               const int c = gg * VEC + u;
-              if (c < NC) wv = fma((V)v[u], xs[c], wv);
+              if (c < NC) wv = fma((V)v[u], DIFF ? xs[c] - xrow : xs[c], wv);
             }
           }
           wv *= a.coefK;

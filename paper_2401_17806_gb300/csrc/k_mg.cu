@@ -50,7 +50,8 @@ struct MGState {
 };
 
 struct MGFine {
-  const void* vals;
+  const void* vals;    // couplings of the PCG matvec (the operator solved)
+  const void* svals;   // couplings of the smoother residuals (BF16 for type 2)
   const int32_t* cols;
   int ne_pad, ne;
   int64_t n;
@@ -104,8 +105,8 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NW], double* part, MGRed
 }
 
 template <int NPHI, typename T, typename V>
-__device__ __forceinline__ V mg_row(const MGFine& f, int64_t row, const V* x) {
-  V y = (V)f.coefK * assembled_row<NPHI, T, V, false>(static_cast<const T*>(f.vals), f.cols, f.ne_pad, f.n, row, x);
+__device__ __forceinline__ V mg_row(const void* vals, const MGFine& f, int64_t row, const V* x) {
+  V y = (V)f.coefK * assembled_row<NPHI, T, V, false>(static_cast<const T*>(vals), f.cols, f.ne_pad, f.n, row, x);
   if (f.coefM != 0.0) y += (V)f.coefM * mass_row<NPHI, V, false>(f.area, f.Mref, row, x);
   return y;
 }
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_matvec(MGFine f, const V* __r
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t row = (int64_t)tile * ROWS + threadIdx.x;
     if (threadIdx.x < ROWS && row < f.n) {
-      const V y = mg_row<NPHI, T, V>(f, row, p);
+      const V y = mg_row<NPHI, T, V>(f.vals, f, row, p);
       q[row] = y;
       const V pv = p[row];
       a0 = fma(pv, y, a0);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_resid_restrict(MGFine f, cons
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t row = (int64_t)tile * ROWS + threadIdx.x;
     V tv = V(0);
-    if (threadIdx.x < ROWS && row < f.n) tv = r[row] - mg_row<NPHI, T, V>(f, row, x1);
+    if (threadIdx.x < ROWS && row < f.n) tv = r[row] - mg_row<NPHI, T, V>(f.svals, f, row, x1);
     s_t[threadIdx.x] = tv;
     __syncthreads();
     if (threadIdx.x < 3 * TB) {
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_post(MGFine f, const V* __res
     V rv = V(0), tv = V(0);
     if (act) {
       rv = r[row];
-      tv = rv - mg_row<NPHI, T, V>(f, row, x2);
+      tv = rv - mg_row<NPHI, T, V>(f.svals, f, row, x2);
     }
     s_t[threadIdx.x] = tv;
     __syncthreads();
@@ -658,7 +659,7 @@ MGSysPtr mg_sys_build(const MGTopo& topo, const DevOp& d, double coefK, double c
 
 namespace {
 
-template <int NPHI, typename T, typename V>
+template <int NPHI, typename TK, typename TS, typename V>
 struct MGRun {
   MGSys& m;
   const DevOp& d;
@@ -668,7 +669,10 @@ struct MGRun {
   int launches = 0;
 
   MGRun(MGSys& m_, const DevOp& d_, cudaStream_t s_, std::vector<MGLevelD<V>>& lv_) : m(m_), d(d_), s(s_), lv(lv_) {
-    f.vals = m.type == 1 ? (const void*)d.K64 : m.type == 2 ? (const void*)d.K16 : (const void*)d.K32;
+    // type 2 (BF16): BF16 couplings in the smoother only; the PCG matvec, which
+    // defines the system solved, keeps the FP32 couplings
+    f.vals = m.type == 1 ? (const void*)d.K64 : (const void*)d.K32;
+    f.svals = m.type == 1 ? (const void*)d.K64 : m.type == 2 ? (const void*)d.K16 : (const void*)d.K32;
     f.cols = d.cols;
     f.ne_pad = d.ne_pad;
     f.ne = d.ne;
@@ -686,7 +690,7 @@ struct MGRun {
 
   // z = M r for r in m.r (x1, x2 and the level vectors as scratch)
   void precond(V* z, MGRed* red_post) {
-    k_mg_resid_restrict<NPHI, T, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.w), m.st);
+    k_mg_resid_restrict<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.w), m.st);
     k_mg_vgather<V><<<g1(m.host.nv), 256, 0, s>>>(m.host.nv, m.v2t_ptr, m.v2t, v(m.w), lv[0].b, m.st);
     launches += 2;
     const int L = (int)lv.size();
@@ -707,7 +711,7 @@ struct MGRun {
       sol = D.y;
     }
     k_mg_prolong_fine<NPHI, V><<<g1(d.n), 256, 0, s>>>(f, sol, v(m.x1), v(m.x2), m.st);
-    k_mg_post<NPHI, T, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x2), z, m.part, red_post, m.st);
+    k_mg_post<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x2), z, m.part, red_post, m.st);
     launches += 2;
   }
 
@@ -723,7 +727,7 @@ struct MGRun {
   }
 
   void iteration(V* x, int par) {
-    k_mg_matvec<NPHI, T, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.p), v(m.q), m.part, &m.red[0], m.st);
+    k_mg_matvec<NPHI, TK, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.p), v(m.q), m.part, &m.red[0], m.st);
     k_mg_update<NPHI, V, false><<<m.grid, kMGThreads, 0, s>>>(f, nullptr, v(m.p), v(m.q), x, v(m.r), v(m.x1),
                                                               &m.red[0], m.st, par, m.part, &m.red[1]);
     launches += 2;
@@ -804,13 +808,13 @@ struct MGRun {
   }
 };
 
-template <typename T, typename V, class F>
+template <typename TK, typename TS, typename V, class F>
 cudaError_t dispatch(MGSys* m, const DevOp& d, cudaStream_t s, std::vector<MGLevelD<V>>& lv, F&& fn) {
   switch (d.nphi) {
-    case 3: { MGRun<3, T, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
-    case 6: { MGRun<6, T, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
-    case 10: { MGRun<10, T, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
-    case 15: { MGRun<15, T, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
+    case 3: { MGRun<3, TK, TS, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
+    case 6: { MGRun<6, TK, TS, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
+    case 10: { MGRun<10, TK, TS, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
+    case 15: { MGRun<15, TK, TS, V> r(*m, d, s, lv); cudaError_t e = fn(r); for (int i = 0; i < r.launches; ++i) count_launch(); return e; }
   }
   return cudaErrorInvalidValue;
 }
@@ -821,14 +825,14 @@ cudaError_t mg_pcg(MGSys* m, const DevOp& d, const void* b, void* x, double stop
                    MGResult* res) {
   if (!m || !res) return cudaErrorInvalidValue;
   if (m->type == 1)
-    return dispatch<double, double>(m, d, s, m->ld, [&](auto& r) {
+    return dispatch<double, double, double>(m, d, s, m->ld, [&](auto& r) {
       return r.solve(static_cast<const double*>(b), static_cast<double*>(x), stop_rel, max_iters, res);
     });
   if (m->type == 2)
-    return dispatch<uint16_t, float>(m, d, s, m->lf, [&](auto& r) {
+    return dispatch<float, uint16_t, float>(m, d, s, m->lf, [&](auto& r) {
       return r.solve(static_cast<const float*>(b), static_cast<float*>(x), stop_rel, max_iters, res);
     });
-  return dispatch<float, float>(m, d, s, m->lf, [&](auto& r) {
+  return dispatch<float, float, float>(m, d, s, m->lf, [&](auto& r) {
     return r.solve(static_cast<const float*>(b), static_cast<float*>(x), stop_rel, max_iters, res);
   });
 }
@@ -836,14 +840,14 @@ cudaError_t mg_pcg(MGSys* m, const DevOp& d, const void* b, void* x, double stop
 cudaError_t mg_apply(MGSys* m, const DevOp& d, const void* r, void* z, cudaStream_t s) {
   if (!m) return cudaErrorInvalidValue;
   if (m->type == 1)
-    return dispatch<double, double>(m, d, s, m->ld, [&](auto& run) {
+    return dispatch<double, double, double>(m, d, s, m->ld, [&](auto& run) {
       return run.apply(static_cast<const double*>(r), static_cast<double*>(z));
     });
   if (m->type == 2)
-    return dispatch<uint16_t, float>(m, d, s, m->lf, [&](auto& run) {
+    return dispatch<float, uint16_t, float>(m, d, s, m->lf, [&](auto& run) {
       return run.apply(static_cast<const float*>(r), static_cast<float*>(z));
     });
-  return dispatch<float, float>(m, d, s, m->lf, [&](auto& run) {
+  return dispatch<float, float, float>(m, d, s, m->lf, [&](auto& run) {
     return run.apply(static_cast<const float*>(r), static_cast<float*>(z));
   });
 }

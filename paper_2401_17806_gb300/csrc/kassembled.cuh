@@ -45,9 +45,23 @@ struct ValOf<uint16_t> {
   using type = float;
 };
 
+// The operator's couplings are applied in difference form: every row of K
+// sums to zero (K 1 = 0), so (K x)_row = sum_c a_c (x_c - x_row).  The FP32
+// and BF16 copies store the self-coupling slot as 0; the FP64 copy keeps it,
+// and a_self (x_row - x_row) adds nothing.  Rounded couplings and rounded
+// arithmetic then still annihilate constants exactly, and the smooth
+// components (the small eigenvalues) keep a relative error at the rounding
+// level instead of one that grows with the condition number.  This also sets
+// the accuracy floor of the FP64 refinement residual.  (The couplings of A P
+// do not sum to zero and are applied plainly.)
+template <typename T>
+struct DiffForm {
+  static constexpr bool value = true;
+};
+
 // Row `row` of K x.  COH: read x from L2 (x is written by other CTAs of a
-// persistent launch).
-template <int NPHI, typename T, typename V, bool COH>
+// persistent launch).  DIFF: couplings in difference form.
+template <int NPHI, typename T, typename V, bool COH, bool DIFF = DiffForm<T>::value>
 __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int32_t* __restrict__ cols,
                                            int ne, int64_t n, int64_t row, const V* x) {
   constexpr int VEC = Pack<T>::VEC;
@@ -57,6 +71,8 @@ __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int
   int col[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b) col[b] = __ldg(cols + (size_t)b * ne + i);
+  V xr = V(0);
+  if (DIFF) xr = COH ? ldcg(x + row) : __ldg(x + row);
   V acc = V(0);
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
@@ -69,7 +85,7 @@ __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int
         const int b = c / NPHI, kk = c % NPHI;
         const V* xp = x + (size_t)col[b] * NPHI + kk;
         const V xv = COH ? ldcg(xp) : __ldg(xp);
-        acc = fma((V)v[u], xv, acc);
+        acc = fma((V)v[u], DIFF ? xv - xr : xv, acc);
       }
     }
   }
@@ -90,44 +106,5 @@ __device__ __forceinline__ V mass_row(const double* __restrict__ area, const dou
   return (V)__ldg(area + i) * acc;
 }
 
-
-// Same row with x given by an accessor xv(index) (used by the persistent CG,
-// where the search direction is formed on the fly as r + beta p).
-template <int NPHI, typename T, typename V, class XF>
-__device__ __forceinline__ V assembled_row_f(const T* __restrict__ vals, const int32_t* __restrict__ cols,
-                                             int ne, int64_t n, int64_t row, XF xv) {
-  constexpr int VEC = Pack<T>::VEC;
-  constexpr int NC = 4 * NPHI;
-  constexpr int NG = (NC + VEC - 1) / VEC;
-  const int i = (int)(row / NPHI);
-  int col[4];
-#pragma unroll
-  for (int b = 0; b < 4; ++b) col[b] = __ldg(cols + (size_t)b * ne + i);
-  V acc = V(0);
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    typename ValOf<T>::type v[VEC];
-    load16(vals + ((size_t)g * n + row) * VEC, v);
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) {
-      const int c = g * VEC + u;
-      if (c < NC) {
-        const int b = c / NPHI, kk = c % NPHI;
-        acc = fma((V)v[u], xv((size_t)col[b] * NPHI + kk), acc);
-      }
-    }
-  }
-  return acc;
-}
-
-template <int NPHI, typename V, class XF>
-__device__ __forceinline__ V mass_row_f(const double* __restrict__ area, const double* __restrict__ Mref,
-                                        int64_t row, XF xv) {
-  const int i = (int)(row / NPHI), k = (int)(row % NPHI);
-  V acc = V(0);
-#pragma unroll
-  for (int kk = 0; kk < NPHI; ++kk) acc = fma((V)__ldg(Mref + k * NPHI + kk), xv((size_t)i * NPHI + kk), acc);
-  return (V)__ldg(area + i) * acc;
-}
 
 }  // namespace dgsl

@@ -465,6 +465,11 @@ __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, i
   float q[RT];
 #pragma unroll
   for (int r = 0; r < RT; ++r) q[r] = 0.f;
+  // the operator's FP32 / BF16 couplings are in difference form, those of A P plain
+  float xr[RT];
+  ld_rp<RT>(xs + k * RP, xr);
+#pragma unroll
+  for (int r = 0; r < RT; ++r) xr[r] = PRE ? 0.f : xr[r];
   const unsigned char* sv = st + (size_t)row * 16;
 #pragma unroll
   for (int gg = 0; gg < NG; ++gg) {
@@ -477,7 +482,7 @@ __device__ __forceinline__ void cg_rows(const BSlotDesc& d, const ChunkCtx& c, i
         float x[RT];
         ld_rp<RT>(xs + (cc / NPHI) * BL + (cc % NPHI) * RP, x);
 #pragma unroll
-        for (int r = 0; r < RT; ++r) q[r] = fmaf(v[u], x[r], q[r]);
+        for (int r = 0; r < RT; ++r) q[r] = fmaf(v[u], x[r] - xr[r], q[r]);
       }
     }
   }

@@ -105,9 +105,57 @@ int check_engine_opts(const dgsl_engine_opts& o, std::string& why) {
   if (o.precision != DGSL_PREC_F32_IR && o.precision != DGSL_PREC_BF16_IR)
     return why = "engine precision must be DGSL_PREC_F32_IR or DGSL_PREC_BF16_IR", DGSL_EINVAL;
   if (!(o.inner_tol > 0.0) || o.max_iters < 1 || o.max_refine < 1) return why = "bad engine options", DGSL_EINVAL;
-  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI)
-    return why = "precond must be DGSL_PRECOND_NONE or DGSL_PRECOND_BLOCK_JACOBI", DGSL_EINVAL;
+  if (o.precond != DGSL_PRECOND_NONE && o.precond != DGSL_PRECOND_BLOCK_JACOBI && o.precond != DGSL_PRECOND_MULTIGRID)
+    return why = "precond must be DGSL_PRECOND_NONE, DGSL_PRECOND_BLOCK_JACOBI or DGSL_PRECOND_MULTIGRID",
+           DGSL_EINVAL;
   return DGSL_OK;
+}
+
+// ---- multigrid requests: concurrent solves, one per worker stream
+// A multigrid solve is a sequence of short launches per iteration (the
+// V-cycle's levels), not one persistent kernel, so multigrid requests are not
+// packed into the engine: each runs the library's solve on a worker's own
+// stream, and the solves of different operators overlap on the device.
+// Requests on one operator run one at a time (they share its workspace).
+constexpr int kMGWorkers = 8;
+
+// Device bytes an operator may grow by at its first multigrid solve of a
+// system (the solve workspace, the vertex topology, the smoother blocks, the
+// PCG vectors; the coarse levels are small): an upper estimate for admission.
+int64_t mg_growth_estimate(const dgsl_operator* op, int precision) {
+  const DevOp& d = op->d;
+  const int64_t vb = precision == DGSL_PREC_F64 ? 8 : 4, vp = 16 / vb;
+  const int64_t work = 24 * d.n + (int64_t)cg_vec_bytes(d, 1) + 64 * 1024;
+  const int64_t topo = 24 * (int64_t)d.ne + 64 * 1024;
+  const int64_t sys = ((d.nphi + vp - 1) / vp) * d.n * 16 + 6 * d.n * vb + 3 * (int64_t)d.ne * vb + (int64_t)d.ne * 40 +
+                      8 * 1024 * 1024;
+  return work + topo + sys;
+}
+
+// The request's solves (one per right-hand side) with the multigrid
+// preconditioner on stream s; the combined info as for engine requests.
+void run_mg_request(const dgsl_request& r, const dgsl_engine_opts& o, cudaStream_t s, dgsl_solve_info* info) {
+  const int nr = request_nrhs(r);
+  dgsl_solve_opts so;
+  dgsl_default_solve_opts(&so);
+  so.tol = r.tol > 0.0 ? r.tol : 1e-10;
+  so.precision = o.precision;
+  so.precond = DGSL_PRECOND_MULTIGRID;
+  so.inner_tol = o.inner_tol;
+  so.max_iters = o.max_iters;
+  so.max_refine = o.max_refine;
+  std::vector<dgsl_solve_info> each(nr);
+  const int st = dgsl_cg_solve(r.op, r.kind, r.coef, r.b, r.x, nr, &so, each.data(), s);
+  dgsl_solve_info out{};
+  out.status = st;
+  for (const auto& e : each) {
+    out.iters = std::max(out.iters, e.iters);
+    out.refinements = std::max(out.refinements, e.refinements);
+    out.cg_launches += e.cg_launches;
+    out.relres = std::max(out.relres, e.relres);
+    out.cg_kernel_ms += e.cg_kernel_ms;
+  }
+  *info = out;
 }
 
 // held: the request's preconditioned operator (precond), else nullptr.
@@ -185,6 +233,47 @@ extern "C" int dgsl_cg_solve_batch(const dgsl_request* reqs, int n, const dgsl_e
     if (int e = check_engine_opts(o, why)) throw Error(e, why);
     for (int i = 0; i < n; ++i)
       if (int e = check_request(reqs[i], o, why)) throw Error(e, "request " + std::to_string(i) + ": " + why);
+    if (o.precond == DGSL_PRECOND_MULTIGRID) {
+      // requests of one operator run in order on one worker; operators spread
+      // over kMGWorkers streams
+      DGSL_CUDA(cudaSetDevice(o.device));
+      cudaStream_t s0 = (cudaStream_t)stream;
+      DGSL_CUDA(cudaStreamSynchronize(s0));  // the inputs are ready before the worker streams read them
+      std::vector<std::vector<int>> lanes(kMGWorkers);
+      std::unordered_map<const dgsl_operator*, int> lane_of;
+      for (int i = 0; i < n; ++i) {
+        auto it = lane_of.find(reqs[i].op);
+        const int l = it != lane_of.end() ? it->second : (int)(lane_of.size() % kMGWorkers);
+        lane_of.emplace(reqs[i].op, l);
+        lanes[l].push_back(i);
+      }
+      std::vector<dgsl_solve_info> out(n);
+      std::vector<std::thread> th;
+      std::atomic<int> failed{0};
+      for (int l = 0; l < kMGWorkers; ++l) {
+        if (lanes[l].empty()) continue;
+        th.emplace_back([&, l] {
+          cudaSetDevice(o.device);
+          cudaStream_t ws = nullptr;
+          if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+            failed = 1;
+            return;
+          }
+          for (int i : lanes[l]) run_mg_request(reqs[i], o, ws, &out[i]);
+          cudaStreamSynchronize(ws);
+          cudaStreamDestroy(ws);
+        });
+      }
+      for (auto& t : th) t.join();
+      if (failed) throw Error(DGSL_ECUDA, "could not create a worker stream");
+      int worst = DGSL_OK;
+      for (int i = 0; i < n; ++i) {
+        if (infos) infos[i] = out[i];
+        if (out[i].status != DGSL_OK && worst == DGSL_OK) worst = out[i].status;
+      }
+      if (worst != DGSL_OK) dgsl_set_last_error("at least one request did not converge (see infos)");
+      return worst;
+    }
     std::lock_guard<std::mutex> lock(g_batch_mu);
     DGSL_CUDA(cudaSetDevice(o.device));
     auto& R = g_batch_engines[o.device];
@@ -338,6 +427,74 @@ struct dgsl_server {
   std::vector<char> slot_late;            // [kMaxSlots] published while the launch was already running
   int64_t submitted = 0, completed = 0, launches = 0;
   int64_t admitted_running = 0;           // late slots the running engine admitted and finished
+  // multigrid mode: worker threads, each with its own stream, admitting
+  // requests while the other workers' solves run
+  bool mg_mode = false;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> wstreams;
+  std::set<const dgsl_operator*> busy;    // operators with a solve running
+  int active = 0;                         // solves running
+
+  void worker(int w) {
+    cudaSetDevice(o.device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      // the first queued request whose operator is free and which fits the budget
+      auto pick = queue.end();
+      int64_t need = 0;
+      for (auto it = queue.begin(); it != queue.end(); ++it) {
+        Request& q = reqs[*it];
+        if (busy.count(q.r.op)) continue;
+        need = op_cost(q.r.op) + mg_growth_estimate(q.r.op, o.precision);
+        if (bytes_in_use + need <= o.hbm_budget_bytes || active == 0) {
+          pick = it;
+          break;
+        }
+        break;  // in order: a request that does not fit waits for memory, later ones wait behind it
+      }
+      if (pick == queue.end()) {
+        if (stopping && queue.empty()) return;
+        cv.wait_for(lk, std::chrono::milliseconds(50));
+        continue;
+      }
+      const uint64_t t = *pick;
+      queue.erase(pick);
+      Request& q = reqs[t];
+      q.state = RQ_ADMITTED;
+      busy.insert(q.r.op);
+      OpRef& ref = op_refs[q.r.op];
+      ++ref.count;
+      ref.charged += need;
+      bytes_in_use += need;
+      const bool late = active > 0;  // joins solves already on the device
+      ++active;
+      ++launches;
+      const dgsl_request r = q.r;
+      const int64_t before = r.op->device_bytes;
+      lk.unlock();
+      dgsl_solve_info info{};
+      run_mg_request(r, o, wstreams[w], &info);
+      cudaStreamSynchronize(wstreams[w]);
+      lk.lock();
+      // the estimate becomes the operator's actual growth
+      OpRef& rf = op_refs[r.op];
+      const int64_t actual = r.op->device_bytes - before;
+      bytes_in_use += actual - mg_growth_estimate(r.op, o.precision);
+      rf.charged += actual - mg_growth_estimate(r.op, o.precision);
+      Request& qd = reqs[t];
+      qd.info = info;
+      qd.state = RQ_DONE;
+      ++completed;
+      if (late) ++admitted_running;
+      if (--rf.count == 0) {
+        bytes_in_use -= rf.charged;
+        op_refs.erase(r.op);
+      }
+      busy.erase(r.op);
+      --active;
+      cv.notify_all();
+    }
+  }
 
   // Device bytes of op not yet charged to the budget.
   int64_t op_cost(const dgsl_operator* op) const {
@@ -476,6 +633,16 @@ extern "C" int dgsl_server_create(const dgsl_engine_opts* opts, dgsl_server** ou
     std::string why;
     if (int e = check_engine_opts(s->o, why)) throw Error(e, why);
     if (s->o.idle_us < 0 || s->o.idle_us > 1000000) throw Error(DGSL_EINVAL, "idle_us must be in [0, 1e6]");
+    if (s->o.precond == DGSL_PRECOND_MULTIGRID) {
+      DGSL_CUDA(cudaSetDevice(s->o.device));
+      s->mg_mode = true;
+      s->wstreams.resize(kMGWorkers);
+      for (auto& w : s->wstreams) DGSL_CUDA(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking));
+      dgsl_server* raw = s.get();
+      for (int w = 0; w < kMGWorkers; ++w) s->workers.emplace_back([raw, w] { raw->worker(w); });
+      *out = s.release();
+      return DGSL_OK;
+    }
     s->R.init(s->o.device);
     DGSL_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     DGSL_CUDA(cudaStreamCreateWithFlags(&s->build_stream, cudaStreamNonBlocking));
@@ -507,6 +674,18 @@ extern "C" int dgsl_submit(dgsl_server* srv, const dgsl_request* req, uint64_t* 
   if (int e = check_request(*req, srv->o, why)) return dgsl_set_last_error(why), e;
   Request q;
   q.r = *req;
+  if (srv->mg_mode) {
+    if (req->op->device_bytes + mg_growth_estimate(req->op, srv->o.precision) > srv->o.hbm_budget_bytes)
+      return dgsl_set_last_error("request can never fit the memory budget"), DGSL_EBUDGET;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    q.ticket = srv->next_ticket++;
+    *ticket = q.ticket;
+    srv->queue.push_back(q.ticket);
+    srv->reqs.emplace(q.ticket, q);
+    ++srv->submitted;
+    srv->cv.notify_all();
+    return DGSL_OK;
+  }
   q.ws_bytes = request_workspace(req->op, request_nrhs(*req), srv->o.precond);
   // with the preconditioner the operator may grow by A P, P and an FP64 P
   const int64_t pre_bytes =
@@ -593,6 +772,18 @@ extern "C" int dgsl_server_get_stats(dgsl_server* srv, dgsl_server_stats* out) {
 
 extern "C" void dgsl_server_destroy(dgsl_server* srv) {
   if (!srv) return;
+  if (srv->mg_mode) {
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->stopping = true;
+    }
+    srv->cv.notify_all();
+    for (auto& t : srv->workers) t.join();
+    cudaSetDevice(srv->o.device);
+    for (auto w : srv->wstreams) cudaStreamDestroy(w);
+    delete srv;
+    return;
+  }
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->stopping = true;

@@ -131,9 +131,9 @@ def test_engine_rejects_bad_precond(problems):
     op, orc, perm, kind, coef, b = problems[0]
     bd = torch.zeros(op.n_dof, dtype=torch.float64, device="cuda")
     with pytest.raises(dgsl.DgslError) as e:
-        dgsl.dgsl_cg_solve_batch([dgsl.request(op, kind, coef, bd, bd.clone())], dgsl.engine_opts(precond=2))
+        dgsl.dgsl_cg_solve_batch([dgsl.request(op, kind, coef, bd, bd.clone())], dgsl.engine_opts(precond=3))
     assert e.value.code == dgsl.EINVAL
     with pytest.raises(dgsl.DgslError):
-        dgsl.Server(dgsl.engine_opts(precond=2))
+        dgsl.Server(dgsl.engine_opts(precond=3))
     with pytest.raises(TypeError):
         dgsl.engine_opts(preconditioner=BJ)

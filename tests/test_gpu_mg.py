@@ -73,7 +73,7 @@ def test_one_application_matches_the_oracle(dgsl_lib, kind, prec):
 
 def test_bf16_couplings_application_is_close(dgsl_lib):
     from paper_2401_17806_gb300 import dgsl
-    op, ops, conn, tri, perm = _setup(24, 2, store=dgsl.STORE_F64 | dgsl.STORE_BF16)
+    op, ops, conn, tri, perm = _setup(24, 2, store=dgsl.STORE_F64 | dgsl.STORE_F32 | dgsl.STORE_BF16)
     A = ops.helmholtz_matrix(1e-3)
     M = MG.TwoLevel(A, conn, tri, 2, singular=False)
     r = synth.standard_normal(op.n_dof, 4)
