@@ -33,10 +33,11 @@ WORKLOAD = dict(N=256, p=3, dt=1e-3, nu=1e-3, seed=0, noise=1e-2, tol=1e-10)
 METRIC = "Schur-CG DOF*iters/s"
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes (read + write) per matrix row per CG iteration of the persistent
-# CG kernel, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# over a 200-iteration launch, 256x256, p = 3, FP32 couplings).  Keyed by (p,
-# precision); a kernel change invalidates it.
-NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 171.1}
+# CG kernel, from one ncu capture each (dram__bytes_read.sum +
+# dram__bytes_write.sum over a 200-iteration launch at 256x256, p = 3, and
+# 50-iteration launches at 1024x1024, p = 2 and p = 4; FP32 couplings).  Keyed
+# by (p, precision); a kernel change invalidates it.
+NCU_DRAM_BYTES_PER_ROW_ITER = {(3, "f32"): 171.1, (2, "f32"): 169.0, (4, "f32"): 290.9}
 
 
 def workload_name(args):
@@ -75,7 +76,9 @@ def parse_args(argv=None):
                     help="cg, batch and serve workloads: block-Jacobi preconditioned CG")
     ap.add_argument("--batch-solves", type=int, default=512)
     ap.add_argument("--batch-nmax", type=int, default=256)
-    ap.add_argument("--batch-paths", type=str, default="engine,engine-bj,multigrid")
+    ap.add_argument("--batch-paths", type=str, default="multigrid",
+                    help="comma list of engine, engine-bj, multigrid (each path's systems stay on the "
+                         "operators: at the full 512-solve size run one path per process)")
     ap.add_argument("--batch-split", action="store_true",
                     help="batch workload: also time the right-hand sides as one request each")
     ap.add_argument("--rhs", type=int, default=8)
@@ -84,6 +87,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-precond", choices=["none", "block-jacobi", "multigrid"], default="multigrid")
     ap.add_argument("--serve-budget", type=float, default=150e9)
+    ap.add_argument("--serve-sample-rate", type=float, default=10.0)
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving sample of the default line")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
@@ -483,6 +487,11 @@ def c3_leg(args):
             gbs = op.n_dof * per_row / (us * 1e-6) / 1e9
             entry["k_cg"] = {"us_per_iter": us, "bytes_per_row_iter": per_row, "achieved_gbs": gbs,
                              "frac": gbs / peak, "peak": peak, "peak_source": peak_src, "grid": ic.grid}
+            tr = NCU_DRAM_BYTES_PER_ROW_ITER.get((p, name))
+            if tr is not None:  # the DRAM traffic ncu measured for this kernel and size
+                dram_gbs = op.n_dof * tr / (us * 1e-6) / 1e9
+                entry["k_cg"].update({"ncu_dram_bytes_per_row_iter": tr, "dram_gbs": dram_gbs,
+                                      "dram_frac": dram_gbs / peak})
             # the full solve with the multigrid preconditioner
             om = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=prec, precond=dgsl.PRECOND_MULTIGRID)
             x.zero_()
@@ -859,18 +868,19 @@ def batch_leg(args):
     ps = rng.integers(1, 5, nsol)
     store = dgsl.STORE_F64 | dgsl.STORE_F32 | (dgsl.STORE_BF16 if args.precision == "bf16" else 0)
     t0 = time.time()
-    ops = [dgsl.Operator(*synth.jittered_periodic_mesh(int(N), 1000 + i), int(p), store=store)
-           for i, (N, p) in enumerate(zip(Ns, ps))]
+    ops = build_operators([(N, p, 1000 + i) for i, (N, p) in enumerate(zip(Ns, ps))], store)
     build_s = time.time() - t0
     reqs, split, bufs = [], [], []
     for i, op in enumerate(ops):
         b = torch.cat([fourier_rhs(op, 5000 + i * R + j, dt) for j in range(R)])
         x = torch.zeros_like(b)
-        xs = torch.zeros_like(b)
+        xs = torch.zeros_like(b) if args.batch_split else None
         bufs.append((op, b, x, xs))  # requests hold raw pointers: keep every tensor alive
         reqs.append(dgsl.request(op, dgsl.SCHUR, dt, b, x, n_rhs=R))
         n = op.n_dof
-        split += [dgsl.request(op, dgsl.SCHUR, dt, b[j * n:(j + 1) * n], xs[j * n:(j + 1) * n]) for j in range(R)]
+        if args.batch_split:
+            split += [dgsl.request(op, dgsl.SCHUR, dt, b[j * n:(j + 1) * n], xs[j * n:(j + 1) * n])
+                      for j in range(R)]
     prec = dgsl.PREC_BF16_IR if args.precision == "bf16" else dgsl.PREC_F32_IR
     cb = 2 if args.precision == "bf16" else 4
     peak, peak_src = measured_hbm_peak()
@@ -947,17 +957,30 @@ def batch_leg(args):
 SERVE_SIZES = (16, 32, 64, 128, 256, 512, 1024)
 
 
+def build_operators(specs, store=None):
+    """dgsl.Operator for every (N, p, seed) of specs, built by host threads
+    (the C-ABI build releases the interpreter lock); returns them in order."""
+    import concurrent.futures as cf
+    from paper_2401_17806_gb300 import dgsl, synth
+    st = store if store is not None else 0
+
+    def one(spec):
+        N, p, seed = spec
+        return dgsl.Operator(*synth.jittered_periodic_mesh(int(N), int(seed)), int(p), store=st)
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, specs))
+
+
 def serve_pool(sizes, dt):
     """One operator per (N, p) of the pool (p = 1..4) and 8 Fourier right-hand
     sides each."""
     import torch
-    from paper_2401_17806_gb300 import dgsl, synth
+    keys = [(N, p) for N in sizes for p in range(1, 5)]
+    ops = build_operators([(N, p, 300 + N + p) for N, p in keys])
     pool = {}
-    for N in sizes:
-        for p in range(1, 5):
-            op = dgsl.Operator(*synth.jittered_periodic_mesh(N, 300 + N + p), p)
-            rhs = torch.cat([fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)])
-            pool[(N, p)] = (op, rhs)
+    for (N, p), op in zip(keys, ops):
+        rhs = torch.cat([fourier_rhs(op, 9000 + 10 * N + 8 * p + j, dt) for j in range(8)])
+        pool[(N, p)] = (op, rhs)
     return pool
 
 
@@ -1063,9 +1086,11 @@ def serve_trace(pool, svc, rate, seconds, seed, precond, budget, nmax, max_rhs=8
         blat.append(free_at - a)
     blat = np.array(blat)
     nsolves = int(sum(int(k) for k, f in zip(kr, fin) if f))
+    failed = [{"N": int(Nr[j]), "p": int(pr[j]), "rhs": int(kr[j]), "status": int(status[j]),
+               "relres": float(relres[j])} for j in range(len(arr)) if fin[j] and status[j] != 0][:10]
     return {
         "rate": rate, "requests": int(len(arr)), "completed": int(fin.sum()),
-        "right_hand_sides": int(kr.sum()), "all_converged": bool(np.all(status[fin] == 0)),
+        "right_hand_sides": int(kr.sum()), "all_converged": bool(np.all(status[fin] == 0)), "not_converged": failed,
         "max_relres": float(np.nanmax(relres)) if fin.any() else None,
         "requests_per_s": float(fin.sum() / end), "solves_per_s": float(nsolves / end),
         "p50_ms": float(np.nanpercentile(lat, 50) * 1e3), "p99_ms": float(np.nanpercentile(lat, 99) * 1e3),
@@ -1116,7 +1141,7 @@ def serve_sample(args):
     """The serving half of the metric in the default line: one fixed seeded
     trace of the serving configuration (N log-uniform in 16..1024, p in 1..4,
     1..8 right-hand sides per request, FP32 couplings with FP64 refinement to
-    1e-10, 150 GB budget) at 30 requests/s for 10 s through the multigrid
+    1e-10, 150 GB budget) at --serve-sample-rate requests/s for 10 s through the multigrid
     server, against the same arrivals served one at a time by FP64 CG."""
     import torch
     from paper_2401_17806_gb300 import dgsl
@@ -1126,11 +1151,11 @@ def serve_sample(args):
     build_s = time.time() - t0
     svc, how, _ = fp64_service_times(pool, dt)
     warm_requests(pool, dgsl.PRECOND_MULTIGRID, dt)
-    r = serve_trace(pool, svc, 30.0, 10.0, 1234, dgsl.PRECOND_MULTIGRID, 150e9, 1024)
+    r = serve_trace(pool, svc, args.serve_sample_rate, 10.0, 1234, dgsl.PRECOND_MULTIGRID, 150e9, 1024)
     fp = r["fp64_one_at_a_time"]
     r.update({
         "metric": "served Schur solves/s and p50/p99 latency at 1e-10",
-        "sample": "one seeded Poisson trace, 30 requests/s for 10 s; N log-uniform 16..1024 (pool of powers of "
+        "sample": f"one seeded Poisson trace, {args.serve_sample_rate:g} requests/s for 10 s; N log-uniform 16..1024 (pool of powers of "
                   "two), p uniform 1..4, 1..8 right-hand sides; multigrid-preconditioned FP32 CG under FP64 "
                   "refinement, 8 concurrent solves, 150 GB budget",
         "baseline": "the same arrivals served FIFO by one-at-a-time unpreconditioned FP64 CG on this GPU: service "

@@ -532,8 +532,11 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
         DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r64, w.d64, std::max(need, 1e-15), mg_budget, s, &mr));
       } else {
         DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
-        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, std::max(o.inner_tol, need)),
-                               mg_budget, s, &mr));
+        // the inner target is not loosened near the outer tolerance (as it is
+        // for the plain CG): a multigrid iteration is cheap next to a refinement
+        // step, and a loose inner solve stalled the refinement of some
+        // right-hand sides at 1e-10..5e-10 on 512^2 and 1024^2 meshes, p >= 3
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, o.inner_tol), mg_budget, s, &mr));
       }
       w.h_res->iters = mr.iters;
       w.h_res->status = 0;

@@ -46,15 +46,21 @@
 // to mean zero; symmetric and positive definite on the mean-free vectors), u
 // being projected by its mean from that reduction where it is used, so p and
 // x stay mean-free.
+#include <cstdlib>
+
 #include "kassembled.cuh"
 #include "kernels.h"
 
 namespace dgsl {
 
 constexpr int kCgConsumers = 128;                // 4 warps, one matrix row per thread
-constexpr int kCgThreads = kCgConsumers + 64;    // + coupling warp + gather warp
 constexpr int kCouplingWarp = kCgConsumers / 32;
-constexpr int kGatherWarp = kCouplingWarp + 1;
+constexpr int kGatherWarp = kCouplingWarp + 1;   // the first of NGW gather warps
+// CTA size with NGW gather warps: the consumers, the coupling warp, the gather warps
+template <int NGW>
+struct CgThreads {
+  static constexpr int value = kCgConsumers + 32 + 32 * NGW;
+};
 
 template <typename T, typename V>
 struct CGParams {
@@ -349,8 +355,8 @@ __device__ __forceinline__ void cp_async8_ca(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-template <int NPHI, typename T, typename V, bool PRE>
-__global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
+template <int NPHI, typename T, typename V, bool PRE, int NGW>
+__global__ void __launch_bounds__(CgThreads<NGW>::value, 1) k_cg(CGParams<T, V> a) {
   using C = TileCfg<NPHI, T, V, PRE>;
   constexpr int S = C::S, TT = C::TT, TR = C::TR, NPAD = C::NPAD, NB = C::NB, CPB = C::CPB, VPC = C::VPC;
   constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG, VP = C::VP, NGP = C::NGP, NOWN = C::NOWN;
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&gfull[i], 32);
+      mbar_init(&gfull[i], 32 * NGW);
       mbar_init(&empty[i], kCgConsumers / 32);
     }
     s_stop = 0;
@@ -461,18 +467,20 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
     return;
   }
 
-  if (warp == kGatherWarp) {
-    // ---- gather producer (32 lanes): cp.async of r, w, s of the coupled
+  if (warp >= kGatherWarp) {
+    // ---- gather producers (NGW warps): cp.async of r, w, s of the coupled
     // blocks and of the own p, x (PRE: p, x, u) and areas, after the pass has
-    // been opened
-    constexpr int NBL = (NB + 31) / 32;
+    // been opened; gather thread gl takes the blocks gl, gl + 32 NGW, ...
+    constexpr int GT = 32 * NGW;
+    const int gl = (warp - kGatherWarp) * 32 + lane;
+    constexpr int NBL = (NB + GT - 1) / GT;
     int cn[NBL];
     auto load_cols = [&](unsigned gg, int (&c)[NBL]) {
       const int tri0 = ((int)blockIdx.x + (int)(gg % (unsigned)nq) * (int)nb) * TT;
       const int nt = min(TT, ne - tri0);
 #pragma unroll
       for (int j = 0; j < NBL; ++j) {
-        const int b = lane + 32 * j;
+        const int b = gl + GT * j;
         c[j] = b < 4 * nt ? __ldg(a.cols + (size_t)(b & 3) * a.ne_pad + tri0 + (b >> 2)) : -1;
       }
     };
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
 #pragma unroll
       for (int j = 0; j < NBL; ++j) {
         if (cc[j] < 0) continue;
-        const int b = lane + 32 * j;
+        const int b = gl + GT * j;
         const int64_t src = (int64_t)cc[j] * NPAD;
         unsigned char* d = st + C::GATHER + (size_t)b * NPAD * sizeof(V);
 #pragma unroll
@@ -546,14 +554,14 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CGParams<T, V> a) {
         }
       }
       const int own = nt * CPB;  // 16-byte chunks of one own vector
-      for (int c = lane; c < NOWN * own; c += 32) {
+      for (int c = gl; c < NOWN * own; c += GT) {
         const int v = c >= 2 * own ? 2 : c >= own ? 1 : 0;  // own vector v: p, x, u
         const int cx = c - v * own;
         cp_async16(st + C::OWN + (size_t)v * TT * NPAD * sizeof(V) + cx * 16,
                    a.vec + (int64_t)v * npv + (int64_t)tri0 * NPAD + cx * VPC);
       }
       if (a.coefM != V(0))
-        for (int c = lane; c < nt; c += 32) cp_async8_ca(st + C::AREA + c * 8, a.area + tri0 + c);
+        for (int c = gl; c < nt; c += GT) cp_async8_ca(st + C::AREA + c * 8, a.area + tri0 + c);
       cp_async_arrive(&gfull[s]);
     }
     cp_async_wait_all();
@@ -769,28 +777,47 @@ cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_n
   return cudaGetLastError();
 }
 
+// Gather warps per CTA of the persistent CG, by degree and coupling width: a
+// table filled from an offline sweep (a deterministic lookup: the choice
+// depends on the system only, never on timing at run time, and does not
+// change the result's bits: the tiles, the grid and the reduction order are
+// the same).
+// DGSL_CG_GATHER_WARPS (1 or 2) overrides the table, for sweeps.
+int cg_gather_warps(const DevOp& op, size_t coupling_bytes, bool pre) {
+  if (const char* e = std::getenv("DGSL_CG_GATHER_WARPS")) {
+    const int v = std::atoi(e);
+    if (v == 1 || v == 2) return v;
+  }
+  // swept at 256^2, 512^2, 1024^2 (50-iteration launches): a second gather warp
+  // gains 3-6% with plain FP32 couplings at p = 2 and 3; at p = 1 and 4 it
+  // changes nothing, and with BF16 couplings it costs the third CTA per SM
+  // (up to 24% slower); FP64 and block-Jacobi kernels keep one
+  return (coupling_bytes == 4 && !pre && (op.nphi == 6 || op.nphi == 10)) ? 2 : 1;
+}
+
 namespace {
 template <class KernelT>
-int coop_blocks(KernelT kern, size_t dyn_smem) {
+int coop_blocks(KernelT kern, int threads, size_t dyn_smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kCgThreads, dyn_smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, dyn_smem);
   per = std::max(1, std::min(per, 8));
   return sms * per;
 }
 
-template <int NPHI, typename T, typename V, bool PRE>
-cudaError_t run_cg(const DevOp& op, const T* vals, const V* pinv, V coefK, V coefM, int mean_zero, V* x, V* r,
-                   double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
-                   int* grid_used) {
-  auto kern = k_cg<NPHI, T, V, PRE>;
+template <int NPHI, typename T, typename V, bool PRE, int NGW>
+cudaError_t run_cg_ngw(const DevOp& op, const T* vals, const V* pinv, V coefK, V coefM, int mean_zero, V* x, V* r,
+                       double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
+                       int* grid_used) {
+  auto kern = k_cg<NPHI, T, V, PRE, NGW>;
+  constexpr int threads = CgThreads<NGW>::value;
   using Cfg = TileCfg<NPHI, T, V, PRE>;
   const size_t dyn = Cfg::S * (size_t)Cfg::STAGE;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (err != cudaSuccess) return err;
   const int ntiles = (op.ne + Cfg::TT - 1) / Cfg::TT;
-  int blocks = std::min(coop_blocks(kern, dyn), w.max_parts);
+  int blocks = std::min(coop_blocks(kern, threads, dyn), w.max_parts);
   blocks = std::max(1, std::min(blocks, ntiles));
   if (grid_used) *grid_used = blocks;
   CGParams<T, V> a;
@@ -818,9 +845,22 @@ cudaError_t run_cg(const DevOp& op, const T* vals, const V* pinv, V coefK, V coe
   err = cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s);
   if (err != cudaSuccess) return err;
   void* args[] = {&a};
-  err = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kCgThreads), args, dyn, s);
+  err = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(threads), args, dyn, s);
   count_launch();
   return err;
+}
+
+template <int NPHI, typename T, typename V, bool PRE>
+cudaError_t run_cg(const DevOp& op, const T* vals, const V* pinv, V coefK, V coefM, int mean_zero, V* x, V* r,
+                   double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
+                   int* grid_used) {
+  // gather warps per CTA from the tuning table (the result does not depend on it:
+  // the tile order, the grid and the reduction order are the same)
+  if (cg_gather_warps(op, sizeof(T), PRE) == 2)
+    return run_cg_ngw<NPHI, T, V, PRE, 2>(op, vals, pinv, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w,
+                                          timeout_ns, s, grid_used);
+  return run_cg_ngw<NPHI, T, V, PRE, 1>(op, vals, pinv, coefK, coefM, mean_zero, x, r, stop_rel, max_iters, w,
+                                        timeout_ns, s, grid_used);
 }
 }  // namespace
 

@@ -104,6 +104,10 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NW], double* part, MGRed
   }
 }
 
+// Row of A x (difference form) with the coupled blocks gathered straight from
+// global memory (L1 / L2): staging a tile's blocks in shared memory first was
+// measured slower here (the extra CTA barriers per tile cost more than the
+// repeated loads).
 template <int NPHI, typename T, typename V>
 __device__ __forceinline__ V mg_row(const void* vals, const MGFine& f, int64_t row, const V* x) {
   V y = (V)f.coefK * assembled_row<NPHI, T, V, false>(static_cast<const T*>(vals), f.cols, f.ne_pad, f.n, row, x);
@@ -155,13 +159,16 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_update(MGFine f, const V* __r
   if (*((volatile const int*)&st->done)) return;
   constexpr int TB = kMGThreads / NPHI, ROWS = TB * NPHI;
   __shared__ V s_r[kMGThreads];
-  V alpha = V(0), mu_q = V(0);
-  if (!INIT) {
+  __shared__ V s_sc[2];
+  if (!INIT && threadIdx.x == 0) {  // scalars once per CTA (an FP64 division per thread is slow here)
     const double mq = f.mean_zero ? red_mv->out[1] / (double)f.n : 0.0;
     const double pq = red_mv->out[0] - mq * red_mv->out[2];
-    alpha = (V)(st->rz[par] / pq);
-    mu_q = (V)mq;
+    s_sc[0] = (V)(st->rz[par] / pq);
+    s_sc[1] = (V)mq;
   }
+  __syncthreads();
+  const V alpha = INIT ? V(0) : s_sc[0];
+  const V mu_q = INIT ? V(0) : s_sc[1];
   const int ntile = (f.ne + TB - 1) / TB;
   V a0 = V(0), a1 = V(0);
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
@@ -252,17 +259,23 @@ __global__ void k_csr_smooth0(int n, const int32_t* __restrict__ rp, const int32
   x[i] = wd[i] * b[i];
   t[i] = b[i] - acc;
 }
-// y = M x (restriction by R = P^T)
+// y = M x with one warp per row (the restriction's rows are long: an
+// aggregate's DOFs and their neighbours); the fixed shuffle tree keeps the
+// order deterministic
 template <typename V>
-__global__ void k_csr_spmv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const V* __restrict__ mv, const V* __restrict__ x, V* __restrict__ y, const MGState* st) {
+__global__ void k_csr_spmv_warp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const V* __restrict__ mv, const V* __restrict__ x, V* __restrict__ y,
+                                const MGState* st) {
   if (*((volatile const int*)&st->done)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
   V acc = V(0);
-  for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(mv[k], x[ci[k]], acc);
-  y[i] = acc;
+  for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) acc = fma(mv[k], x[ci[k]], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[i] = acc;
 }
+
 // x += P e
 template <typename V>
 __global__ void k_csr_prolong_add(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -288,14 +301,74 @@ __global__ void k_csr_smooth1(int n, const int32_t* __restrict__ rp, const int32
   y[i] = fma(wd[i], b[i] - acc, x[i]);
 }
 // x = C b (dense coarsest inverse, row-major nc x nc; one CTA)
+// Device view of one coarse level (pointers into MGSys's arrays).
 template <typename V>
-__global__ void k_dense_mv(int nc, const V* __restrict__ C, const V* __restrict__ b, V* __restrict__ x,
-                           const MGState* st) {
+struct MGLevelView {
+  int n, nnext;
+  const int32_t *Arp, *Aci, *Prp, *Pci, *Rrp, *Rci;
+  const V *Av, *wd, *Pv, *Rv;
+  V *b, *x, *t, *y;
+};
+
+// Levels this small run inside one CTA: one SM moves the data of a level of
+// 7,637 rows (256^2 mesh, level 1) in ~220 us against ~15 us for the grid
+// kernels, so only the last levels go there.
+constexpr int kTailRows = 1024;
+constexpr int kTailThreads = 1024;
+
+// The V-cycle from level l0 (right-hand side in its b) down to the dense
+// coarsest level and back, in ONE CTA (__syncthreads between the steps): the
+// same steps as the per-level kernels, for the levels too small to fill the
+// GPU, where a launch per step would cost more than its work.  The solution
+// of level l0 ends in its y (in x when l0 is the coarsest).
+template <typename V>
+__global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<V>* __restrict__ lv, int l0, int L,
+                                                             const V* __restrict__ C, const MGState* st) {
   if (*((volatile const int*)&st->done)) return;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    V acc = V(0);
-    for (int j = 0; j < nc; ++j) acc = fma(C[(size_t)i * nc + j], __ldg(b + j), acc);
-    x[i] = acc;
+  for (int l = l0; l + 1 < L; ++l) {
+    const MGLevelView<V> D = lv[l];
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+      V acc = V(0);
+      for (int k = D.Arp[i]; k < D.Arp[i + 1]; ++k) {
+        const int j = D.Aci[k];
+        acc = fma(D.Av[k], D.wd[j] * D.b[j], acc);
+      }
+      D.x[i] = D.wd[i] * D.b[i];
+      D.t[i] = D.b[i] - acc;
+    }
+    __syncthreads();
+    V* bn = lv[l + 1].b;
+    for (int i = threadIdx.x; i < D.nnext; i += blockDim.x) {
+      V acc = V(0);
+      for (int k = D.Rrp[i]; k < D.Rrp[i + 1]; ++k) acc = fma(D.Rv[k], D.t[D.Rci[k]], acc);
+      bn[i] = acc;
+    }
+    __syncthreads();
+  }
+  {
+    const MGLevelView<V> Z = lv[L - 1];
+    for (int i = threadIdx.x; i < Z.n; i += blockDim.x) {
+      V acc = V(0);
+      for (int j = 0; j < Z.n; ++j) acc = fma(C[(size_t)j * Z.n + i], Z.b[j], acc);
+      Z.x[i] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = L - 2; l >= l0; --l) {
+    const MGLevelView<V> D = lv[l];
+    const V* sol = l + 1 == L - 1 ? lv[l + 1].x : lv[l + 1].y;
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+      V acc = D.x[i];
+      for (int k = D.Prp[i]; k < D.Prp[i + 1]; ++k) acc = fma(D.Pv[k], sol[D.Pci[k]], acc);
+      D.x[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+      V acc = V(0);
+      for (int k = D.Arp[i]; k < D.Arp[i + 1]; ++k) acc = fma(D.Av[k], D.x[D.Aci[k]], acc);
+      D.y[i] = fma(D.wd[i], D.b[i] - acc, D.x[i]);
+    }
+    __syncthreads();
   }
 }
 
@@ -353,11 +426,19 @@ template <typename V, bool FIRST>
 __global__ void k_mg_dir(int64_t n, int mean_zero, const V* __restrict__ z, V* __restrict__ p, const MGRed* red_up,
                          const MGRed* red_post, MGState* st, int par) {
   if (*((volatile const int*)&st->done)) return;
-  const double rr = red_up->out[0], sr = red_up->out[1];
-  const double mz = mean_zero ? red_post->out[1] / (double)n : 0.0;
-  const double rz = red_post->out[0] - mz * sr;
-  const double beta = FIRST ? 0.0 : rz / st->rz[par];
-  const V mzv = (V)mz, bv = (V)beta;
+  __shared__ double s_sc[4];
+  if (threadIdx.x == 0) {  // scalars once per CTA (an FP64 division per thread is slow here)
+    const double rr = red_up->out[0], sr = red_up->out[1];
+    const double mz = mean_zero ? red_post->out[1] / (double)n : 0.0;
+    const double rz = red_post->out[0] - mz * sr;
+    s_sc[0] = rr;
+    s_sc[1] = mz;
+    s_sc[2] = rz;
+    s_sc[3] = FIRST ? 0.0 : rz / st->rz[par];
+  }
+  __syncthreads();
+  const double rr = s_sc[0], rz = s_sc[2];
+  const V mzv = (V)s_sc[1], bv = (V)s_sc[3];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = FIRST ? z[i] - mzv : fma(bv, p[i], z[i] - mzv);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -520,6 +601,8 @@ struct MGSys {
   std::vector<MGLevelD<float>> lf;
   std::vector<MGLevelD<double>> ld;
   void* C = nullptr;
+  void* views = nullptr;       // MGLevelView<V>[levels] on the device
+  int tail = 0;                // first level run by k_coarse_tail
   // kMGBatch PCG iterations captured once as a CUDA graph (on a private
   // stream: the caller's may be the legacy stream, which cannot capture) and
   // replayed on the caller's stream; it writes the solution vector exec_x
@@ -586,6 +669,15 @@ void upload_levels(MGSys& m, std::vector<MGLevelD<V>>& out, cudaStream_t s) {
     D.y = mg_alloc<V>(m.allocs, m.bytes, D.n);
   }
   m.C = upload(m, cast<V>(m.host.C), s);
+  std::vector<MGLevelView<V>> views(lv.size());
+  m.tail = (int)lv.size() - 1;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const MGLevelD<V>& D = out[l];
+    views[l] = MGLevelView<V>{D.n, D.nnext, D.Arp, D.Aci, D.Prp, D.Pci, D.Rrp, D.Rci, D.Av, D.wd, D.Pv, D.Rv,
+                              D.b, D.x, D.t, D.y};
+  }
+  for (int l = (int)lv.size() - 1; l >= 0 && out[l].n <= kTailRows; --l) m.tail = l;
+  m.views = upload(m, views, s);
 }
 
 }  // namespace
@@ -693,17 +785,18 @@ struct MGRun {
     k_mg_resid_restrict<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.w), m.st);
     k_mg_vgather<V><<<g1(m.host.nv), 256, 0, s>>>(m.host.nv, m.v2t_ptr, m.v2t, v(m.w), lv[0].b, m.st);
     launches += 2;
-    const int L = (int)lv.size();
-    for (int l = 0; l + 1 < L; ++l) {
+    const int L = (int)lv.size(), T = m.tail;
+    for (int l = 0; l < T; ++l) {
       auto& D = lv[l];
       k_csr_smooth0<V><<<g1(D.n), 256, 0, s>>>(D.n, D.Arp, D.Aci, D.Av, D.wd, D.b, D.x, D.t, m.st);
-      k_csr_spmv<V><<<g1(D.nnext), 256, 0, s>>>(D.nnext, D.Rrp, D.Rci, D.Rv, D.t, lv[l + 1].b, m.st);
+      k_csr_spmv_warp<V><<<g1(32 * (int64_t)D.nnext), 256, 0, s>>>(D.nnext, D.Rrp, D.Rci, D.Rv, D.t, lv[l + 1].b,
+                                                                   m.st);
       launches += 2;
     }
-    k_dense_mv<V><<<1, 256, 0, s>>>(lv[L - 1].n, v(m.C), lv[L - 1].b, lv[L - 1].x, m.st);
+    k_coarse_tail<V><<<1, kTailThreads, 0, s>>>(static_cast<const MGLevelView<V>*>(m.views), T, L, v(m.C), m.st);
     ++launches;
-    V* sol = lv[L - 1].x;
-    for (int l = L - 2; l >= 0; --l) {
+    V* sol = T == L - 1 ? lv[T].x : lv[T].y;
+    for (int l = T - 1; l >= 0; --l) {
       auto& D = lv[l];
       k_csr_prolong_add<V><<<g1(D.n), 256, 0, s>>>(D.n, D.Prp, D.Pci, D.Pv, sol, D.x, m.st);
       k_csr_smooth1<V><<<g1(D.n), 256, 0, s>>>(D.n, D.Arp, D.Aci, D.Av, D.wd, D.b, D.x, D.y, m.st);

@@ -293,6 +293,13 @@ void mg_build_levels(MGHost& mg, const CsrD& A0, const CsrD& G0, bool singular) 
   mg.nc = mg.lv.back().A.n;
   if (mg.nc > 16 * kMGCoarsest) throw Error(DGSL_EINVAL, "multigrid: the aggregation stalled above the dense size");
   mg.C = coarsest_inverse(mg.lv.back().A, singular);
+  const int nc = mg.nc;  // exactly symmetric (the kernels read it by columns)
+  for (int i = 0; i < nc; ++i)
+    for (int j = i + 1; j < nc; ++j) {
+      const double v = 0.5 * (mg.C[(size_t)i * nc + j] + mg.C[(size_t)j * nc + i]);
+      mg.C[(size_t)i * nc + j] = v;
+      mg.C[(size_t)j * nc + i] = v;
+    }
 }
 
 }  // namespace dgsl
