@@ -18,6 +18,7 @@ time FP64 baseline), and the oracle timed on the host cores (cpu_baseline).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -79,6 +80,9 @@ def parse_args(argv=None):
     ap.add_argument("--batch-paths", type=str, default="multigrid",
                     help="comma list of engine, engine-bj, multigrid (each path's systems stay on the "
                          "operators: at the full 512-solve size run one path per process)")
+    ap.add_argument("--batch-engine-iters", type=int, default=0,
+                    help="batch workload: cap the engine paths at this many CG passes per refinement step and "
+                         "one refinement (a throughput probe of the engine at full size: its solves stop unconverged)")
     ap.add_argument("--batch-split", action="store_true",
                     help="batch workload: also time the right-hand sides as one request each")
     ap.add_argument("--rhs", type=int, default=8)
@@ -364,6 +368,19 @@ def gpu_leg(args, rank, world, local):
                          refinements=sum(i.refinements for i in m_infos) / args.steps,
                          relres_max=max(i.relres for i in m_infos), first_run_s=setup_s,
                          launches_per_step=(dgsl.dgsl_launch_count() - l1) / args.steps)
+        # the same multigrid stage in FP64 throughout (one untimed run builds
+        # the FP64 hierarchies): the iterations the FP32 inner solves cost extra
+        if args.precision != "f64":
+            om64 = dgsl.solve_opts(tol=WORKLOAD["tol"], precision=dgsl.PREC_F64, precond=dgsl.PRECOND_MULTIGRID)
+            with torch.cuda.stream(stream):
+                st.run(stream, om64)
+                ev0.record(stream)
+                f_infos = st.run(stream, om64)
+                ev1.record(stream)
+            stream.synchronize()
+            res["mg"]["fp64"] = dict(ms=ev0.elapsed_time(ev1), schur_iters=f_infos[0].iters,
+                                     helm_iters=sum(i.iters for i in f_infos[1:]),
+                                     relres_max=max(i.relres for i in f_infos))
     # ---- semi-Lagrangian transport of the stage's main-grid velocity (two
     # components) by itself over dt, on the same mesh (Sec. 2.5, eq. intstage)
     if not args.no_sl:
@@ -393,9 +410,15 @@ def fourier_rhs(op, seed, dt):
     amplitude ~ |k|^-2); Mbar applied by the library (Helmholtz with nu_dt = 0)."""
     import torch
     from paper_2401_17806_gb300 import synth
-    xy = op.node_coords(0)
-    f = synth.fourier_field(xy[:, 0], xy[:, 1], synth.fourier_modes(seed)) * dt * dt
-    fd = torch.tensor(f, dtype=torch.float64, device="cuda")
+    xy = torch.tensor(op.node_coords(0), device="cuda")
+    k, amp, phase = synth.fourier_modes(seed)
+    # the field sum evaluated on the device (synth.fourier_field's formula; the
+    # host loop over 32 modes took minutes on the 10M-node pool meshes)
+    fd = torch.zeros(xy.shape[0], dtype=torch.float64, device="cuda")
+    tp = 2.0 * math.pi
+    for (kx, ky), a, ph in zip(k, amp, phase):
+        fd += float(a) * torch.cos(tp * (float(kx) * xy[:, 0] + float(ky) * xy[:, 1]) + float(ph))
+    fd *= dt * dt
     b = torch.empty_like(fd)
     op.dgsl_apply_helmholtz(0.0, fd, b)
     return b
@@ -579,7 +602,13 @@ def sl_leg(args):
     ms = ev0.elapsed_time(ev1) / calls
     pv, pt = sl_flops(p, 2)
     flops = pv * visits + pt * nt
-    peak = 1250.0  # GFLOP/s: nominal GB300 FP64 (Blackwell Ultra)
+    # the FP64 FMA rate measured on this device by the library's probe (the
+    # walk is FP64-pipe bound); the nominal 1.25 TFLOP/s only if it fails
+    try:
+        peak = dgsl.dgsl_measure_fma_rate(fp64=True) / 1e9
+        peak_src = "measured: dgsl_measure_fma_rate (event-timed FP64 FMA chains, 2 flop per FMA)"
+    except dgsl.DgslError:
+        peak, peak_src = 1250.0, "nominal GB300 FP64 rate (the probe failed)"
     line = {
         "metric": "semi-Lagrangian Gauss-point trajectories/s", "workload": "sl", "data": "synthetic",
         "value": nt / (ms * 1e-3), "unit": "trajectories/s", "ms_per_call": ms, "steps": args.steps,
@@ -592,7 +621,7 @@ def sl_leg(args):
                          % int((op.n_tri * (144 + 2 * 8 * op.n_phi * 3)) / 1e6)},
         "roofline": {"kernel": "k_sl_walk", "bound": "alu", "achieved": flops / (ms * 1e-3) / 1e9,
                      "peak": peak, "unit": "GFLOP/s (FP64)", "frac": flops / (ms * 1e-3) / 1e9 / peak,
-                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+                     "peak_source": peak_src,
                      "flops_per_cell_visit": pv, "flops_per_trajectory": pt},
         "clocks": clk,
         "stages": sl_stage_timings(op, vbar, cstar, dt, calls, stream, nt),
@@ -898,7 +927,9 @@ def batch_leg(args):
     for name in args.batch_paths.split(","):
         pc = {"engine": dgsl.PRECOND_NONE, "engine-bj": dgsl.PRECOND_BLOCK_JACOBI,
               "multigrid": dgsl.PRECOND_MULTIGRID}[name]
-        opts = dgsl.engine_opts(precision=prec, precond=pc)
+        capped = args.batch_engine_iters > 0 and pc != dgsl.PRECOND_MULTIGRID
+        opts = (dgsl.engine_opts(precision=prec, precond=pc, max_iters=args.batch_engine_iters, max_refine=1)
+                if capped else dgsl.engine_opts(precision=prec, precond=pc))
         t = time.perf_counter()
         if pc != dgsl.PRECOND_NONE:  # build every system's preconditioner once, outside the timing
             dgsl.dgsl_cg_solve_batch(reqs, dgsl.engine_opts(precision=prec, precond=pc, max_iters=1, max_refine=1))
@@ -913,6 +944,9 @@ def batch_leg(args):
                  "iters_p50": iters[len(iters) // 2], "iters_max": iters[-1],
                  "max_relres": max(i.relres for i in infos), "gpu_launches": launches,
                  "preconditioner_setup_s": setup_s}
+        if capped:
+            entry["capped_passes"] = args.batch_engine_iters
+            entry["note"] = "throughput probe: every solve stops after the capped passes (not converged)"
         if name == "engine":
             # the engine's algorithmic bytes: every request's passes over its couplings
             alg = sum(i.iters * op.n_dof * engine_bytes_per_row_pass(op.n_phi, cb, R) for i, op in zip(infos, ops))
@@ -1046,6 +1080,7 @@ def serve_trace(pool, svc, rate, seconds, seed, precond, budget, nmax, max_rhs=8
     done_t = np.full(len(arr), np.nan)
     status = np.zeros(len(arr), dtype=np.int64)
     relres = np.full(len(arr), np.nan)
+    floor = np.zeros(len(arr))
     start = time.perf_counter()
     i = 0
     while True:
@@ -1066,6 +1101,7 @@ def serve_trace(pool, svc, rate, seconds, seed, precond, budget, nmax, max_rhs=8
                     done_t[owner[t]] = tnow
                     status[owner[t]] = inf.status
                     relres[owner[t]] = inf.relres
+                    floor[owner[t]] = inf.relres_floor
                 else:
                     keep.append(t)
             outstanding = keep
@@ -1087,7 +1123,8 @@ def serve_trace(pool, svc, rate, seconds, seed, precond, budget, nmax, max_rhs=8
     blat = np.array(blat)
     nsolves = int(sum(int(k) for k, f in zip(kr, fin) if f))
     failed = [{"N": int(Nr[j]), "p": int(pr[j]), "rhs": int(kr[j]), "status": int(status[j]),
-               "relres": float(relres[j])} for j in range(len(arr)) if fin[j] and status[j] != 0][:10]
+               "relres": float(relres[j]), "fp64_floor": float(floor[j])}
+              for j in range(len(arr)) if fin[j] and status[j] != 0][:10]
     return {
         "rate": rate, "requests": int(len(arr)), "completed": int(fin.sum()),
         "right_hand_sides": int(kr.sum()), "all_converged": bool(np.all(status[fin] == 0)), "not_converged": failed,
@@ -1482,6 +1519,15 @@ def main():
             "hierarchy_build_and_first_stage_s": mg["first_run_s"],
             "kernel_launches_per_step": mg["launches_per_step"],
         }
+        if "fp64" in mg:
+            f = mg["fp64"]
+            line["multigrid"]["fp64_multigrid"] = {
+                "what": "the same stage with the multigrid PCG in FP64 throughout (one step)",
+                "ms_per_step": f["ms"], "schur_iters_per_step": f["schur_iters"],
+                "helmholtz_iters_per_step": f["helm_iters"], "max_relres": f["relres_max"],
+                "fp32_ir_iteration_overhead": (mg["schur_iters"] + mg["helm_iters"])
+                / max(1, f["schur_iters"] + f["helm_iters"]) - 1.0,
+                "fp32_ir_stage_speedup": f["ms"] / (mg["ms"] / args.steps)}
     if serve is not None:
         line["serving"] = serve
     if "sl" in res:

@@ -319,6 +319,14 @@ typedef struct {
                             solve's stream) */
   int32_t grid;          /* CTAs of the persistent CG launches */
   int32_t pad;
+  double relres_floor;   /* dgsl_cg_solve, status DGSL_ENOTCONV only (else 0):
+                            the expected relative residual of the exact
+                            solution rounded to FP64, from the returned x and
+                            the FP64 couplings (each value's rounding error
+                            uniform in +-2^-53, independent).  No FP64 vector
+                            has a residual far below it: a relres within a
+                            small multiple of it is at FP64's own accuracy.
+                            The engine and the no-allocation solve leave 0. */
 } dgsl_solve_info;
 
 /* Solves A x = b for kind DGSL_SCHUR (A = S with dt = coef) or
@@ -394,6 +402,15 @@ void dgsl_default_solve_opts(dgsl_solve_opts* opts);
  * the kernel records the timeout and returns; *status receives DGSL_ETIMEOUT
  * if it did (DGSL_OK otherwise) and the device stays usable.  Synchronous. */
 int dgsl_selftest_wait_timeout(int device, int which, double timeout_s, int* status);
+
+/* Measured FMA throughput of the device (no counterpart in the paper: the
+ * denominator of the roofline of the FP64-ALU-bound kernels, the
+ * semi-Lagrangian walk above all).  fp64 = 1 times FP64, 0 FP32: 3 warm-up and
+ * 10 timed launches (CUDA events on a private stream) of SMs x 8 blocks of 256
+ * threads, each thread running 8 independent FMA chains; *flops_per_s receives
+ * 2 x FMAs / second.  Allocates a small output buffer (freed before return).
+ * Synchronous; DGSL_EINVAL for a bad argument, DGSL_ECUDA on a CUDA error. */
+int dgsl_measure_fma_rate(int device, int fp64, double* flops_per_s);
 
 /* Same solve as dgsl_cg_solve (precond must be DGSL_PRECOND_NONE: the fixed
  * scratch has no room for the preconditioner's blocks; else DGSL_EINVAL), for

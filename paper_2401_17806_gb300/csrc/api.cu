@@ -532,11 +532,8 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
         DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r64, w.d64, std::max(need, 1e-15), mg_budget, s, &mr));
       } else {
         DGSL_CUDA(launch_scale_to_f32(w.r64, 1.0 / rnorm, w.r32, n, s));
-        // the inner target is not loosened near the outer tolerance (as it is
-        // for the plain CG): a multigrid iteration is cheap next to a refinement
-        // step, and a loose inner solve stalled the refinement of some
-        // right-hand sides at 1e-10..5e-10 on 512^2 and 1024^2 meshes, p >= 3
-        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, o.inner_tol), mg_budget, s, &mr));
+        DGSL_CUDA(dgsl::mg_pcg(mgh->sys.get(), d, w.r32, w.d32, std::min(1.0, std::max(o.inner_tol, need)),
+                               mg_budget, s, &mr));
       }
       w.h_res->iters = mr.iters;
       w.h_res->status = 0;
@@ -585,6 +582,15 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
     DGSL_CUDA(launch_sum_to_first(w.part2, nparts, s));
     DGSL_CUDA(launch_remove_mean_f64(x, w.part2, n, s));
   }
+  // a solve that stopped short of the tolerance reports the FP64 rounding
+  // floor of its residual: the relative residual of the returned x's exact
+  // counterpart rounded to FP64 (expected value; see k_residual_floor_f64)
+  double floor_rel = 0.0;
+  if (status == DGSL_ENOTCONV && bnorm2 > 0.0) {
+    DGSL_CUDA(launch_residual_floor_f64(d, coefK, coefM, x, w.part2, w.max_parts, &nparts, s));
+    const Sums sf = read_sums(op, w.part2, nparts, s);
+    floor_rel = std::sqrt(sf.s / 3.0) * std::ldexp(1.0, -53) / std::sqrt(bnorm2);
+  }
   DGSL_CUDA(cudaStreamSynchronize(s));
   if (info) {
     info->status = status;
@@ -595,6 +601,7 @@ int solve_one(dgsl_operator* op, int kind, double coef, const double* b, double*
     info->cg_kernel_ms = kernel_ms;
     info->grid = grid_used;
     info->pad = 0;
+    info->relres_floor = floor_rel;
   }
   return status;
 }
@@ -841,6 +848,7 @@ int solve_one_noalloc(const DevOp& d, unsigned char* base, int max_parts, int ki
     info->cg_kernel_ms = 0.0;
     info->grid = grid_used;
     info->pad = 0;
+    info->relres_floor = 0.0;
   }
   return status;
 }
@@ -884,6 +892,39 @@ extern "C" int dgsl_cg_solve_noalloc(const dgsl_operator* cop, int kind, double 
     if (worst != DGSL_OK) g_last_error = worst == DGSL_ENOTCONV ? "not converged within max_iters" : "device wait timed out";
     return worst;
   });
+}
+
+// ------------------------------------------------------------ FMA rate probe
+extern "C" int dgsl_measure_fma_rate(int device, int fp64, double* flops_per_s) {
+  if (!flops_per_s || (fp64 != 0 && fp64 != 1)) return fail(DGSL_EINVAL, "fp64 must be 0 or 1 and the output given");
+  try {
+    DGSL_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    DGSL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int blocks = sms * 8, iters = fp64 ? 4096 : 65536, reps = 10;
+    void* out = nullptr;
+    DGSL_CUDA(cudaMalloc(&out, (size_t)blocks * 256 * 8));
+    std::unique_ptr<void, void (*)(void*)> guard(out, [](void* q) { cudaFree(q); });
+    cudaStream_t st = nullptr;
+    DGSL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    std::unique_ptr<CUstream_st, void (*)(cudaStream_t)> sguard(st, [](cudaStream_t q) { cudaStreamDestroy(q); });
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DGSL_CUDA(cudaEventCreate(&e0));
+    std::unique_ptr<CUevent_st, void (*)(cudaEvent_t)> g0(e0, [](cudaEvent_t q) { cudaEventDestroy(q); });
+    DGSL_CUDA(cudaEventCreate(&e1));
+    std::unique_ptr<CUevent_st, void (*)(cudaEvent_t)> g1(e1, [](cudaEvent_t q) { cudaEventDestroy(q); });
+    for (int r = 0; r < 3; ++r) DGSL_CUDA(launch_fma_rate(fp64, out, blocks, iters, st));  // warm-up
+    DGSL_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) DGSL_CUDA(launch_fma_rate(fp64, out, blocks, iters, st));
+    DGSL_CUDA(cudaEventRecord(e1, st));
+    DGSL_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DGSL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *flops_per_s = 2.0 * (double)blocks * 256.0 * 8.0 * (double)iters * reps / (ms * 1e-3);
+    return DGSL_OK;
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  }
 }
 
 // ------------------------------------------------------------ failure-detection self-test

@@ -594,6 +594,31 @@ HostBlocks build_blocks(const HostMesh& hm, const RefOps& ro) {
       }
     });
   }
+  // S = G^T Mhat^-1 G is symmetric (eq. pressure_final), but the two sides of
+  // an edge compute their transposed blocks with different rounding.  The
+  // stored couplings are made exactly symmetric (each pair of transposed
+  // entries replaced by its mean), as CG assumes: with the difference form's
+  // zero row sums the column sums then vanish too, and the FP32 / BF16 copies
+  // rounded from these values are symmetric as well.
+  parallel_for(nd, [&](int64_t e) {
+    double* A = &hb.Ko[((size_t)hb.elr[2 * e] * 3 + hb.eloc[2 * e]) * n * n];
+    double* B = &hb.Ko[((size_t)hb.elr[2 * e + 1] * 3 + hb.eloc[2 * e + 1]) * n * n];
+    for (int k = 0; k < n; ++k)
+      for (int l = 0; l < n; ++l) {
+        const double v = 0.5 * (A[(size_t)k * n + l] + B[(size_t)l * n + k]);
+        A[(size_t)k * n + l] = v;
+        B[(size_t)l * n + k] = v;
+      }
+  });
+  parallel_for(ne, [&](int64_t i) {
+    double* D = &hb.Kd[(size_t)i * n * n];
+    for (int k = 0; k < n; ++k)
+      for (int l = k + 1; l < n; ++l) {
+        const double v = 0.5 * (D[(size_t)k * n + l] + D[(size_t)l * n + k]);
+        D[(size_t)k * n + l] = v;
+        D[(size_t)l * n + k] = v;
+      }
+  });
   return hb;
 }
 

@@ -450,6 +450,52 @@ __global__ void __launch_bounds__(256) k_residual_f64(const double* __restrict__
   }
 }
 
+// sum over rows of sum_c (a_c x_c)^2, a_c the row's FP64 couplings of
+// coefK K + coefM Mbar (the self coupling included): with each x_c rounded to
+// FP64 (a relative error uniform in +-2^-53, independent between values) the
+// residual moves by a vector of expected squared norm 2^-106 / 3 times this
+// sum.  That is the residual the exactly rounded solution would show: the
+// floor under which no FP64 iterate's residual can be driven.
+template <int NPHI>
+__global__ void __launch_bounds__(256) k_residual_floor_f64(const double* __restrict__ vals,
+                                                            const int32_t* __restrict__ cols, int ne, int64_t n,
+                                                            const double* __restrict__ area,
+                                                            const double* __restrict__ Mref, double coefK,
+                                                            double coefM, const double* __restrict__ x,
+                                                            double* __restrict__ part) {
+  constexpr int NC = 4 * NPHI;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(row / NPHI), k = (int)(row - (int64_t)i * NPHI);
+    int col[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) col[b] = __ldg(cols + (size_t)b * ne + i);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int b = c / NPHI, kk = c % NPHI;
+      double a = coefK * __ldg(vals + ((size_t)(c / 2) * n + row) * 2 + c % 2);
+      if (b == 0 && coefM != 0.0) a += coefM * __ldg(area + i) * __ldg(Mref + k * NPHI + kk);
+      const double t = a * __ldg(x + (size_t)col[b] * NPHI + kk);
+      acc[0] = fma(t, t, acc[0]);
+    }
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = acc[0];
+    part[2 * blockIdx.x + 1] = acc[1];
+  }
+}
+
+cudaError_t launch_residual_floor_f64(const DevOp& op, double coefK, double coefM, const double* x, double* part,
+                                      int max_parts, int* nparts, cudaStream_t s) {
+  const int g = std::min(grid_for(op.n), max_parts);
+  *nparts = g;
+  DGSL_DISPATCH_P(op.p, (void)NPSI; k_residual_floor_f64<NPHI><<<g, 256, 0, s>>>(
+                            op.K64, op.cols, op.ne_pad, op.n, op.area, op.Mref, coefK, coefM, x, part));
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual_f64(const DevOp& op, double coefK, double coefM, int mean_zero, const double* b,
                                 const double* x, double b_mean, double* r, double* part, int max_parts, int* nparts,
                                 cudaStream_t s) {

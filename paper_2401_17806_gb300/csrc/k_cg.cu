@@ -356,7 +356,7 @@ __device__ __forceinline__ void cp_async8_ca(void* dst, const void* src) {
 }
 
 template <int NPHI, typename T, typename V, bool PRE, int NGW>
-__global__ void __launch_bounds__(CgThreads<NGW>::value, 1) k_cg(CGParams<T, V> a) {
+__device__ __forceinline__ void cg_body(const CGParams<T, V>& a) {
   using C = TileCfg<NPHI, T, V, PRE>;
   constexpr int S = C::S, TT = C::TT, TR = C::TR, NPAD = C::NPAD, NB = C::NB, CPB = C::CPB, VPC = C::VPC;
   constexpr int VEC = C::VEC, NC = C::NC, NG = C::NG, VP = C::VP, NGP = C::NGP, NOWN = C::NOWN;
@@ -749,6 +749,20 @@ __global__ void __launch_bounds__(CgThreads<NGW>::value, 1) k_cg(CGParams<T, V> 
   }
 }
 
+template <int NPHI, typename T, typename V, bool PRE, int NGW>
+__global__ void __launch_bounds__(CgThreads<NGW>::value, 1) k_cg(CGParams<T, V> a) {
+  cg_body<NPHI, T, V, PRE, NGW>(a);
+}
+
+// The same kernel with at most 96 registers per thread.  A CTA of 6 warps then
+// needs 5 warps' registers per SM sub-partition at 3 CTAs per SM (5 x 32 x 96
+// = 15,360 of 16,384); at the uncapped 102 registers (FP32 couplings, p = 2)
+// only 2 CTAs fit, although their shared memory would allow 3.
+template <int NPHI, typename T, typename V, bool PRE, int NGW>
+__global__ void __maxnreg__(96) k_cg_r96(CGParams<T, V> a) {
+  cg_body<NPHI, T, V, PRE, NGW>(a);
+}
+
 // Self-test of the bounded waits: `which` = 0 runs the grid barrier of this
 // file expecting one CTA more than the launch has; 1 waits on an mbarrier no
 // copy will complete.  Both waits must give up after timeout_ns, record
@@ -767,6 +781,32 @@ __global__ void k_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns
     if (threadIdx.x == 0 && !mbar_wait_bounded(&mb, 0u, timeout_ns)) atomicCAS(&bar->status, kStatusOk, kStatusTimeout);
     __syncthreads();
   }
+}
+
+// FMA throughput probe: every thread runs 8 independent chains x <- x a + b
+// (no memory traffic inside the loop); the chains' sum is stored so that
+// nothing is optimised away.
+template <typename V>
+__global__ void __launch_bounds__(256) k_fma_rate(V* out, int iters, V a, V b) {
+  V x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = (V)(threadIdx.x + i) * (V)1e-3;
+  for (int k = 0; k < iters; ++k)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  V acc = V(0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc += x[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+cudaError_t launch_fma_rate(int fp64, void* out, int blocks, int iters, cudaStream_t s) {
+  if (fp64)
+    k_fma_rate<double><<<blocks, 256, 0, s>>>(static_cast<double*>(out), iters, 0.999999, 1e-7);
+  else
+    k_fma_rate<float><<<blocks, 256, 0, s>>>(static_cast<float*>(out), iters, 0.999999f, 1e-7f);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s) {
@@ -789,13 +829,26 @@ int cg_gather_warps(const DevOp& op, size_t coupling_bytes, bool pre) {
     if (v == 1 || v == 2) return v;
   }
   // swept at 256^2, 512^2, 1024^2 (50-iteration launches): a second gather warp
-  // gains 3-6% with plain FP32 couplings at p = 2 and 3; at p = 1 and 4 it
-  // changes nothing, and with BF16 couplings it costs the third CTA per SM
-  // (up to 24% slower); FP64 and block-Jacobi kernels keep one
-  return (coupling_bytes == 4 && !pre && (op.nphi == 6 || op.nphi == 10)) ? 2 : 1;
+  // gains 3-6% with plain FP32 couplings at p = 3; at p = 1 and 4 it changes
+  // nothing, and with BF16 couplings it costs the third CTA per SM (up to 24%
+  // slower).  FP32 at p = 2 keeps one: its register-capped kernel then fits 3
+  // CTAs per SM (two gather warps would need 7 warps' registers per CTA).  FP64
+  // and block-Jacobi kernels keep one.
+  return (coupling_bytes == 4 && !pre && op.nphi == 10) ? 2 : 1;
 }
 
 namespace {
+// FP32 couplings at p = 2 with one gather warp run the register-capped kernel
+// (3 CTAs per SM instead of 2); every other configuration the plain one.  Only
+// the kernel selected is instantiated.
+template <int NPHI, typename T, typename V, bool PRE, int NGW>
+constexpr auto cg_kernel() {
+  if constexpr (NPHI == 6 && sizeof(T) == 4 && !PRE && NGW == 1)
+    return k_cg_r96<NPHI, T, V, PRE, NGW>;
+  else
+    return k_cg<NPHI, T, V, PRE, NGW>;
+}
+
 template <class KernelT>
 int coop_blocks(KernelT kern, int threads, size_t dyn_smem) {
   int dev = 0, sms = 0, per = 0;
@@ -810,7 +863,7 @@ template <int NPHI, typename T, typename V, bool PRE, int NGW>
 cudaError_t run_cg_ngw(const DevOp& op, const T* vals, const V* pinv, V coefK, V coefM, int mean_zero, V* x, V* r,
                        double stop_rel, int max_iters, const CGWork& w, uint64_t timeout_ns, cudaStream_t s,
                        int* grid_used) {
-  auto kern = k_cg<NPHI, T, V, PRE, NGW>;
+  auto kern = cg_kernel<NPHI, T, V, PRE, NGW>();
   constexpr int threads = CgThreads<NGW>::value;
   using Cfg = TileCfg<NPHI, T, V, PRE>;
   const size_t dyn = Cfg::S * (size_t)Cfg::STAGE;

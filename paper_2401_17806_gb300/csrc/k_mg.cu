@@ -25,6 +25,7 @@
 // reading anything back; the host checks convergence every few iterations,
 // and a finished solve turns the remaining launches into early returns.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "kassembled.cuh"
@@ -107,10 +108,12 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NW], double* part, MGRed
 // Row of A x (difference form) with the coupled blocks gathered straight from
 // global memory (L1 / L2): staging a tile's blocks in shared memory first was
 // measured slower here (the extra CTA barriers per tile cost more than the
-// repeated loads).
+// repeated loads).  x is always one of the system's own vectors (allocated
+// here, so aligned): for even N_phi the blocks are read two values per load.
 template <int NPHI, typename T, typename V>
 __device__ __forceinline__ V mg_row(const void* vals, const MGFine& f, int64_t row, const V* x) {
-  V y = (V)f.coefK * assembled_row<NPHI, T, V, false>(static_cast<const T*>(vals), f.cols, f.ne_pad, f.n, row, x);
+  V y = (V)f.coefK * assembled_row<NPHI, T, V, false, DiffForm<T>::value, NPHI % 2 == 0>(
+                         static_cast<const T*>(vals), f.cols, f.ne_pad, f.n, row, x);
   if (f.coefM != 0.0) y += (V)f.coefM * mass_row<NPHI, V, false>(f.area, f.Mref, row, x);
   return y;
 }
@@ -243,6 +246,35 @@ __global__ void k_mg_vgather(int nv, const int32_t* __restrict__ ptr, const int3
 }
 
 // ---- coarse levels (CSR, one thread per row)
+// init + sum_k av[k] (s[ci[k]] x[ci[k]]) (SCALE) or init + sum_k av[k] x[ci[k]]
+// over k in [k0, k1), accumulated in k order.  The loads of four entries are issued
+// before their products, so a row costs one dependent load chain per four
+// entries instead of one per entry (the coarse levels are latency-bound).
+template <typename V, bool SCALE>
+__device__ __forceinline__ V csr_dot(const int32_t* __restrict__ ci, const V* __restrict__ av,
+                                     const V* __restrict__ s, const V* x, int k0, int k1, V init = V(0)) {
+  V acc = init;
+  int k = k0;
+  for (; k + 4 <= k1; k += 4) {
+    int j[4];
+    V a[4], v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) j[u] = ci[k + u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = av[k + u];
+      v[u] = SCALE ? s[j[u]] * x[j[u]] : x[j[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fma(a[u], v[u], acc);
+  }
+  for (; k < k1; ++k) {
+    const int jj = ci[k];
+    acc = fma(av[k], SCALE ? s[jj] * x[jj] : x[jj], acc);
+  }
+  return acc;
+}
+
 // x = wd b;  t = b - A (wd b)
 template <typename V>
 __global__ void k_csr_smooth0(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -251,11 +283,7 @@ __global__ void k_csr_smooth0(int n, const int32_t* __restrict__ rp, const int32
   if (*((volatile const int*)&st->done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  V acc = V(0);
-  for (int k = rp[i]; k < rp[i + 1]; ++k) {
-    const int j = ci[k];
-    acc = fma(av[k], wd[j] * b[j], acc);
-  }
+  const V acc = csr_dot<V, true>(ci, av, wd, b, rp[i], rp[i + 1]);
   x[i] = wd[i] * b[i];
   t[i] = b[i] - acc;
 }
@@ -284,9 +312,7 @@ __global__ void k_csr_prolong_add(int n, const int32_t* __restrict__ rp, const i
   if (*((volatile const int*)&st->done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  V acc = x[i];
-  for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(pv[k], e[ci[k]], acc);
-  x[i] = acc;
+  x[i] = csr_dot<V, false>(ci, pv, nullptr, e, rp[i], rp[i + 1], x[i]);
 }
 // y = x + wd (b - A x)
 template <typename V>
@@ -296,8 +322,7 @@ __global__ void k_csr_smooth1(int n, const int32_t* __restrict__ rp, const int32
   if (*((volatile const int*)&st->done)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  V acc = V(0);
-  for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(av[k], x[ci[k]], acc);
+  const V acc = csr_dot<V, false>(ci, av, nullptr, x, rp[i], rp[i + 1]);
   y[i] = fma(wd[i], b[i] - acc, x[i]);
 }
 // x = C b (dense coarsest inverse, row-major nc x nc; one CTA)
@@ -328,27 +353,21 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<
   for (int l = l0; l + 1 < L; ++l) {
     const MGLevelView<V> D = lv[l];
     for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
-      V acc = V(0);
-      for (int k = D.Arp[i]; k < D.Arp[i + 1]; ++k) {
-        const int j = D.Aci[k];
-        acc = fma(D.Av[k], D.wd[j] * D.b[j], acc);
-      }
+      const V acc = csr_dot<V, true>(D.Aci, D.Av, D.wd, D.b, D.Arp[i], D.Arp[i + 1]);
       D.x[i] = D.wd[i] * D.b[i];
       D.t[i] = D.b[i] - acc;
     }
     __syncthreads();
     V* bn = lv[l + 1].b;
-    for (int i = threadIdx.x; i < D.nnext; i += blockDim.x) {
-      V acc = V(0);
-      for (int k = D.Rrp[i]; k < D.Rrp[i + 1]; ++k) acc = fma(D.Rv[k], D.t[D.Rci[k]], acc);
-      bn[i] = acc;
-    }
+    for (int i = threadIdx.x; i < D.nnext; i += blockDim.x)
+      bn[i] = csr_dot<V, false>(D.Rci, D.Rv, nullptr, D.t, D.Rrp[i], D.Rrp[i + 1]);
     __syncthreads();
   }
   {
     const MGLevelView<V> Z = lv[L - 1];
     for (int i = threadIdx.x; i < Z.n; i += blockDim.x) {
       V acc = V(0);
+#pragma unroll 8
       for (int j = 0; j < Z.n; ++j) acc = fma(C[(size_t)j * Z.n + i], Z.b[j], acc);
       Z.x[i] = acc;
     }
@@ -357,15 +376,11 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<
   for (int l = L - 2; l >= l0; --l) {
     const MGLevelView<V> D = lv[l];
     const V* sol = l + 1 == L - 1 ? lv[l + 1].x : lv[l + 1].y;
-    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
-      V acc = D.x[i];
-      for (int k = D.Prp[i]; k < D.Prp[i + 1]; ++k) acc = fma(D.Pv[k], sol[D.Pci[k]], acc);
-      D.x[i] = acc;
-    }
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x)
+      D.x[i] = csr_dot<V, false>(D.Pci, D.Pv, nullptr, sol, D.Prp[i], D.Prp[i + 1], D.x[i]);
     __syncthreads();
     for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
-      V acc = V(0);
-      for (int k = D.Arp[i]; k < D.Arp[i + 1]; ++k) acc = fma(D.Av[k], D.x[D.Aci[k]], acc);
+      const V acc = csr_dot<V, false>(D.Aci, D.Av, nullptr, D.x, D.Arp[i], D.Arp[i + 1]);
       D.y[i] = fma(D.wd[i], D.b[i] - acc, D.x[i]);
     }
     __syncthreads();
@@ -509,6 +524,18 @@ X* mg_alloc(std::vector<void*>& allocs, int64_t& bytes, size_t count) {
 
 void check(cudaError_t e) {
   if (e != cudaSuccess) throw Error(DGSL_ECUDA, cudaGetErrorString(e));
+}
+
+// CTAs per SM of the fine-level kernels (128 threads, ~40 registers: up to 16
+// fit).  A fixed number: it sets the order of the deterministic reductions,
+// so a system gets the same bits in every run.  DGSL_MG_CTAS_PER_SM (1..16)
+// overrides it, for sweeps.
+int mg_ctas_per_sm() {
+  if (const char* e = std::getenv("DGSL_MG_CTAS_PER_SM")) {
+    const int v = std::atoi(e);
+    if (v >= 1 && v <= 16) return v;
+  }
+  return 8;
 }
 
 int sm_count() {
@@ -716,7 +743,7 @@ MGSysPtr mg_sys_build(const MGTopo& topo, const DevOp& d, double coefK, double c
   const int sms = sm_count();
   const int tb = kMGThreads / d.nphi;
   const int ntile = (d.ne + tb - 1) / tb;
-  m.grid = std::max(1, std::min(ntile, sms * 8));
+  m.grid = std::max(1, std::min(ntile, sms * mg_ctas_per_sm()));
   m.cvid = topo.d_cvid;
   m.v2t_ptr = topo.d_v2t_ptr;
   m.v2t = topo.d_v2t;

@@ -59,11 +59,27 @@ struct DiffForm {
   static constexpr bool value = true;
 };
 
+// Two consecutive values of x (8 bytes for FP32, 16 for FP64) in one load.
+__device__ __forceinline__ void ld_pair(const float* p, float& a, float& b) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  a = t.x;
+  b = t.y;
+}
+__device__ __forceinline__ void ld_pair(const double* p, double& a, double& b) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  a = t.x;
+  b = t.y;
+}
+
 // Row `row` of K x.  COH: read x from L2 (x is written by other CTAs of a
-// persistent launch).  DIFF: couplings in difference form.
-template <int NPHI, typename T, typename V, bool COH, bool DIFF = DiffForm<T>::value>
+// persistent launch).  DIFF: couplings in difference form.  PAIR (even N_phi
+// only): read the coupled blocks of x two values per load, which needs x
+// aligned to two values (the callers' own allocations); the products and
+// their order are the same.
+template <int NPHI, typename T, typename V, bool COH, bool DIFF = DiffForm<T>::value, bool PAIR = false>
 __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int32_t* __restrict__ cols,
                                            int ne, int64_t n, int64_t row, const V* x) {
+  static_assert(!PAIR || (NPHI % 2 == 0 && !COH), "pair loads need an even block length");
   constexpr int VEC = Pack<T>::VEC;
   constexpr int NC = 4 * NPHI;
   constexpr int NG = (NC + VEC - 1) / VEC;
@@ -74,6 +90,7 @@ __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int
   V xr = V(0);
   if (DIFF) xr = COH ? ldcg(x + row) : __ldg(x + row);
   V acc = V(0);
+  V xodd = V(0);  // PAIR: the second value of the last pair
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     typename ValOf<T>::type v[VEC];
@@ -84,7 +101,15 @@ __device__ __forceinline__ V assembled_row(const T* __restrict__ vals, const int
       if (c < NC) {
         const int b = c / NPHI, kk = c % NPHI;
         const V* xp = x + (size_t)col[b] * NPHI + kk;
-        const V xv = COH ? ldcg(xp) : __ldg(xp);
+        V xv;
+        if constexpr (PAIR) {
+          if (kk % 2 == 0)
+            ld_pair(xp, xv, xodd);
+          else
+            xv = xodd;
+        } else {
+          xv = COH ? ldcg(xp) : __ldg(xp);
+        }
         acc = fma((V)v[u], DIFF ? xv - xr : xv, acc);
       }
     }

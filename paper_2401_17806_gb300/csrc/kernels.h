@@ -61,6 +61,11 @@ cudaError_t launch_mass_inv(const DevOp& op, const double* x, double* y, int nco
 cudaError_t launch_extrapolate(const double* a, double* prev, double* y, int64_t n, cudaStream_t s);
 
 // ---- vector helpers for the refinement loop
+// Sum over rows of sum_c (a_c x_c)^2 (FP64 couplings of coefK K + coefM Mbar,
+// the self coupling included) into part[2 * block] (k_apply.cu): the rounding
+// floor of the FP64 residual.
+cudaError_t launch_residual_floor_f64(const DevOp& op, double coefK, double coefM, const double* x, double* part,
+                                      int max_parts, int* nparts, cudaStream_t s);
 // r = b - A x (FP64 assembled form, A = coefM Mbar + coefK K), optional mean
 // projection of b; partial sums of r.r written to part[nblocks]; returns the
 // number of CTAs used (<= max_parts).
@@ -128,6 +133,9 @@ int cg_max_blocks(const DevOp& op, int prec);
 size_t cg_vec_bytes(const DevOp& op, int precond);
 // Bounded-wait self-test (see k_cg.cu): records kStatusTimeout in bar->status.
 cudaError_t launch_selftest_wait(GridBarrier* bar, int which, uint64_t timeout_ns, cudaStream_t s);
+// FMA throughput probe (k_cg.cu): blocks x 256 threads, 8 chains of iters FMAs
+// each; out holds blocks * 256 values of the vector type.
+cudaError_t launch_fma_rate(int fp64, void* out, int blocks, int iters, cudaStream_t s);
 
 // ---- semi-Lagrangian trajectories and transport (Sec. 2.5, eq. intstage; k_sl.cu)
 // Device copy of SLHost (host.h): per-triangle records [ne][16] doubles

@@ -154,6 +154,7 @@ void run_mg_request(const dgsl_request& r, const dgsl_engine_opts& o, cudaStream
     out.cg_launches += e.cg_launches;
     out.relres = std::max(out.relres, e.relres);
     out.cg_kernel_ms += e.cg_kernel_ms;
+    out.relres_floor = std::max(out.relres_floor, e.relres_floor);
   }
   *info = out;
 }
@@ -201,6 +202,7 @@ void info_from(const BCompletion& c, dgsl_solve_info* info) {
   info->cg_kernel_ms = 0.0;
   info->grid = 0;
   info->pad = 0;
+  info->relres_floor = 0.0;
 }
 
 std::mutex g_batch_mu;

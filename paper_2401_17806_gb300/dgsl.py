@@ -65,7 +65,7 @@ class dgsl_solve_opts(C.Structure):
 class dgsl_solve_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("refinements", C.c_int32),
                 ("cg_launches", C.c_int32), ("relres", C.c_double), ("cg_kernel_ms", C.c_double),
-                ("grid", C.c_int32), ("pad", C.c_int32)]
+                ("grid", C.c_int32), ("pad", C.c_int32), ("relres_floor", C.c_double)]
 
 
 MAX_RHS = 8  # right-hand sides per engine request
@@ -135,6 +135,7 @@ _SIGS = {
     "dgsl_default_solve_opts": (None, [C.POINTER(dgsl_solve_opts)]),
     "dgsl_default_engine_opts": (None, [C.POINTER(dgsl_engine_opts)]),
     "dgsl_selftest_wait_timeout": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
+    "dgsl_measure_fma_rate": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "dgsl_cg_solve_batch": (C.c_int, [C.POINTER(dgsl_request), C.c_int, C.POINTER(dgsl_engine_opts),
                                       C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_server_create": (C.c_int, [C.POINTER(dgsl_engine_opts), C.POINTER(C.c_void_p)]),
@@ -568,6 +569,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def dgsl_measure_fma_rate(fp64=True, device=0):
+    """Measured FMA throughput of the device in flop/s (2 per FMA)."""
+    v = C.c_double(0.0)
+    _check(load().dgsl_measure_fma_rate(int(device), int(bool(fp64)), C.byref(v)))
+    return v.value
 
 
 def dgsl_selftest_wait_timeout(which, timeout_s=0.2, device=0):

@@ -117,8 +117,9 @@ def test_mg_solve_meets_the_oracle_bars(dgsl_lib, prec, kind):
         assert err <= 1e-10
     else:
         assert err <= 10 * kappa * max(res, EPS64)
-    # tens of iterations to 1e-13 (unpreconditioned CG needs thousands here)
-    assert info.iters <= 150, info.iters
+    # tens of iterations per refinement step (unpreconditioned CG needs
+    # thousands here); a target near 4e-15 takes up to 8 steps of ~20
+    assert info.iters <= 200, info.iters
 
 
 def test_mg_iterations_nearly_flat_under_refinement(dgsl_lib):
