@@ -287,9 +287,20 @@ __global__ void k_csr_smooth0(int n, const int32_t* __restrict__ rp, const int32
   x[i] = wd[i] * b[i];
   t[i] = b[i] - acc;
 }
+// sum_k mv[k] x[ci[k]] over k in [k0, k1) by one warp (lane-strided partial
+// sums, then a fixed shuffle tree: a deterministic order); lane 0 holds it.
+template <typename V>
+__device__ __forceinline__ V warp_dot(const int32_t* __restrict__ ci, const V* __restrict__ mv, const V* x, int k0,
+                                      int k1, int lane) {
+  V acc = V(0);
+  for (int k = k0 + lane; k < k1; k += 32) acc = fma(mv[k], ci ? x[ci[k]] : x[k - k0], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
 // y = M x with one warp per row (the restriction's rows are long: an
-// aggregate's DOFs and their neighbours); the fixed shuffle tree keeps the
-// order deterministic
+// aggregate's DOFs and their neighbours)
 template <typename V>
 __global__ void k_csr_spmv_warp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                 const V* __restrict__ mv, const V* __restrict__ x, V* __restrict__ y,
@@ -297,10 +308,7 @@ __global__ void k_csr_spmv_warp(int n, const int32_t* __restrict__ rp, const int
   if (*((volatile const int*)&st->done)) return;
   const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (i >= n) return;
-  V acc = V(0);
-  for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) acc = fma(mv[k], x[ci[k]], acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const V acc = warp_dot<V>(ci, mv, x, rp[i], rp[i + 1], lane);
   if (lane == 0) y[i] = acc;
 }
 
@@ -335,10 +343,11 @@ struct MGLevelView {
   V *b, *x, *t, *y;
 };
 
-// Levels this small run inside one CTA: one SM moves the data of a level of
-// 7,637 rows (256^2 mesh, level 1) in ~220 us against ~15 us for the grid
-// kernels, so only the last levels go there.
-constexpr int kTailRows = 1024;
+// Levels this small run inside one CTA (always the dense coarsest level).  The
+// CSR gathers of a level go through one SM's L1/L2 path there: a level of
+// 7,637 rows (256^2 mesh, level 1) took ~220 us against ~15 us in the grid
+// kernels, and one of 904 rows (level 2) still ~45 us against ~25 us.
+constexpr int kTailRows = 256;
 constexpr int kTailThreads = 1024;
 
 // The V-cycle from level l0 (right-hand side in its b) down to the dense
@@ -350,6 +359,7 @@ template <typename V>
 __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<V>* __restrict__ lv, int l0, int L,
                                                              const V* __restrict__ C, const MGState* st) {
   if (*((volatile const int*)&st->done)) return;
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31), nwarp = (int)(blockDim.x >> 5);
   for (int l = l0; l + 1 < L; ++l) {
     const MGLevelView<V> D = lv[l];
     for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
@@ -358,18 +368,22 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<
       D.t[i] = D.b[i] - acc;
     }
     __syncthreads();
+    // the restriction's rows are long (an aggregate's DOFs and their
+    // neighbours): one warp per row, as k_csr_spmv_warp
     V* bn = lv[l + 1].b;
-    for (int i = threadIdx.x; i < D.nnext; i += blockDim.x)
-      bn[i] = csr_dot<V, false>(D.Rci, D.Rv, nullptr, D.t, D.Rrp[i], D.Rrp[i + 1]);
+    for (int i = warp; i < D.nnext; i += nwarp) {
+      const V acc = warp_dot<V>(D.Rci, D.Rv, D.t, D.Rrp[i], D.Rrp[i + 1], lane);
+      if (lane == 0) bn[i] = acc;
+    }
     __syncthreads();
   }
   {
+    // dense coarsest solve, one warp per row of C (exactly symmetric: row i
+    // holds column i, read contiguously)
     const MGLevelView<V> Z = lv[L - 1];
-    for (int i = threadIdx.x; i < Z.n; i += blockDim.x) {
-      V acc = V(0);
-#pragma unroll 8
-      for (int j = 0; j < Z.n; ++j) acc = fma(C[(size_t)j * Z.n + i], Z.b[j], acc);
-      Z.x[i] = acc;
+    for (int i = warp; i < Z.n; i += nwarp) {
+      const V acc = warp_dot<V>(nullptr, C + (size_t)i * Z.n, Z.b, 0, Z.n, lane);
+      if (lane == 0) Z.x[i] = acc;
     }
     __syncthreads();
   }
@@ -526,16 +540,42 @@ void check(cudaError_t e) {
   if (e != cudaSuccess) throw Error(DGSL_ECUDA, cudaGetErrorString(e));
 }
 
-// CTAs per SM of the fine-level kernels (128 threads, ~40 registers: up to 16
-// fit).  A fixed number: it sets the order of the deterministic reductions,
-// so a system gets the same bits in every run.  DGSL_MG_CTAS_PER_SM (1..16)
-// overrides it, for sweeps.
-int mg_ctas_per_sm() {
+// CTAs per SM of the fine-level kernels: as many as all four stay resident
+// with (the occupancy of the kernels themselves, by degree and type).  The
+// kernels are latency-bound (long-scoreboard stalls on the coupled blocks), so
+// resident warps are what they need: at 1024^2, p = 4, 12 CTAs per SM ran an
+// iteration in 6.38 ms against 7.92 ms at 8 (256^2, p = 3: 384 against 388
+// us).  The number depends on the device and the system only, so the order of
+// the deterministic reductions, and the bits, are the same in every run.
+// DGSL_MG_CTAS_PER_SM (1..16) overrides it, for sweeps.
+template <int NPHI, typename TK, typename TS, typename V>
+int fine_occupancy() {
+  int o[4] = {0, 0, 0, 0};
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_mg_matvec<NPHI, TK, V>, kMGThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_mg_update<NPHI, V, false>, kMGThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_mg_resid_restrict<NPHI, TS, V>, kMGThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_mg_post<NPHI, TS, V>, kMGThreads, 0);
+  return std::max(1, std::min(std::min(o[0], o[1]), std::min(o[2], o[3])));
+}
+
+template <typename TK, typename TS, typename V>
+int fine_occupancy(int nphi) {
+  switch (nphi) {
+    case 3: return fine_occupancy<3, TK, TS, V>();
+    case 6: return fine_occupancy<6, TK, TS, V>();
+    case 10: return fine_occupancy<10, TK, TS, V>();
+    default: return fine_occupancy<15, TK, TS, V>();
+  }
+}
+
+int mg_ctas_per_sm(int nphi, int type) {
   if (const char* e = std::getenv("DGSL_MG_CTAS_PER_SM")) {
     const int v = std::atoi(e);
     if (v >= 1 && v <= 16) return v;
   }
-  return 8;
+  if (type == 1) return fine_occupancy<double, double, double>(nphi);
+  if (type == 2) return fine_occupancy<float, uint16_t, float>(nphi);
+  return fine_occupancy<float, float, float>(nphi);
 }
 
 int sm_count() {
@@ -743,7 +783,7 @@ MGSysPtr mg_sys_build(const MGTopo& topo, const DevOp& d, double coefK, double c
   const int sms = sm_count();
   const int tb = kMGThreads / d.nphi;
   const int ntile = (d.ne + tb - 1) / tb;
-  m.grid = std::max(1, std::min(ntile, sms * mg_ctas_per_sm()));
+  m.grid = std::max(1, std::min(ntile, sms * mg_ctas_per_sm(d.nphi, type)));
   m.cvid = topo.d_cvid;
   m.v2t_ptr = topo.d_v2t_ptr;
   m.v2t = topo.d_v2t;
