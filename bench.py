@@ -88,6 +88,9 @@ def parse_args(argv=None):
     ap.add_argument("--rhs", type=int, default=8)
     ap.add_argument("--serve-nmax", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="serve workload: arrivals per rate at most (the window is shortened to about this "
+                         "many requests at high rates; above the server's capacity they queue)")
     ap.add_argument("--serve-rates", type=str, default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-precond", choices=["none", "block-jacobi", "multigrid"], default="multigrid")
     ap.add_argument("--serve-budget", type=float, default=150e9)
@@ -1166,14 +1169,17 @@ def serve_leg(args):
     warm_requests(pool, pc, dt)
     results = []
     for k, rate in enumerate(float(v) for v in args.serve_rates.split(",")):
-        results.append(serve_trace(pool, svc, rate, args.serve_seconds, 77 + k, pc, args.serve_budget,
+        window = min(args.serve_seconds, args.serve_requests / rate)
+        results.append(serve_trace(pool, svc, rate, window, 77 + k, pc, args.serve_budget,
                                    args.serve_nmax))
+        results[-1]["arrival_window_s"] = window
         print(json.dumps(results[-1]), file=sys.stderr, flush=True)
     print(json.dumps({
         "metric": "served Schur solves/s and p50/p99 latency", "workload": "serve", "data": "synthetic",
         "config": {"N_pool": sizes, "p_range": [1, 4], "rhs_per_request": [1, 8], "tol": WORKLOAD["tol"],
                    "precond": args.serve_precond, "hbm_budget_bytes": args.serve_budget,
-                   "seconds_per_rate": args.serve_seconds, "operator_pool_build_s": build_s,
+                   "seconds_per_rate": args.serve_seconds, "max_requests_per_rate": args.serve_requests,
+                   "operator_pool_build_s": build_s,
                    "fp64_service_times": {f"{n}x{n} p={p}": h for (n, p), h in sorted(how.items())},
                    "sample": f"N log-uniform in 16..{args.serve_nmax}"},
         "sweep": results}))
