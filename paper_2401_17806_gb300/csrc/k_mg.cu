@@ -17,7 +17,10 @@
 // couplings (16-byte loads, one thread per matrix row) and keep a tile of
 // TB = 128 / N_phi triangles per 128-thread CTA, so the per-triangle blocks of
 // D^-1 (the interleaved layout of the block-Jacobi preconditioner) and the
-// restriction to the three vertices work on shared memory.  Every reduction is
+// restriction to the three vertices work on shared memory.  The couplings are
+// streamed twice per iteration (A p, and r - A x1); the post-smoothing residual
+// r - A x2 is formed as (r - A x1) - (A Pc) e0 from 12 precomputed
+// coefficients per row of A Pc.  Every reduction is
 // deterministic: per-CTA partial sums, and the last CTA to arrive sums them in
 // CTA order.  The coarse levels are small CSR matrices (one thread per row)
 // and a dense coarsest inverse.  Scalars live in device memory, so an
@@ -199,12 +202,13 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_update(MGFine f, const V* __r
   grid_reduce<2>(v, part, red);
 }
 
-// w[t][m] = sum_k lambda_m(xi_k) (r - A x1)_(t, k): the residual restricted
-// to each triangle's vertices.
+// t1 = r - A x1 (kept for the post-smoothing) and w[t][m] = sum_k
+// lambda_m(xi_k) t1_(t, k): the residual restricted to each triangle's
+// vertices.
 template <int NPHI, typename T, typename V>
 __global__ void __launch_bounds__(kMGThreads) k_mg_resid_restrict(MGFine f, const V* __restrict__ r,
                                                                  const V* __restrict__ x1, V* __restrict__ w,
-                                                                 const MGState* st) {
+                                                                 V* __restrict__ t1, const MGState* st) {
   if (*((volatile const int*)&st->done)) return;
   constexpr int TB = kMGThreads / NPHI, ROWS = TB * NPHI;
   __shared__ V s_t[kMGThreads];
@@ -212,7 +216,10 @@ __global__ void __launch_bounds__(kMGThreads) k_mg_resid_restrict(MGFine f, cons
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t row = (int64_t)tile * ROWS + threadIdx.x;
     V tv = V(0);
-    if (threadIdx.x < ROWS && row < f.n) tv = r[row] - mg_row<NPHI, T, V>(f.svals, f, row, x1);
+    if (threadIdx.x < ROWS && row < f.n) {
+      tv = r[row] - mg_row<NPHI, T, V>(f.svals, f, row, x1);
+      t1[row] = tv;
+    }
     s_t[threadIdx.x] = tv;
     __syncthreads();
     if (threadIdx.x < 3 * TB) {
@@ -401,44 +408,114 @@ __global__ void __launch_bounds__(kTailThreads) k_coarse_tail(const MGLevelView<
   }
 }
 
-// x2 = x1 + Pc e0
-template <int NPHI, typename V>
-__global__ void k_mg_prolong_fine(MGFine f, const V* __restrict__ e0, const V* __restrict__ x1, V* __restrict__ x2,
-                                  const MGState* st) {
-  if (*((volatile const int*)&st->done)) return;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= f.n) return;
-  const int tri = (int)(row / NPHI), k = (int)(row - (int64_t)tri * NPHI);
-  V l[3];
-  node_lam<NPHI, V>(k, l);
-  V acc = x1[row];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) acc = fma(l[m], e0[f.cvid[(size_t)tri * 3 + m]], acc);
-  x2[row] = acc;
+// One coupling of the smoother's operator as FP64: row `row`, slot c (block
+// c / N_phi, node c % N_phi) of the interleaved layout.
+template <typename T>
+__device__ __forceinline__ double coupling_at(const T* vals, int64_t n, int64_t row, int c) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  const T v = vals[((int64_t)(c / VEC) * n + row) * VEC + c % VEC];
+  if constexpr (sizeof(T) == 2)
+    return (double)__uint_as_float((unsigned)v << 16);
+  else
+    return (double)v;
 }
 
-// z = x2 + omega_f D^-1 (r - A x2); reduction (r.z, sum z)
-template <int NPHI, typename T, typename V>
-__global__ void __launch_bounds__(kMGThreads) k_mg_post(MGFine f, const V* __restrict__ r, const V* __restrict__ x2,
-                                                       V* __restrict__ z, double* part, MGRed* red,
-                                                       const MGState* st) {
+// beta[row][b][m] = coefK sum_kk K_eff[row][(b, kk)] lambda_m(xi_kk): the
+// stiffness part of A Pc, row by row (b = 0 the own triangle, 1..3 the
+// neighbours, m their vertices).  K_eff is the difference form of the
+// smoother's couplings (off-diagonal a_c, diagonal -sum a_c), so each row of
+// beta sums to zero and is applied as sum beta (e0_v - (Pc e0)_row).  Layout
+// [12 / VP][n][VP] with VP values of V per 16 bytes.  FP64 arithmetic.
+template <int NPHI, typename TS, typename V>
+__global__ void k_mg_beta(const TS* __restrict__ vals, int64_t n, double coefK, V* __restrict__ beta) {
+  constexpr int VP = 16 / (int)sizeof(V);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int k = (int)(row % NPHI);
+  double bt[12] = {};
+  double rs = 0.0;
+  for (int c = 0; c < 4 * NPHI; ++c) {
+    const int b = c / NPHI, kk = c % NPHI;
+    if (b == 0 && kk == k) continue;  // the self slot: (x_row - x_row) in the difference form
+    const double a = coupling_at<TS>(vals, n, row, c);
+    double l[3];
+    node_lam<NPHI, double>(kk, l);
+    for (int m = 0; m < 3; ++m) bt[b * 3 + m] += a * l[m];
+    rs += a;
+  }
+  double lk[3];
+  node_lam<NPHI, double>(k, lk);
+  for (int m = 0; m < 3; ++m) bt[m] -= rs * lk[m];
+  for (int q = 0; q < 12; ++q) beta[((int64_t)(q / VP) * n + row) * VP + q % VP] = (V)(coefK * bt[q]);
+}
+
+// Post-smoothing from the pre-smoothing residual: with x2 = x1 + Pc e0,
+// r - A x2 = t1 - (A Pc) e0, and (A Pc) e0 = sum_(b, m) beta (e0_v - pe)
+// (+ coefM A_t sum_kk Mref[k][kk] (Pc e0)_kk for the Helmholtz mass term),
+// pe = (Pc e0)_row.  Then z = x2 + omega_f D^-1 (r - A x2); reduction (r.z,
+// sum z).  This reads 12 coefficients per row instead of the row's 4 N_phi
+// couplings and needs no x2 vector.
+template <int NPHI, typename V>
+__global__ void __launch_bounds__(kMGThreads) k_mg_post(MGFine f, const V* __restrict__ r, const V* __restrict__ x1,
+                                                       const V* __restrict__ t1, const V* __restrict__ e0,
+                                                       const V* __restrict__ beta, V* __restrict__ z, double* part,
+                                                       MGRed* red, const MGState* st) {
   if (*((volatile const int*)&st->done)) return;
   constexpr int TB = kMGThreads / NPHI, ROWS = TB * NPHI;
+  constexpr int VP = 16 / (int)sizeof(V);
   __shared__ V s_t[kMGThreads];
   const int ntile = (f.ne + TB - 1) / TB;
   V a0 = V(0), a1 = V(0);
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t row = (int64_t)tile * ROWS + threadIdx.x;
     const bool act = threadIdx.x < ROWS && row < f.n;
-    V rv = V(0), tv = V(0);
+    V rv = V(0), tv = V(0), x2v = V(0);
     if (act) {
+      const int tri = (int)(row / NPHI), k = (int)(row - (int64_t)tri * NPHI);
+      V lk[3];
+      node_lam<NPHI, V>(k, lk);
+      V ev[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) ev[m] = e0[__ldg(f.cvid + (size_t)tri * 3 + m)];
+      V pe = V(0);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) pe = fma(lk[m], ev[m], pe);
+      x2v = x1[row] + pe;
+      V bt[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) bt[q] = __ldg(beta + ((int64_t)(q / VP) * f.n + row) * VP + q % VP);
+      V apc = V(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int cb = b == 0 ? tri : __ldg(f.cols + (size_t)b * f.ne_pad + tri);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const V e = b == 0 ? ev[m] : e0[__ldg(f.cvid + (size_t)cb * 3 + m)];
+          apc = fma(bt[b * 3 + m], e - pe, apc);
+        }
+      }
+      if (f.coefM != 0.0) {
+        V ml[3] = {V(0), V(0), V(0)};
+#pragma unroll
+        for (int kk = 0; kk < NPHI; ++kk) {
+          V l[3];
+          node_lam<NPHI, V>(kk, l);
+          const V mr = (V)__ldg(f.Mref + k * NPHI + kk);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) ml[m] = fma(mr, l[m], ml[m]);
+        }
+        V mp = V(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) mp = fma(ml[m], ev[m], mp);
+        apc = fma((V)(f.coefM * __ldg(f.area + tri)), mp, apc);
+      }
       rv = r[row];
-      tv = rv - mg_row<NPHI, T, V>(f.svals, f, row, x2);
+      tv = t1[row] - apc;
     }
     s_t[threadIdx.x] = tv;
     __syncthreads();
     if (act) {
-      const V zv = x2[row] + mg_bj<NPHI, V>(f, row, s_t + (threadIdx.x / NPHI) * NPHI);
+      const V zv = x2v + mg_bj<NPHI, V>(f, row, s_t + (threadIdx.x / NPHI) * NPHI);
       z[row] = zv;
       a0 = fma(rv, zv, a0);
       a1 += zv;
@@ -554,7 +631,7 @@ int fine_occupancy() {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[0], k_mg_matvec<NPHI, TK, V>, kMGThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[1], k_mg_update<NPHI, V, false>, kMGThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[2], k_mg_resid_restrict<NPHI, TS, V>, kMGThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_mg_post<NPHI, TS, V>, kMGThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o[3], k_mg_post<NPHI, V>, kMGThreads, 0);
   return std::max(1, std::min(std::min(o[0], o[1]), std::min(o[2], o[3])));
 }
 
@@ -566,6 +643,29 @@ int fine_occupancy(int nphi) {
     case 10: return fine_occupancy<10, TK, TS, V>();
     default: return fine_occupancy<15, TK, TS, V>();
   }
+}
+
+template <typename TS, typename V>
+cudaError_t launch_beta_t(const DevOp& d, const void* vals, double coefK, void* beta, cudaStream_t s) {
+  const unsigned g = (unsigned)((d.n + 255) / 256);
+  const TS* tv = static_cast<const TS*>(vals);
+  V* bv = static_cast<V*>(beta);
+  switch (d.nphi) {
+    case 3: k_mg_beta<3, TS, V><<<g, 256, 0, s>>>(tv, d.n, coefK, bv); break;
+    case 6: k_mg_beta<6, TS, V><<<g, 256, 0, s>>>(tv, d.n, coefK, bv); break;
+    case 10: k_mg_beta<10, TS, V><<<g, 256, 0, s>>>(tv, d.n, coefK, bv); break;
+    default: k_mg_beta<15, TS, V><<<g, 256, 0, s>>>(tv, d.n, coefK, bv); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// beta from the couplings the smoother applies (BF16 for type 2, FP32 for
+// type 0, FP64 for type 1), so the pre- and post-smoothing use one operator
+cudaError_t launch_beta(const DevOp& d, int type, double coefK, void* beta, cudaStream_t s) {
+  if (type == 1) return launch_beta_t<double, double>(d, d.K64, coefK, beta, s);
+  if (type == 2) return launch_beta_t<uint16_t, float>(d, d.K16, coefK, beta, s);
+  return launch_beta_t<float, float>(d, d.K32, coefK, beta, s);
 }
 
 int mg_ctas_per_sm(int nphi, int type) {
@@ -657,7 +757,8 @@ struct MGSys {
   int grid = 0;                // CTAs of the fine-level kernels
   // fine level (vector type V: float for types 0 and 2, double for 1)
   void* dinv = nullptr;
-  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x1 = nullptr, *x2 = nullptr, *w = nullptr;
+  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x1 = nullptr, *t1 = nullptr, *w = nullptr;
+  void* beta = nullptr;        // [12 / VP][n][VP]: the stiffness part of A Pc (k_mg_beta)
   double* part = nullptr;      // [grid][3]
   MGRed* red = nullptr;        // [3]: matvec, update, post
   MGState* st = nullptr;
@@ -800,7 +901,9 @@ MGSysPtr mg_sys_build(const MGTopo& topo, const DevOp& d, double coefK, double c
   m.p = vec(d.n);
   m.q = vec(d.n);
   m.x1 = vec(d.n);
-  m.x2 = vec(d.n);
+  m.t1 = vec(d.n);
+  m.beta = vec((size_t)12 * d.n);
+  check(launch_beta(d, type, coefK, m.beta, s));
   m.w = vec((size_t)3 * d.ne);
   m.part = mg_alloc<double>(m.allocs, m.bytes, (size_t)m.grid * 3);
   m.red = mg_alloc<MGRed>(m.allocs, m.bytes, 3);
@@ -847,9 +950,9 @@ struct MGRun {
   V* v(void* p) { return static_cast<V*>(p); }
   int g1(int64_t n) { return (int)std::max<int64_t>(1, (n + 255) / 256); }
 
-  // z = M r for r in m.r (x1, x2 and the level vectors as scratch)
+  // z = M r for r in m.r (x1, t1 and the level vectors as scratch)
   void precond(V* z, MGRed* red_post) {
-    k_mg_resid_restrict<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.w), m.st);
+    k_mg_resid_restrict<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.w), v(m.t1), m.st);
     k_mg_vgather<V><<<g1(m.host.nv), 256, 0, s>>>(m.host.nv, m.v2t_ptr, m.v2t, v(m.w), lv[0].b, m.st);
     launches += 2;
     const int L = (int)lv.size(), T = m.tail;
@@ -870,9 +973,9 @@ struct MGRun {
       launches += 2;
       sol = D.y;
     }
-    k_mg_prolong_fine<NPHI, V><<<g1(d.n), 256, 0, s>>>(f, sol, v(m.x1), v(m.x2), m.st);
-    k_mg_post<NPHI, TS, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x2), z, m.part, red_post, m.st);
-    launches += 2;
+    k_mg_post<NPHI, V><<<m.grid, kMGThreads, 0, s>>>(f, v(m.r), v(m.x1), v(m.t1), sol, v(m.beta), z, m.part,
+                                                     red_post, m.st);
+    ++launches;
   }
 
   int gdir() { return (int)std::max<int64_t>(1, std::min<int64_t>((d.n + 255) / 256, (int64_t)sm_count() * 8)); }
