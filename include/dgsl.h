@@ -167,6 +167,18 @@ int dgsl_node_coords(const dgsl_operator* op, int grid, double* xy);
  * also for host-only operators. */
 int dgsl_query_sl_tables(const dgsl_operator* op, int32_t* nbr, double* trans);
 
+/* Host FP64 copies of the assembled couplings of K = G^T Mhat^{-1} G (the
+ * Schur operator is dt^2 K, eq. pressure_final; the viscous one Mbar + nu dt K,
+ * eq. ad5), internal triangle order (any pointer may be NULL):
+ *   Kd  [n_tri][n_phi k][n_phi l]     block (i, i): row (i, k), column (i, l)
+ *   Ko  [n_tri][3][n_phi k][n_phi l]  block (i, nbr[i][e]) across local edge e
+ *   nbr [n_tri][3]                    the neighbour across local edge e
+ * These are the values the device copies are made from (FP64 as is, FP32 and
+ * BF16 rounded, with the self coupling stored as 0 in the difference form).
+ * Kept only for host_only or factored builds (DGSL_EINVAL otherwise).  Pure
+ * host call. */
+int dgsl_query_couplings(const dgsl_operator* op, double* Kd, double* Ko, int32_t* nbr);
+
 /* Host FP64 copies of the blocks, internal edge order (any may be NULL):
  *   G    [n_edge][2 side][2 comp][n_phi m][n_phi k] = Q_{s,j}[L_s(m), k, comp]
  *        (eq. ad5.2 restricted to the dual nodes of side s)

@@ -249,6 +249,15 @@ int dgsl_query_blocks(const dgsl_operator* op, double* G, double* Minv, double* 
   return DGSL_OK;
 }
 
+int dgsl_query_couplings(const dgsl_operator* op, double* Kd, double* Ko, int32_t* nbr) {
+  if (!op) return fail(DGSL_EINVAL, "NULL operator");
+  if (!op->have_blocks) return fail(DGSL_EINVAL, "couplings kept only for host_only or factored builds");
+  if (Kd) std::memcpy(Kd, op->hb.Kd.data(), op->hb.Kd.size() * sizeof(double));
+  if (Ko) std::memcpy(Ko, op->hb.Ko.data(), op->hb.Ko.size() * sizeof(double));
+  if (nbr) std::memcpy(nbr, op->hb.nbr.data(), op->hb.nbr.size() * sizeof(int32_t));
+  return DGSL_OK;
+}
+
 static int check_vec_args(const void* a, const void* b, int n_rhs) {
   if (!a || !b) return fail(DGSL_EINVAL, "vector pointers must be non-NULL");
   if (n_rhs < 1) return fail(DGSL_EINVAL, "n_rhs must be >= 1");

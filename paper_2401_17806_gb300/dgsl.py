@@ -136,6 +136,7 @@ _SIGS = {
     "dgsl_default_engine_opts": (None, [C.POINTER(dgsl_engine_opts)]),
     "dgsl_selftest_wait_timeout": (C.c_int, [C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)]),
     "dgsl_measure_fma_rate": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "dgsl_query_couplings": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dgsl_cg_solve_batch": (C.c_int, [C.POINTER(dgsl_request), C.c_int, C.POINTER(dgsl_engine_opts),
                                       C.POINTER(dgsl_solve_info), C.c_void_p]),
     "dgsl_server_create": (C.c_int, [C.POINTER(dgsl_engine_opts), C.POINTER(C.c_void_p)]),
@@ -277,6 +278,17 @@ class Operator:
         out = np.zeros((n, 2))
         _check(load().dgsl_node_coords(self.h, int(grid), C.c_void_p(out.ctypes.data)))
         return out
+
+    def couplings(self):
+        """(Kd [n_tri][n_phi][n_phi], Ko [n_tri][3][n_phi][n_phi], nbr [n_tri][3]),
+        internal order (host_only or factored builds)."""
+        n = self.n_phi
+        Kd = np.zeros((self.n_tri, n, n))
+        Ko = np.zeros((self.n_tri, 3, n, n))
+        nbr = np.zeros((self.n_tri, 3), dtype=np.int32)
+        _check(load().dgsl_query_couplings(self.h, C.c_void_p(Kd.ctypes.data), C.c_void_p(Ko.ctypes.data),
+                                           C.c_void_p(nbr.ctypes.data)))
+        return Kd, Ko, nbr
 
     def blocks(self):
         n, npsi = self.n_phi, self.n_psi
