@@ -121,14 +121,15 @@ constexpr int kMGWorkers = 8;
 
 // Device bytes an operator may grow by at its first multigrid solve of a
 // system (the solve workspace, the vertex topology, the smoother blocks, the
-// PCG vectors; the coarse levels are small): an upper estimate for admission.
+// 12 coefficients per row of A Pc, the six fine vectors; the coarse levels are
+// small): an upper estimate for admission.
 int64_t mg_growth_estimate(const dgsl_operator* op, int precision) {
   const DevOp& d = op->d;
   const int64_t vb = precision == DGSL_PREC_F64 ? 8 : 4, vp = 16 / vb;
   const int64_t work = 24 * d.n + (int64_t)cg_vec_bytes(d, 1) + 64 * 1024;
   const int64_t topo = 24 * (int64_t)d.ne + 64 * 1024;
-  const int64_t sys = ((d.nphi + vp - 1) / vp) * d.n * 16 + 6 * d.n * vb + 3 * (int64_t)d.ne * vb + (int64_t)d.ne * 40 +
-                      8 * 1024 * 1024;
+  const int64_t sys = ((d.nphi + vp - 1) / vp) * d.n * 16 + 12 * d.n * vb + 6 * d.n * vb + 3 * (int64_t)d.ne * vb +
+                      (int64_t)d.ne * 40 + 8 * 1024 * 1024;
   return work + topo + sys;
 }
 
